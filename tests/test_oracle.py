@@ -1,0 +1,393 @@
+"""Pins for the CPU oracle against facts the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each case is a closed form, a
+brute-force dense computation, an algebraic identity stated in the paper, or a
+number printed in the paper (``tests/golden``).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _grid(n):
+    return np.arange(1, n + 1) / (n + 1)
+
+
+# --------------------------------------------------------------------------
+# Sequential march (Eq. (timemarch)) and right-hand side (Eq. (finesys)).
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("theta", [0.0, 0.5, 1.0, 0.3])
+@pytest.mark.parametrize("k", [1, 4, 11])
+def test_march_eigenmode_1d(theta, k):
+    """sin(k pi x) decays by the closed-form factor r_k per step."""
+    n, nt, tau, T = 31, 24, 0.7, 0.002 if theta < 0.5 else 0.05
+    dt = T / nt
+    x = _grid(n)
+    u0 = np.sin(k * math.pi * x)
+    u = O.theta_march(1, n, 1, nt, tau, theta, dt, u0, None)
+    h = 1.0 / (n + 1)
+    lam = -(4 * tau / h ** 2) * math.sin(k * math.pi * h / 2) ** 2
+    r = (1 + (1 - theta) * dt * lam) / (1 - theta * dt * lam)
+    ref = np.array([r ** j for j in range(nt + 1)])[:, None] * u0[None]
+    assert np.abs(u - ref).max() <= 1e-13
+
+
+@pytest.mark.parametrize("theta", [0.5, 1.0])
+def test_march_eigenmode_2d(theta):
+    nx, ny, nt, tau, T = 9, 7, 12, 1.3, 0.02
+    dt = T / nt
+    k, l = 3, 2
+    ux, uy = np.sin(k * math.pi * _grid(nx)), np.sin(l * math.pi * _grid(ny))
+    u0 = np.outer(uy, ux)
+    u = O.theta_march(2, nx, ny, nt, tau, theta, dt, u0, None)
+    lam = -(4 * tau * (nx + 1) ** 2) * math.sin(k * math.pi / (2 * (nx + 1))) ** 2 \
+          - (4 * tau * (ny + 1) ** 2) * math.sin(l * math.pi / (2 * (ny + 1))) ** 2
+    r = (1 + (1 - theta) * dt * lam) / (1 - theta * dt * lam)
+    ref = np.array([r ** j for j in range(nt + 1)])[:, None, None] * u0[None]
+    assert np.abs(u - ref).max() <= 1e-13
+
+
+@pytest.mark.parametrize("theta", [0.5, 1.0, 0.2])
+def test_march_eigenmode_with_source(theta):
+    """g_k = c_k sin(k pi x): the march reduces to the scalar theta-scheme for the mode."""
+    n, nt, tau, T, k = 15, 20, 1.0, 0.03, 2
+    dt = T / nt
+    x = _grid(n)
+    mode = np.sin(k * math.pi * x)
+    rng = np.random.default_rng(5)
+    c = rng.standard_normal(nt + 1)
+    g = c[:, None] * mode[None]
+    u = O.theta_march(1, n, 1, nt, tau, theta, dt, 0.5 * mode, g)
+    h = 1.0 / (n + 1)
+    lam = -(4 * tau / h ** 2) * math.sin(k * math.pi * h / 2) ** 2
+    s = [0.5]
+    for j in range(1, nt + 1):
+        # scalar theta-scheme: (1 - theta dt lam) s_j = (1 + (1-theta) dt lam) s_{j-1}
+        #                       + dt ((1-theta) c_{j-1} + theta c_j)
+        s.append(((1 + (1 - theta) * dt * lam) * s[-1] + dt * ((1 - theta) * c[j - 1] + theta * c[j]))
+                 / (1 - theta * dt * lam))
+    ref = np.array(s)[:, None] * mode[None]
+    assert np.abs(u - ref).max() <= 1e-13
+
+
+def test_steady_state_source():
+    """If g = -A_n u* then u_0 = u* stays put for any theta (weights of gbar sum to one)."""
+    n, nt, tau = 20, 10, 2.0
+    rng = np.random.default_rng(1)
+    us = rng.standard_normal(n)
+    L = O.fd_laplacian(n, tau)
+    g = np.repeat((-L.apply(us))[None], nt + 1, axis=0)
+    for theta in (0.0, 0.37, 0.5, 1.0):
+        u = O.theta_march(1, n, 1, nt, tau, theta, 1e-4, us, g)
+        assert np.abs(u - us[None]).max() <= 1e-11
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_march_equals_dense_solve(dim):
+    """Brute force: the march solves the dense all-at-once system Eq. (finesys)."""
+    rng = np.random.default_rng(2)
+    nx, ny, nt = (9, 1, 8) if dim == 1 else (5, 4, 6)
+    lv = O.build_levels(dim, nx, ny, nt, 1.7, 0.6, 0.01, (), (), "one")[0]
+    f = rng.standard_normal(lv.shape())
+    u = O.march(lv, f)
+    A = O.dense_A(lv)
+    ref = np.linalg.solve(A, f.ravel())
+    assert np.abs(u.ravel() - ref).max() <= 1e-12
+    # the oracle's stencil matvec is the dense matrix
+    assert np.abs(lv.apply_A(u).ravel() - A @ u.ravel()).max() <= 1e-12
+
+
+def test_dense_A_structure():
+    """Eq. (finesys): identity block, psi on the diagonal, -phi below."""
+    n, nt, tau, theta, dt = 6, 3, 1.0, 0.5, 0.01
+    lv = O.build_levels(1, n, 1, nt, tau, theta, dt, (), (), "one")[0]
+    A = O.dense_A(lv)
+    h = 1.0 / (n + 1)
+    An = tau / h ** 2 * (np.diag(-2 * np.ones(n)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1))
+    psi = np.eye(n) - theta * dt * An
+    phi = np.eye(n) + (1 - theta) * dt * An
+    assert np.array_equal(A[:n, :n], np.eye(n))
+    assert np.allclose(A[n:2 * n, n:2 * n], psi, rtol=0, atol=1e-12)
+    assert np.allclose(A[2 * n:3 * n, n:2 * n], -phi, rtol=0, atol=1e-12)
+    assert not A[:n, n:].any()
+
+
+def test_rhs_assembly_weights():
+    """f_0 = u_0 and f_k = dt gbar_k with gbar_k = (1-theta) g_{k-1} + theta g_k."""
+    nt, n, theta, dt = 4, 3, 0.25, 0.1
+    u0 = np.array([1.0, 2.0, 3.0])
+    g = np.zeros((nt + 1, n))
+    g[2] = 1.0       # impulse at t_2: enters f_2 with weight theta and f_3 with 1-theta
+    f = O.assemble_rhs(u0, g, nt, theta, dt)
+    assert np.array_equal(f[0], u0)
+    assert np.allclose(f[2], dt * theta) and np.allclose(f[3], dt * (1 - theta))
+    assert not f[1].any() and not f[4].any()
+
+
+# --------------------------------------------------------------------------
+# Transfers and Galerkin coarse operators (Sec. 3.2).
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [8, 9, 1, 2, 3])
+def test_YtZ_identity(n):
+    Y, Z = O.agglomeration_Y(n), O.agglomeration_Z(n)
+    assert np.allclose(Y.T @ Z, np.eye(Z.shape[1]))
+    assert Z.shape[1] == (n + 1) // 2
+
+
+def test_pairs_give_sqrt2_spacing():
+    """Y^T A Z with pair agglomeration is the FD Laplacian with dX^2 = 2 dx^2 (Sec. 3.2)."""
+    n, tau = 16, 1.3
+    L = O.fd_laplacian(n, tau)
+    C = O.galerkin_space(L).dense()
+    h = 1.0 / (n + 1)
+    m = n // 2
+    ref = tau / (2 * h * h) * (np.diag(-2 * np.ones(m)) + np.diag(np.ones(m - 1), 1) + np.diag(np.ones(m - 1), -1))
+    assert np.allclose(C, ref, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("dim,nx,ny,nt,nu,space,theta", [
+    (1, 7, 1, 6, 2, False, 0.5), (1, 7, 1, 6, 3, False, 1.0), (1, 7, 1, 8, 4, False, 0.3),
+    (1, 8, 1, 6, 2, True, 0.5), (1, 9, 1, 6, 3, True, 1.0), (1, 5, 1, 4, 2, True, 0.0),
+    (2, 4, 3, 4, 2, False, 0.5), (2, 5, 4, 4, 2, True, 1.0), (2, 3, 5, 6, 3, True, 0.7),
+])
+def test_galerkin_is_modified_theta_scheme(dim, nx, ny, nt, nu, space, theta):
+    """Y^T A_h Z (dense, brute force) equals the next level built as a theta-scheme with
+    a' = nu a + (nu-1) b, b' = b, L' = Y^T L Z (Eqs. (timecoarse1)-(timecoarse3), read
+    as the literal Galerkin product)."""
+    levels = O.build_levels(dim, nx, ny, nt, 0.9, theta, 0.013, (nu,), (space,), "one")
+    A = O.dense_A(levels[0])
+    Y, Z = O.dense_transfers(levels[0], nu, space)
+    assert np.abs(Y.T @ A @ Z - O.dense_A(levels[1])).max() <= 1e-12 * np.abs(A).max()
+
+
+def test_printed_coarse_formula_differs_off_half():
+    """The printed coarse blocks I-(nu-theta)dtA and -(I+theta dt A) agree with the
+    Galerkin product only at theta = 1/2 (reading recorded for Eq. (timecoarse2))."""
+    n, nt, nu, dt = 5, 4, 2, 0.01
+    for theta, agree in ((0.5, True), (1.0, False)):
+        lv = O.build_levels(1, n, 1, nt, 1.0, theta, dt, (nu,), (False,), "one")
+        An = lv[0].Lx.dense()
+        printed = np.eye(n) - (nu - theta) * dt * An
+        galerkin = np.eye(n) - lv[1].a * An
+        assert np.allclose(printed, galerkin) == agree
+
+
+@pytest.mark.parametrize("dim,space", [(1, False), (1, True), (2, True)])
+def test_restrict_interpolate_are_dense_Y_Z(dim, space):
+    rng = np.random.default_rng(3)
+    nx, ny, nt, nu = (7, 1, 6, 3) if dim == 1 else (5, 3, 4, 2)
+    lv = O.build_levels(dim, nx, ny, nt, 1.0, 0.5, 0.01, (nu,), (space,), "one")
+    Y, Z = O.dense_transfers(lv[0], nu, space)
+    v = rng.standard_normal(lv[0].shape())
+    assert np.allclose(O.restrict(lv[0], nu, space, v).ravel(), Y.T @ v.ravel(), atol=1e-14)
+    vt = rng.standard_normal(lv[1].shape())
+    assert np.allclose(O.interpolate(lv[0], nu, space, vt).ravel(), Z @ vt.ravel(), atol=1e-14)
+
+
+def test_lambda_max_matches_dense_spectrum():
+    # n_t = 1 keeps the dense matrix free of repeated (defective) diagonal blocks
+    lv = O.build_levels(2, 5, 4, 1, 1.2, 1.0, 0.02, (), (), "lambda_max")[0]
+    ev = np.linalg.eigvals(O.dense_A(lv)).real
+    assert abs(lv.mu - ev.max()) <= 1e-10 * ev.max()
+    # 1D closed form: 1 + theta dt (4 tau/h^2) sin^2(n pi h / 2)
+    n, tau, dt = 13, 0.8, 0.003
+    lv1 = O.build_levels(1, n, 1, 3, tau, 0.5, dt, (), (), "lambda_max")[0]
+    h = 1.0 / (n + 1)
+    assert abs(lv1.mu - (1 + 0.5 * dt * 4 * tau / h ** 2 * math.sin(n * math.pi * h / 2) ** 2)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Preconditioner, decoupled coarsest level, FGMRES (Sec. 3.1, 3.3.2, 4.1, Alg. 2).
+# --------------------------------------------------------------------------
+
+def _table1_kappa(coarsening, C, nt, nu):
+    n = 64
+    h = 1.0 / (n + 1)
+    dt = C * h * h / 2
+    lv = O.build_levels(1, n, 1, nt, 1.0, 0.5, dt, (), (), "one")[0]
+    A = O.dense_A(lv)
+    if nu is None:
+        s = np.linalg.svd(A, compute_uv=False)
+        return s[0] / s[-1]
+    Y, Z = O.dense_transfers(lv, nu, coarsening == "TS")
+    s = np.linalg.svd(A @ O.dense_Q(A, Y, Z, 1.0), compute_uv=False)
+    return s[0] / s[-1]
+
+
+def _table1_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1_condition_numbers.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            c, C, nt, k2, k4, k8, kA = line.split()
+            rows.append((c, float(C), int(nt), [float(k2), float(k4), float(k8)], float(kA)))
+    return rows
+
+
+@pytest.mark.parametrize("row", [r for r in _table1_rows() if r[1] >= 0.32],
+                         ids=lambda r: f"{r[0]}-C{r[1]}")
+def test_table1_condition_numbers(row):
+    coarsening, C, nt, kappas, kA = row
+    for nu, ref in zip((2, 4, 8), kappas):
+        assert abs(_table1_kappa(coarsening, C, nt, nu) - ref) <= 0.015
+    assert abs(_table1_kappa(coarsening, C, nt, None) - kA) <= 0.015
+
+
+def test_table1_smallest_courant_T_nu2():
+    row = [r for r in _table1_rows() if r[0] == "T" and r[1] == 0.16][0]
+    assert abs(_table1_kappa("T", 0.16, row[2], 2) - row[3][0]) <= 0.015
+
+
+def test_table2_two_level_iterations():
+    with open(os.path.join(GOLDEN, "table2_iterations.txt")) as fh:
+        rows = [list(map(int, l.split())) for l in fh if l.strip() and not l.startswith("#")]
+    for n, nt, *iters in rows:
+        h = 1.0 / (n + 1)
+        dt = 0.32 * h * h
+        u0 = np.random.default_rng(7).uniform(size=n)
+        f = O.assemble_rhs(u0, None, nt, 0.5, dt)
+        for nu, ref in zip((2, 4, 8), iters):
+            H = O.make_hierarchy(1, n, 1, nt, 1.0, 0.5, dt, (nu,), (False,), (), 0, mu_mode="one")
+            _, info = O.fgmres(H, f, 1e-6, restart=200, maxit=200)
+            assert abs(info.iterations - ref) <= 3, (n, nu, info.iterations, ref)
+
+
+@pytest.mark.parametrize("dim,space,n_cgs", [(1, False, 0), (1, False, 4), (1, True, 2), (2, True, 2)])
+def test_two_level_precondition_is_dense_Q(dim, space, n_cgs):
+    """Substeps 4.1-4.5 apply Eq. (Qh) (n_cgs = 0) / Eq. (Qhtilde) (decoupled)."""
+    rng = np.random.default_rng(4)
+    nx, ny, nt = (6, 1, 8) if dim == 1 else (4, 3, 8)
+    H = O.make_hierarchy(dim, nx, ny, nt, 1.0, 0.5, 0.02, (2,), (space,), (), n_cgs)
+    lv0, lv1 = H.levels
+    A = O.dense_A(lv0)
+    Y, Z = O.dense_transfers(lv0, 2, space)
+    AH = None if n_cgs == 0 else O.dense_decoupled(lv1, n_cgs)
+    Q = O.dense_Q(A, Y, Z, lv0.mu, AH)
+    v = rng.standard_normal(lv0.shape())
+    assert np.abs(O.precondition(H, 0, v).ravel() - Q @ v.ravel()).max() <= 1e-11
+
+
+def test_coarsest_solve_is_dense_decoupled():
+    rng = np.random.default_rng(8)
+    for dim, nx, ny in ((1, 7, 1), (2, 4, 3)):
+        lv = O.build_levels(dim, nx, ny, 12, 1.0, 1.0, 0.05, (), (), "one")[0]
+        r = rng.standard_normal(lv.shape())
+        for n_cgs in (1, 3, 12):
+            x = O.coarsest_solve(lv, r, n_cgs)
+            ref = np.linalg.solve(O.dense_decoupled(lv, n_cgs), r.ravel())
+            assert np.abs(x.ravel() - ref).max() <= 1e-12
+
+
+def test_decoupled_spectrum_equals_coupled():
+    """sigma(A_h Qtilde_h) = sigma(A_h Q_h) (Sec. 3.3.2): both are block lower triangular
+    over the coarse time blocks and share their diagonal blocks A_kk Q_k."""
+    n, nu = 6, 2
+    lv = O.build_levels(1, n, 1, 8, 1.0, 0.5, 0.01, (nu,), (False,), "one")
+    A = O.dense_A(lv[0])
+    Y, Z = O.dense_transfers(lv[0], nu, False)
+    M1 = A @ O.dense_Q(A, Y, Z, 1.0)
+    M2 = A @ O.dense_Q(A, Y, Z, 1.0, O.dense_decoupled(lv[1], 4))
+    starts = [0] + [n + K * nu * n for K in range(lv[1].nt)] + [A.shape[0]]
+    for b in range(len(starts) - 1):
+        s0, s1 = starts[b], starts[b + 1]
+        assert np.abs(M1[s0:s1, s0:s1] - M2[s0:s1, s0:s1]).max() <= 1e-12
+        if s1 < A.shape[0]:
+            assert np.abs(M1[s0:s1, s1:]).max() <= 1e-12 and np.abs(M2[s0:s1, s1:]).max() <= 1e-12
+    assert np.abs(M1 - M2).max() > 1e-3          # the matrices themselves differ
+    # eigenvalues agree up to the sensitivity of the defective cluster at 1
+    e1 = np.sort_complex(np.linalg.eigvals(M1))
+    e2 = np.sort_complex(np.linalg.eigvals(M2))
+    assert np.abs(e1 - e2).max() <= 1e-3
+    # T-coarsening with mu = 1: a cluster sits exactly at 1 (Sec. 3.3.1)
+    assert np.sum(np.abs(e1 - 1.0) < 1e-8) >= lv[1].nt * n
+
+
+def test_inner_fgmres_minimises_residual():
+    """Fixed-m FGMRES (zero guess) returns the minimum-residual combination of its
+    preconditioned directions: brute-force least squares over span(X) agrees."""
+    rng = np.random.default_rng(9)
+    H = O.make_hierarchy(1, 9, 1, 16, 1.0, 1.0, 0.01, (2, 2), (False, False), (2,), 2)
+    lv = H.levels[1]
+    b = rng.standard_normal(lv.shape())
+    u = O.fgmres_fixed(H, 1, b, 2)
+    # rebuild the two directions the same process generates
+    beta = np.linalg.norm(b)
+    v1 = b / beta
+    x1 = O.precondition(H, 1, v1)
+    w = lv.apply_A(x1)
+    w = w - np.vdot(w, v1) * v1
+    v2 = w / np.linalg.norm(w)
+    x2 = O.precondition(H, 1, v2)
+    AX = np.stack([lv.apply_A(x1).ravel(), lv.apply_A(x2).ravel()], axis=1)
+    y = np.linalg.lstsq(AX, b.ravel(), rcond=None)[0]
+    assert np.abs(u.ravel() - (y[0] * x1 + y[1] * x2).ravel()).max() <= 1e-10 * np.abs(u).max()
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_mk_solve_reaches_march(dim):
+    """Any convergent MK/FGMRES run reproduces the unique solution of Eq. (finesys)."""
+    if dim == 1:
+        P = W.custom(1, 31, 64, 0.1, 1.0, 0.5, W.Schedule((2, 2), (False, False), (1,), 4), seed=3,
+                     with_source=True)
+    else:
+        P = W.custom(2, 15, 32, 0.05, 1.0, 1.0, W.Schedule((2, 2), (True, True), (2,), 4), seed=4)
+    s = P.schedule
+    H = O.make_hierarchy(P.dim, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, s.nu, s.space, s.m_inner, s.n_cgs)
+    f = O.assemble_rhs(P.u0, P.g, P.nt, P.theta, P.dt)
+    u, info = O.fgmres(H, f, 1e-12, restart=60, maxit=400)
+    ref = O.theta_march(P.dim, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)
+    assert info.rel_residual < 1e-12
+    assert O.max_rel_error(u, ref) <= 1e-10
+
+
+# --------------------------------------------------------------------------
+# Adjoint.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_adjoint_march_solves_transpose(dim):
+    rng = np.random.default_rng(10)
+    nx, ny = (8, 1) if dim == 1 else (5, 4)
+    lv = O.build_levels(dim, nx, ny, 7, 1.0, 0.6, 0.01, (), (), "one")[0]
+    b = rng.standard_normal(lv.shape())
+    lam = O.adjoint_march(lv, b)
+    assert np.abs(O.dense_A(lv).T @ lam.ravel() - b.ravel()).max() <= 1e-12
+    # dot-product identity <A x, y> = <x, A^T y> with y = A^{-T} b
+    x = rng.standard_normal(lv.shape())
+    assert abs(np.vdot(lv.apply_A(x), lam) - np.vdot(x, b)) <= 1e-10 * abs(np.vdot(x, b))
+
+
+@pytest.mark.parametrize("dim,theta", [(1, 0.5), (2, 1.0)])
+def test_adjoint_gradients_vs_central_differences(dim, theta):
+    rng = np.random.default_rng(11)
+    if dim == 1:
+        nx, ny, nt, T = 15, 1, 16, 0.05
+        shape = (nx,)
+    else:
+        nx, ny, nt, T = 7, 6, 8, 0.05
+        shape = (ny, nx)
+    tau, dt = 0.8, T / nt
+    u0 = rng.standard_normal(shape)
+    g = rng.standard_normal((nt + 1,) + shape)
+    tgt = rng.standard_normal(shape)
+    J, gu0, gg, gtau, _ = O.misfit_gradients(dim, nx, ny, nt, tau, theta, dt, u0, g, tgt)
+    eps = 1e-6
+    fwd = lambda u0_, g_, tau_: O.misfit_value(dim, nx, ny, nt, tau_, theta, dt, u0_, g_, tgt)
+    d = rng.standard_normal(shape)
+    fd = (fwd(u0 + eps * d, g, tau) - fwd(u0 - eps * d, g, tau)) / (2 * eps)
+    assert abs(fd - np.sum(gu0 * d)) <= 1e-6 * max(1.0, abs(fd))
+    dg = rng.standard_normal(g.shape)
+    fd = (fwd(u0, g + eps * dg, tau) - fwd(u0, g - eps * dg, tau)) / (2 * eps)
+    assert abs(fd - np.sum(gg * dg)) <= 1e-6 * max(1.0, abs(fd))
+    fd = (fwd(u0, g, tau + eps) - fwd(u0, g, tau - eps)) / (2 * eps)
+    assert abs(fd - gtau) <= 1e-6 * max(1.0, abs(fd))
