@@ -1,0 +1,243 @@
+/*
+ * mk.h -- C ABI of libmk: the all-at-once space-time solve of the theta-scheme
+ * system by FGMRES preconditioned with the multilevel Krylov (MK) cycle
+ * (Erlangga, "Parallel-in-time Multilevel Krylov Methods: A Prototype").
+ *
+ * Problem (Sec. 1, Eq. (dae), Eq. (thetascheme); Sec. 3.3 model problem):
+ *   u' = A_n u + g on (0,T], A_n = tau * (2nd-order FD Laplacian) on the unit
+ *   interval (dim 1) or unit square (dim 2), n interior points per direction,
+ *   h = 1/(n+1), zero Dirichlet boundaries.  theta-scheme with step dt:
+ *     psi u_k = phi u_{k-1} + dt gbar_k,  psi = I - theta dt A_n,
+ *     phi = I + (1-theta) dt A_n,  gbar_k = (1-theta) g_{k-1} + theta g_k.
+ * All-at-once system (Sec. 2, Eq. (finesys)): A_h u_h = f_h, block lower
+ *   bidiagonal (I, psi, ..., psi on the diagonal, -phi below), f_0 = u_0,
+ *   f_k = dt gbar_k.
+ *
+ * Array layout at this boundary: dense, row-major, time-major FP64:
+ *   1D: x[k][i], shape (n_t+1, nx);  2D: x[k][j][i], shape (n_t+1, ny, nx).
+ * A spatial vector (u_0, gradients w.r.t. u_0) has shape (nx) / (ny, nx).
+ *
+ * Pointers: every array argument may point to device memory (current device)
+ * or to host memory (pageable or pinned); the library detects which with
+ * cudaPointerGetAttributes and stages host arrays through its own device
+ * buffers.  The caller owns every array it passes; the library never keeps a
+ * caller pointer after a call returns.  The library owns its workspace, created
+ * by mk_create_problem / on the first solve with given options, and freed by
+ * mk_destroy.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ * are stream-ordered.  When any output is in host memory, or `info` is
+ * non-NULL, the call synchronises the stream before returning.
+ *
+ * Errors: every entry point returns an mk_status; nothing is thrown across the
+ * ABI.  On error, outputs are unspecified unless stated otherwise.
+ *
+ * Thread safety: one problem must not be used by two host threads at once.
+ */
+#ifndef MK_H
+#define MK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mk_status {
+    MK_OK = 0,
+    MK_ERR_INVALID = 1,        /* bad argument: sizes, theta not in [0,1], dt <= 0, NULL pointer,
+                                  n_t not divisible by the coarsening, unsupported option */
+    MK_ERR_NOMEM = 2,          /* device allocation failed */
+    MK_ERR_CUDA = 3,           /* a CUDA runtime call failed (see mk_last_cuda_error) */
+    MK_ERR_NONFINITE = 4,      /* NaN/Inf in an input or in the iteration */
+    MK_ERR_NOT_CONVERGED = 5,  /* max_iters reached: u_out holds the last iterate, info the residual */
+    MK_ERR_TIMEOUT = 6         /* a bounded device-side wait expired */
+} mk_status;
+
+/* Spatial operator A_n (Sec. 3.3): tau * second-order FD Laplacian, zero Dirichlet,
+   nx (and ny) interior points, h = 1/(n+1) per direction. */
+typedef struct mk_stencil {
+    int32_t dim;   /* 1 or 2 */
+    int32_t nx;    /* >= 1 */
+    int32_t ny;    /* >= 1 in 2D, ignored (taken as 1) in 1D */
+    double tau;    /* > 0 */
+} mk_stencil;
+
+#define MK_MAX_LEVELS 12
+
+/* Options of one MK solve.  Fill with mk_default_opts, then override. */
+typedef struct mk_solve_opts {
+    double tol;          /* stop when ||f - A u||_2 / ||f||_2 < tol (Sec. 3.3.1 criterion); default 1e-12 */
+    int32_t restart;     /* FGMRES(m) restart length on level 1; default 40 */
+    int32_t max_iters;   /* total outer iterations; default 2000 */
+    int32_t levels;      /* L >= 2: level 1 (fine) .. level L (coarsest, decoupled); default 3 */
+    int32_t nu[MK_MAX_LEVELS];      /* time coarsening factor from level l to l+1 (entries 0..L-2); default 2 */
+    int32_t space[MK_MAX_LEVELS];   /* 1: agglomerate space (pairs / 2x2) on that coarsening (Case 2, TS) */
+    int32_t m_inner[MK_MAX_LEVELS]; /* fixed FGMRES iterations on level l+2 (entries 0..L-3); default 2,
+                                       and 1 on the level just above the coarsest (Sec. 4.2) */
+    int32_t n_cgs;       /* decoupled slabs on the coarsest level (Sec. 3.3.2); 0 = exact coupled
+                            coarse solve (sequential); default 16 */
+    int32_t mu_mode;     /* 0: mu_l = lambda_max(A_l) (Sec. 3.1); 1: mu = 1; 2: mu = mu_value */
+    double mu_value;
+    int32_t precision;   /* 0: FP64 throughout.  1: mixed -- MK cycle, transfers, inner levels and
+                            coarsest slabs in FP32; level-1 residual, Arnoldi, least squares and the
+                            true-residual check in FP64. */
+    int32_t use_graph;   /* 1: capture each restart cycle in a CUDA graph (default 1) */
+} mk_solve_opts;
+
+typedef struct mk_solve_info {
+    int32_t iterations;      /* outer FGMRES iterations */
+    int32_t restarts;        /* completed restart cycles */
+    double rel_residual;     /* final true ||f - A u|| / ||f|| (FP64) */
+    double f_norm;           /* ||f||_2 */
+    double solve_ms;         /* device time of the solve (CUDA events on `stream`) */
+    int32_t kernel_launches; /* kernels launched by the solve */
+    int32_t levels;          /* levels actually built */
+} mk_solve_info;
+
+typedef struct mk_problem mk_problem;
+
+/* Defaults listed above. */
+void mk_default_opts(mk_solve_opts *opts);
+
+/* Human-readable status name. */
+const char *mk_status_string(mk_status s);
+
+/* Last CUDA error string seen by the library on this thread ("" if none). */
+const char *mk_last_cuda_error(void);
+
+/* Number of library kernels launched since the library was loaded (all threads). */
+int64_t mk_kernel_launch_count(void);
+
+/*
+ * mk_create_problem -- set up A_h (Eq. (finesys)) for the theta-scheme with step dt over
+ * nt steps, and the source part of f_h: f_k = dt((1-theta) g_{k-1} + theta g_k), k >= 1.
+ *   A_n   : spatial operator (host struct).
+ *   theta : in [0,1].   dt : > 0.   nt : >= 1.
+ *   g     : (nt+1) x n source samples g_k = g(k dt), host or device, or NULL for g = 0.
+ *           Copied; not retained.
+ *   out   : receives the new problem (host pointer).
+ * Errors: MK_ERR_INVALID, MK_ERR_NOMEM, MK_ERR_CUDA.
+ */
+mk_status mk_create_problem(const mk_stencil *A_n, double theta, double dt, int32_t nt,
+                            const double *g, mk_problem **out);
+
+/* Replace the source g of an existing problem ((nt+1) x n samples, host or device, or
+   NULL for g = 0): recomputes f_k, k >= 1.  Copied; not retained. */
+mk_status mk_set_source(mk_problem *p, const double *g, void *stream);
+
+/* Frees the problem and all its workspace.  NULL is ignored. */
+void mk_destroy(mk_problem *p);
+
+/*
+ * mk_solve -- solve A_h u = f_h (f_0 = u0) by FGMRES (Algorithm 2) right-preconditioned by
+ * the MK cycle Q (Eq. (Qh), substeps 4.1-4.5, recursion of Sec. 4.1, decoupled coarsest
+ * level Eq. (Qhtilde)).  Initial guess u^0 = 0.
+ *   u0    : n initial values.   opts: NULL = defaults.
+ *   u_out : (nt+1) x n solution, caller-allocated.
+ *   info  : host struct or NULL.
+ * Errors: MK_ERR_INVALID (options incompatible with nt/n), MK_ERR_NONFINITE,
+ *         MK_ERR_NOT_CONVERGED (u_out holds the last iterate), MK_ERR_NOMEM, MK_ERR_CUDA.
+ */
+mk_status mk_solve(mk_problem *p, const double *u0, const mk_solve_opts *opts,
+                   double *u_out, mk_solve_info *info, void *stream);
+
+/*
+ * mk_solve_rhs -- same solver for an arbitrary right-hand side f ((nt+1) x n), u^0 = 0.
+ * mk_solve(p, u0, ...) equals mk_solve_rhs with f_0 = u0 and the problem's source blocks.
+ */
+mk_status mk_solve_rhs(mk_problem *p, const double *f, const mk_solve_opts *opts,
+                       double *u_out, mk_solve_info *info, void *stream);
+
+/*
+ * mk_march -- sequential theta-march on the GPU, Eq. (timemarch): block forward
+ * substitution of A_h u = f_h, FP64, one step after another (the baseline the MK
+ * solve is compared with).  u_out: (nt+1) x n.
+ */
+mk_status mk_march(mk_problem *p, const double *u0, double *u_out, void *stream);
+
+/*
+ * mk_adjoint -- discrete adjoint of Eq. (finesys) for a loss J(u).
+ * Solves A_h^T lam = dJ/du with the same MK solver run on the time-reversed system
+ * (A_h^T is block upper bidiagonal; reversing time gives the forward structure, psi and
+ * phi being symmetric), then forms
+ *   dJ/du0   = lam_0 = b_0 + phi lam_1,
+ *   dJ/dg_k  = dt (theta lam_k + (1-theta) lam_{k+1})   (lam_{nt+1} = 0; no lam_0 term),
+ *   dJ/dtau  = sum_{k>=1} dt lam_k^T Lhat (theta u_k + (1-theta) u_{k-1}),  Lhat = A_n / tau.
+ *   u      : (nt+1) x n forward solution, or NULL when grad_tau is NULL.
+ *   dJdu   : (nt+1) x n.
+ *   grad_u0: n, or NULL.  grad_g: (nt+1) x n, or NULL.  grad_tau: one double, or NULL.
+ *   lam_out: (nt+1) x n adjoint state, or NULL.
+ */
+mk_status mk_adjoint(mk_problem *p, const double *u, const double *dJdu,
+                     const mk_solve_opts *opts, double *grad_u0, double *grad_g,
+                     double *grad_tau, double *lam_out, mk_solve_info *info, void *stream);
+
+/* Problem geometry (host ints / doubles). */
+mk_status mk_problem_shape(const mk_problem *p, int32_t *dim, int32_t *nx, int32_t *ny, int32_t *nt,
+                           double *theta, double *dt, double *tau);
+
+/* ------------------------------------------------------------------------------------
+ * Operator-level entry points.  Each runs one step of the hot path on dense FP64 arrays
+ * of the given level so that it can be checked on its own.  `level` is 1-based
+ * (1 = fine).  `precision` 0 computes in FP64, 1 in FP32 (inputs rounded to FP32 first,
+ * as in the mixed cycle; outputs widened back to FP64).  The hierarchy is the one `opts`
+ * describes (NULL = defaults).
+ * ------------------------------------------------------------------------------------ */
+
+typedef struct mk_level_desc {
+    int32_t dim, nx, ny, nt;   /* spatial sizes and time steps on this level */
+    double a, b;               /* (A x)_k = (I - aL) x_k - (I + bL) x_{k-1} */
+    double mu;                 /* shift used when restricting from this level */
+} mk_level_desc;
+
+/* Level geometry and weights (Galerkin coarse operator of Eqs. (timecoarse1)-(timecoarse3)):
+   a_{l+1} = nu a_l + (nu-1) b_l, b_{l+1} = b_l, nt_{l+1} = nt_l / nu.
+   If xcoef/ycoef are non-NULL they receive the spatial operator L_l = Y^T L_{l-1} Z as
+   3 x nx (resp. 3 x ny) host doubles: rows lo, di, up. */
+mk_status mk_level_info(mk_problem *p, const mk_solve_opts *opts, int32_t level,
+                        mk_level_desc *desc, double *xcoef, double *ycoef);
+
+/* f = f_h for initial state u0 (RHS assembly of Eq. (finesys)).  f: (nt+1) x n. */
+mk_status mk_op_rhs(mk_problem *p, const double *u0, double *f, void *stream);
+
+/* w = A_l x  (space-time stencil matvec). */
+mk_status mk_op_apply(mk_problem *p, const mk_solve_opts *opts, int32_t level, int32_t precision,
+                      const double *x, double *w, void *stream);
+
+/* r = f - A_1 u and ||r||_2 (host double, may be NULL). */
+mk_status mk_op_residual(mk_problem *p, const double *f, const double *u, double *r,
+                         double *rnorm, void *stream);
+
+/* vhat = Y^T (A_l v - mu_l v)  (substeps 4.1-4.2), level l -> l+1. */
+mk_status mk_op_restrict(mk_problem *p, const mk_solve_opts *opts, int32_t level, int32_t precision,
+                         const double *v, double *vhat, void *stream);
+
+/* x = v - Z vt and w = A_l x  (substeps 4.4-4.5 fused with step 5), vt on level l+1. */
+mk_status mk_op_interp_correct(mk_problem *p, const mk_solve_opts *opts, int32_t level,
+                               int32_t precision, const double *v, const double *vt,
+                               double *x, double *w, void *stream);
+
+/* x = Atilde_L^{-1} r on the coarsest level (decoupled slabs, Eq. (Qhtilde)). */
+mk_status mk_op_coarsest(mk_problem *p, const mk_solve_opts *opts, int32_t precision,
+                         const double *r, double *x, void *stream);
+
+/* x = Q_l v: one full MK cycle from level l (inner FGMRES on intermediate levels). */
+mk_status mk_op_precond(mk_problem *p, const mk_solve_opts *opts, int32_t level,
+                        const double *v, double *x, void *stream);
+
+/* One Arnoldi orthogonalisation (classical Gram-Schmidt, twice) of w against the j
+   columns of V (j x N, orthonormal), N = (nt+1) n on level 1:
+   h[0..j-1] = coefficients, h[j] = ||w'||, w <- w' / h[j].  h: host, j+1 doubles. */
+mk_status mk_op_orthogonalize(mk_problem *p, int32_t j, const double *V, double *w,
+                              double *h, void *stream);
+
+/* Least squares y = argmin || beta e_1 - H y ||, H (j+1) x j column-major (host),
+   solved on the device by Givens rotations.  y: host, j doubles; res: |g_{j+1}|. */
+mk_status mk_op_lsq(int32_t j, const double *H, double beta, double *y, double *res, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MK_H */

@@ -1,0 +1,283 @@
+"""Python binding of libmk: the all-at-once space-time theta-scheme solve by FGMRES with the
+multilevel Krylov (MK) preconditioner (Erlangga, parallel-in-time MK), on one GB300.
+
+This module only marshals arguments to the C ABI (include/mk.h); every step of the solve runs
+in the library's CUDA kernels.  Arrays are torch tensors (CUDA or CPU) or numpy arrays, FP64,
+C-contiguous: space-time arrays (n_t+1, nx) / (n_t+1, ny, nx), spatial ones (nx) / (ny, nx).
+Functions carry the ABI's names; ``Problem`` and ``HeatSolve`` are conveniences on top.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import (MK_MAX_LEVELS, MKError, mk_level_desc, mk_solve_info, mk_solve_opts,
+                   mk_stencil)
+
+__all__ = ["mk_default_opts", "mk_create_problem", "mk_set_source", "mk_destroy", "mk_solve",
+           "mk_solve_rhs", "mk_march", "mk_adjoint", "mk_level_info", "mk_op_rhs", "mk_op_apply",
+           "mk_op_residual", "mk_op_restrict", "mk_op_interp_correct", "mk_op_coarsest",
+           "mk_op_precond", "mk_op_orthogonalize", "mk_op_lsq", "mk_kernel_launch_count",
+           "make_opts", "Problem", "HeatSolve", "MKError", "lib"]
+
+
+def lib():
+    return _lib.load()
+
+
+def _ptr(a) -> Optional[int]:
+    """Raw pointer of a float64 C-contiguous torch tensor / numpy array (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("arrays must be float64 and C-contiguous")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be float64 and contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def _current_stream_for(*arrays):
+    try:
+        import torch
+    except ImportError:
+        return None
+    for a in arrays:
+        if isinstance(a, torch.Tensor) and a.is_cuda:
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+def mk_default_opts() -> mk_solve_opts:
+    o = mk_solve_opts()
+    lib().mk_default_opts(ctypes.byref(o))
+    return o
+
+
+def make_opts(levels: int = 3, nu: Sequence[int] = (), space: Sequence[bool] = (),
+              m_inner: Sequence[int] = (), n_cgs: int = 16, tol: float = 1e-12, restart: int = 40,
+              max_iters: int = 2000, precision: str = "fp64", mu: str | float = "lambda_max",
+              use_graph: bool = True) -> mk_solve_opts:
+    """Options struct from Python values (unset per-level entries keep the defaults)."""
+    o = mk_default_opts()
+    o.levels = levels
+    for i, v in enumerate(nu):
+        o.nu[i] = int(v)
+    for i, v in enumerate(space):
+        o.space[i] = 1 if v else 0
+    for i, v in enumerate(m_inner):
+        o.m_inner[i] = int(v)
+    o.n_cgs = n_cgs
+    o.tol = tol
+    o.restart = restart
+    o.max_iters = max_iters
+    o.precision = {"fp64": 0, "mixed": 1}[precision]
+    if mu == "lambda_max":
+        o.mu_mode = 0
+    elif mu == "one":
+        o.mu_mode = 1
+    else:
+        o.mu_mode, o.mu_value = 2, float(mu)
+    o.use_graph = 1 if use_graph else 0
+    return o
+
+
+def mk_kernel_launch_count() -> int:
+    return int(lib().mk_kernel_launch_count())
+
+
+def mk_create_problem(dim: int, nx: int, ny: int, tau: float, theta: float, dt: float, nt: int,
+                      g=None) -> int:
+    st = mk_stencil(dim, nx, ny if dim == 2 else 1, tau)
+    out = ctypes.c_void_p()
+    _lib.check(lib().mk_create_problem(ctypes.byref(st), theta, dt, nt, _ptr(g), ctypes.byref(out)),
+               "mk_create_problem")
+    return out.value
+
+
+def mk_set_source(p: int, g, stream=None) -> None:
+    _lib.check(lib().mk_set_source(p, _ptr(g), _stream(stream) or _current_stream_for(g)),
+               "mk_set_source")
+
+
+def mk_destroy(p: int) -> None:
+    lib().mk_destroy(p)
+
+
+def mk_solve(p: int, u0, u_out, opts: Optional[mk_solve_opts] = None, stream=None,
+             allow_not_converged: bool = False) -> mk_solve_info:
+    info = mk_solve_info()
+    s = _stream(stream) or _current_stream_for(u0, u_out)
+    code = lib().mk_solve(p, _ptr(u0), ctypes.byref(opts) if opts else None, _ptr(u_out),
+                          ctypes.byref(info), s)
+    _lib.check(code, "mk_solve", allow=(_lib.MK_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return info
+
+
+def mk_solve_rhs(p: int, f, u_out, opts: Optional[mk_solve_opts] = None, stream=None) -> mk_solve_info:
+    info = mk_solve_info()
+    s = _stream(stream) or _current_stream_for(f, u_out)
+    _lib.check(lib().mk_solve_rhs(p, _ptr(f), ctypes.byref(opts) if opts else None, _ptr(u_out),
+                                  ctypes.byref(info), s), "mk_solve_rhs")
+    return info
+
+
+def mk_march(p: int, u0, u_out, stream=None) -> None:
+    s = _stream(stream) or _current_stream_for(u0, u_out)
+    _lib.check(lib().mk_march(p, _ptr(u0), _ptr(u_out), s), "mk_march")
+
+
+def mk_adjoint(p: int, u, dJdu, opts: Optional[mk_solve_opts] = None, grad_u0=None, grad_g=None,
+               want_tau: bool = False, lam=None, stream=None):
+    """Returns (dJ/dtau or None, solve info); other gradients are written in place."""
+    info = mk_solve_info()
+    gt = ctypes.c_double(0.0)
+    s = _stream(stream) or _current_stream_for(u, dJdu)
+    _lib.check(lib().mk_adjoint(p, _ptr(u), _ptr(dJdu), ctypes.byref(opts) if opts else None,
+                                _ptr(grad_u0), _ptr(grad_g),
+                                ctypes.addressof(gt) if want_tau else None, _ptr(lam),
+                                ctypes.byref(info), s), "mk_adjoint")
+    return (gt.value if want_tau else None), info
+
+
+def mk_level_info(p: int, opts: Optional[mk_solve_opts], level: int):
+    d = mk_level_desc()
+    # sizes first, then coefficients
+    _lib.check(lib().mk_level_info(p, ctypes.byref(opts) if opts else None, level, ctypes.byref(d),
+                                   None, None), "mk_level_info")
+    xc = np.zeros(3 * d.nx)
+    yc = np.zeros(3 * d.ny) if d.dim == 2 else None
+    _lib.check(lib().mk_level_info(p, ctypes.byref(opts) if opts else None, level, None, _ptr(xc),
+                                   _ptr(yc)), "mk_level_info")
+    return d, xc.reshape(3, d.nx), (yc.reshape(3, d.ny) if yc is not None else None)
+
+
+def mk_op_rhs(p: int, u0, f, stream=None) -> None:
+    _lib.check(lib().mk_op_rhs(p, _ptr(u0), _ptr(f), _stream(stream)), "mk_op_rhs")
+
+
+def mk_op_apply(p: int, opts, level: int, precision: int, x, w, stream=None) -> None:
+    _lib.check(lib().mk_op_apply(p, ctypes.byref(opts) if opts else None, level, precision, _ptr(x),
+                                 _ptr(w), _stream(stream)), "mk_op_apply")
+
+
+def mk_op_residual(p: int, f, u, r, stream=None) -> float:
+    nrm = ctypes.c_double(0.0)
+    _lib.check(lib().mk_op_residual(p, _ptr(f), _ptr(u), _ptr(r), ctypes.byref(nrm), _stream(stream)),
+               "mk_op_residual")
+    return nrm.value
+
+
+def mk_op_restrict(p: int, opts, level: int, precision: int, v, vhat, stream=None) -> None:
+    _lib.check(lib().mk_op_restrict(p, ctypes.byref(opts) if opts else None, level, precision, _ptr(v),
+                                    _ptr(vhat), _stream(stream)), "mk_op_restrict")
+
+
+def mk_op_interp_correct(p: int, opts, level: int, precision: int, v, vt, x, w, stream=None) -> None:
+    _lib.check(lib().mk_op_interp_correct(p, ctypes.byref(opts) if opts else None, level, precision,
+                                          _ptr(v), _ptr(vt), _ptr(x), _ptr(w), _stream(stream)),
+               "mk_op_interp_correct")
+
+
+def mk_op_coarsest(p: int, opts, precision: int, r, x, stream=None) -> None:
+    _lib.check(lib().mk_op_coarsest(p, ctypes.byref(opts) if opts else None, precision, _ptr(r), _ptr(x),
+                                    _stream(stream)), "mk_op_coarsest")
+
+
+def mk_op_precond(p: int, opts, level: int, v, x, stream=None) -> None:
+    _lib.check(lib().mk_op_precond(p, ctypes.byref(opts) if opts else None, level, _ptr(v), _ptr(x),
+                                   _stream(stream)), "mk_op_precond")
+
+
+def mk_op_orthogonalize(p: int, j: int, V, w, h, stream=None) -> None:
+    _lib.check(lib().mk_op_orthogonalize(p, j, _ptr(V), _ptr(w), _ptr(h), _stream(stream)),
+               "mk_op_orthogonalize")
+
+
+def mk_op_lsq(j: int, H, beta: float, y, stream=None) -> float:
+    res = ctypes.c_double(0.0)
+    _lib.check(lib().mk_op_lsq(j, _ptr(H), beta, _ptr(y), ctypes.byref(res), _stream(stream)),
+               "mk_op_lsq")
+    return res.value
+
+
+class Problem:
+    """Owning handle of an mk_problem."""
+
+    def __init__(self, dim: int, nx: int, tau: float, theta: float, dt: float, nt: int, g=None,
+                 ny: int = 1):
+        self.dim, self.nx, self.ny, self.nt = dim, nx, (ny if dim == 2 else 1), nt
+        self.tau, self.theta, self.dt = tau, theta, dt
+        self.handle = mk_create_problem(dim, nx, self.ny, tau, theta, dt, nt, g)
+
+    @property
+    def space_shape(self):
+        return (self.nx,) if self.dim == 1 else (self.ny, self.nx)
+
+    @property
+    def shape(self):
+        return (self.nt + 1,) + self.space_shape
+
+    def close(self):
+        if self.handle:
+            mk_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class HeatSolve:
+    """torch.autograd.Function factory: u = A_h^{-1} f_h(u0, g) with the MK solver forward and
+    the adjoint MK solve backward (gradients w.r.t. u0, g and tau)."""
+
+    @staticmethod
+    def apply(problem: Problem, u0, g, tau_tensor, opts: Optional[mk_solve_opts] = None):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, u0_, g_, tau_):
+                if abs(float(tau_) - problem.tau) > 0.0:
+                    raise ValueError("tau differs from the problem's tau; create a new Problem")
+                if g_ is not None:
+                    mk_set_source(problem.handle, g_.contiguous())
+                u = torch.empty(problem.shape, dtype=torch.float64, device=u0_.device)
+                mk_solve(problem.handle, u0_.contiguous(), u, opts)
+                ctx.save_for_backward(u)
+                return u
+
+            @staticmethod
+            def backward(ctx, gu):
+                (u,) = ctx.saved_tensors
+                gu0 = torch.empty(problem.space_shape, dtype=torch.float64, device=u.device)
+                gg = torch.empty(problem.shape, dtype=torch.float64, device=u.device)
+                gtau, _ = mk_adjoint(problem.handle, u, gu.contiguous(), opts, grad_u0=gu0, grad_g=gg,
+                                     want_tau=True)
+                return gu0, gg, torch.tensor(gtau, dtype=torch.float64, device=tau_tensor.device)
+
+        return _Fn.apply(u0, g, tau_tensor)

@@ -1,0 +1,810 @@
+// C ABI of libmk (see include/mk.h): argument checks, host/device pointer staging, and
+// the operator-level entry points used to check each step of the path on its own.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "solver.h"
+
+namespace mk {
+
+int g_num_sms = 0;
+static std::atomic<int64_t> g_launches{0};
+static thread_local std::string g_last_err;
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void set_cuda_error(cudaError_t e) { g_last_err = cudaGetErrorString(e); }
+
+cudaError_t slab_set_attributes();
+
+// adjoint helpers (stencil.cu)
+void launch_reverse_pack(const Geom &g, const double *dense, double *padded, cudaStream_t s);
+void launch_adjoint_grads(const Geom &g, double theta, double dt, double tau, SpaceOp<double> L,
+                          const double *y, const double *b, const double *upad, double *lam,
+                          double *grad_u0, double *grad_g, const ReduceScratch &rs, KState ks,
+                          cudaStream_t s);
+
+}  // namespace mk
+
+using namespace mk;
+
+struct mk_problem {
+    Problem P;
+};
+
+#define CK(call)                                                                 \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) {                                                 \
+            set_cuda_error(e_);                                                  \
+            return e_ == cudaErrorMemoryAllocation ? MK_ERR_NOMEM : MK_ERR_CUDA; \
+        }                                                                        \
+    } while (0)
+
+#define CKS(expr)                       \
+    do {                                \
+        mk_status s_ = (expr);          \
+        if (s_ != MK_OK) return s_;     \
+    } while (0)
+
+static mk_status ensure_device() {
+    if (g_num_sms > 0) return MK_OK;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(slab_set_attributes());
+    g_num_sms = sms > 0 ? sms : 1;
+    return MK_OK;
+}
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Input array: device pointer as is, host array copied into tmp.
+static mk_status stage_in(const double *p, size_t n, DevMem &tmp, const double *&dp, cudaStream_t s) {
+    if (is_device_ptr(p)) {
+        dp = p;
+        return MK_OK;
+    }
+    CK(tmp.alloc(sizeof(double) * (n ? n : 1)));
+    CK(cudaMemcpyAsync(tmp.p, p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    dp = tmp.as<double>();
+    return MK_OK;
+}
+
+// Output array: device pointer as is, host array gets a device staging buffer.
+struct OutStage {
+    double *user = nullptr;
+    double *dev = nullptr;
+    size_t n = 0;
+    bool host = false;
+    DevMem tmp;
+};
+static mk_status stage_out(double *p, size_t n, OutStage &o) {
+    o.user = p;
+    o.n = n;
+    if (is_device_ptr(p)) {
+        o.dev = p;
+        return MK_OK;
+    }
+    o.host = true;
+    CK(o.tmp.alloc(sizeof(double) * (n ? n : 1)));
+    o.dev = o.tmp.as<double>();
+    return MK_OK;
+}
+static mk_status finish_out(OutStage &o, cudaStream_t s) {
+    if (!o.host) return MK_OK;
+    CK(cudaMemcpyAsync(o.user, o.dev, sizeof(double) * o.n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MK_OK;
+}
+
+static size_t space_n(const Problem &P) { return (size_t)P.nx * (P.dim == 2 ? P.ny : 1); }
+static size_t st_n(const Problem &P) { return space_n(P) * (size_t)(P.nt + 1); }
+
+static mk_solve_opts resolve_opts(const mk_solve_opts *o) {
+    mk_solve_opts r;
+    if (o) r = *o;
+    else mk_default_opts(&r);
+    return r;
+}
+
+extern "C" {
+
+void mk_default_opts(mk_solve_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-12;
+    o->restart = 40;
+    o->max_iters = 2000;
+    o->levels = 3;
+    for (int i = 0; i < MK_MAX_LEVELS; ++i) {
+        o->nu[i] = 2;
+        o->space[i] = 0;
+        o->m_inner[i] = 2;
+    }
+    o->m_inner[0] = 1;   // with 3 levels the only intermediate level sits above the coarsest
+    o->n_cgs = 16;
+    o->mu_mode = 0;
+    o->mu_value = 1.0;
+    o->precision = 0;
+    o->use_graph = 1;
+}
+
+const char *mk_status_string(mk_status s) {
+    switch (s) {
+        case MK_OK: return "MK_OK";
+        case MK_ERR_INVALID: return "MK_ERR_INVALID";
+        case MK_ERR_NOMEM: return "MK_ERR_NOMEM";
+        case MK_ERR_CUDA: return "MK_ERR_CUDA";
+        case MK_ERR_NONFINITE: return "MK_ERR_NONFINITE";
+        case MK_ERR_NOT_CONVERGED: return "MK_ERR_NOT_CONVERGED";
+        case MK_ERR_TIMEOUT: return "MK_ERR_TIMEOUT";
+    }
+    return "MK_ERR_UNKNOWN";
+}
+
+const char *mk_last_cuda_error(void) { return g_last_err.c_str(); }
+
+int64_t mk_kernel_launch_count(void) { return g_launches.load(); }
+
+mk_status mk_problem_shape(const mk_problem *p, int32_t *dim, int32_t *nx, int32_t *ny,
+                           int32_t *nt, double *theta, double *dt, double *tau) {
+    if (!p) return MK_ERR_INVALID;
+    if (dim) *dim = p->P.dim;
+    if (nx) *nx = p->P.nx;
+    if (ny) *ny = p->P.ny;
+    if (nt) *nt = p->P.nt;
+    if (theta) *theta = p->P.theta;
+    if (dt) *dt = p->P.dt;
+    if (tau) *tau = p->P.tau;
+    return MK_OK;
+}
+
+mk_status mk_set_source(mk_problem *p, const double *g, void *stream) {
+    if (!p) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Problem &P = p->P;
+    CK(cudaMemsetAsync(P.fsrc.p, 0, sizeof(double) * P.g.len, s));
+    P.has_source = g != nullptr;
+    if (!g) return MK_OK;
+    DevMem tmp;
+    const double *dg = nullptr;
+    CKS(stage_in(g, st_n(P), tmp, dg, s));
+    launch_rhs_source(P.g, P.theta, P.dt, dg, P.fsrc.as<double>(), s);
+    CK(cudaGetLastError());
+    if (tmp.p) CK(cudaStreamSynchronize(s));
+    return MK_OK;
+}
+
+mk_status mk_create_problem(const mk_stencil *A, double theta, double dt, int32_t nt,
+                            const double *g, mk_problem **out) {
+    if (!A || !out) return MK_ERR_INVALID;
+    *out = nullptr;
+    if (A->dim != 1 && A->dim != 2) return MK_ERR_INVALID;
+    if (A->nx < 1 || (A->dim == 2 && A->ny < 1)) return MK_ERR_INVALID;
+    if (!(theta >= 0.0 && theta <= 1.0) || !(dt > 0.0) || nt < 1 || !(A->tau > 0.0))
+        return MK_ERR_INVALID;
+    if (!std::isfinite(dt) || !std::isfinite(A->tau)) return MK_ERR_INVALID;
+    CKS(ensure_device());
+    std::unique_ptr<mk_problem> p(new mk_problem());
+    Problem &P = p->P;
+    P.dim = A->dim;
+    P.nx = A->nx;
+    P.ny = A->dim == 2 ? A->ny : 1;
+    P.nt = nt;
+    P.theta = theta;
+    P.dt = dt;
+    P.tau = A->tau;
+    P.g = make_geom(P.dim, P.nx, P.ny, nt);
+    CK(P.fsrc.alloc(sizeof(double) * P.g.len));
+    CKS(mk_set_source(p.get(), g, nullptr));
+    CK(cudaStreamSynchronize(nullptr));
+    *out = p.release();
+    return MK_OK;
+}
+
+void mk_destroy(mk_problem *p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    delete p;
+}
+
+// pack a dense (nt+1) x n array into the padded fine-level layout
+static void pack_fine(const Problem &P, const double *dense, double *padded, cudaStream_t s) {
+    launch_pack<double, double>(P.g, dense, padded, s);
+}
+
+static mk_status solve_common(mk_problem *p, const mk_solve_opts &o, mk_solve_info *info,
+                              cudaStream_t s, Hierarchy *H, double *u_out_dev) {
+    Problem &P = p->P;
+    int64_t before = mk_kernel_launch_count();
+    mk_status st = run_solve(P, *H, o, nullptr, info, s);
+    if (st != MK_OK && st != MK_ERR_NOT_CONVERGED) return st;
+    launch_unpack<double, double>(P.g, H->u.as<double>(), u_out_dev, s);
+    CK(cudaGetLastError());
+    if (info) info->kernel_launches = (int32_t)(mk_kernel_launch_count() - before);
+    return st;
+}
+
+mk_status mk_solve(mk_problem *p, const double *u0, const mk_solve_opts *opts, double *u_out,
+                   mk_solve_info *info, void *stream) {
+    if (!p || !u0 || !u_out) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    mk_solve_opts o = resolve_opts(opts);
+    Problem &P = p->P;
+    CKS(validate_opts(P, o));
+    Hierarchy *H = nullptr;
+    CKS(build_hierarchy(P, o, H));
+    DevMem tin;
+    const double *du0 = nullptr;
+    CKS(stage_in(u0, space_n(P), tin, du0, s));
+    OutStage os;
+    CKS(stage_out(u_out, st_n(P), os));
+    // f = source blocks, f_0 = u0
+    CK(cudaMemcpyAsync(H->f.p, P.fsrc.p, sizeof(double) * P.g.len, cudaMemcpyDeviceToDevice, s));
+    Geom g0 = P.g;
+    g0.nt = 0;
+    launch_pack<double, double>(g0, du0, H->f.as<double>(), s);
+    mk_status st = solve_common(p, o, info, s, H, os.dev);
+    if (st != MK_OK && st != MK_ERR_NOT_CONVERGED) return st;
+    CKS(finish_out(os, s));
+    return st;
+}
+
+mk_status mk_solve_rhs(mk_problem *p, const double *f, const mk_solve_opts *opts, double *u_out,
+                       mk_solve_info *info, void *stream) {
+    if (!p || !f || !u_out) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    mk_solve_opts o = resolve_opts(opts);
+    Problem &P = p->P;
+    CKS(validate_opts(P, o));
+    Hierarchy *H = nullptr;
+    CKS(build_hierarchy(P, o, H));
+    DevMem tin;
+    const double *df = nullptr;
+    CKS(stage_in(f, st_n(P), tin, df, s));
+    OutStage os;
+    CKS(stage_out(u_out, st_n(P), os));
+    pack_fine(P, df, H->f.as<double>(), s);
+    mk_status st = solve_common(p, o, info, s, H, os.dev);
+    if (st != MK_OK && st != MK_ERR_NOT_CONVERGED) return st;
+    CKS(finish_out(os, s));
+    return st;
+}
+
+mk_status mk_march(mk_problem *p, const double *u0, double *u_out, void *stream) {
+    if (!p || !u0 || !u_out) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Problem &P = p->P;
+    CKS(prepare_march(P));
+    DevMem tin, fbuf, ubuf;
+    const double *du0 = nullptr;
+    CKS(stage_in(u0, space_n(P), tin, du0, s));
+    OutStage os;
+    CKS(stage_out(u_out, st_n(P), os));
+    CK(fbuf.alloc(sizeof(double) * P.g.len));
+    CK(ubuf.alloc(sizeof(double) * P.g.len));
+    CK(cudaMemcpyAsync(fbuf.p, P.fsrc.p, sizeof(double) * P.g.len, cudaMemcpyDeviceToDevice, s));
+    Geom g0 = P.g;
+    g0.nt = 0;
+    launch_pack<double, double>(g0, du0, fbuf.as<double>(), s);
+    SpaceOp<double> op{P.m_c64.as<double>(), P.dim == 2 ? P.m_c64.as<double>() + 3 * P.nx : nullptr};
+    const double a = P.theta * P.dt, b = (1.0 - P.theta) * P.dt;
+    if (P.dim == 1)
+        launch_march_1d(P.g, b, op, P.m_alpha.as<double>(), P.m_gamma.as<double>(),
+                        P.m_binv.as<double>(), P.m_npad, P.m_nlev, fbuf.as<double>(),
+                        ubuf.as<double>(), s);
+    else
+        launch_march_2d(P.g, a, b, op, P.m_Sx.as<double>(), P.m_Sxi.as<double>(),
+                        P.m_lamx.as<double>(), P.m_Sy.as<double>(), P.m_Syi.as<double>(),
+                        P.m_lamy.as<double>(), fbuf.as<double>(), ubuf.as<double>(), s);
+    launch_unpack<double, double>(P.g, ubuf.as<double>(), os.dev, s);
+    CK(cudaGetLastError());
+    CKS(finish_out(os, s));
+    // keep the staging buffers alive until the work that uses them is done
+    CK(cudaStreamSynchronize(s));
+    return MK_OK;
+}
+
+mk_status mk_adjoint(mk_problem *p, const double *u, const double *dJdu, const mk_solve_opts *opts,
+                     double *grad_u0, double *grad_g, double *grad_tau, double *lam_out,
+                     mk_solve_info *info, void *stream) {
+    if (!p || !dJdu) return MK_ERR_INVALID;
+    if (grad_tau && !u) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    mk_solve_opts o = resolve_opts(opts);
+    Problem &P = p->P;
+    CKS(validate_opts(P, o));
+    Hierarchy *H = nullptr;
+    CKS(build_hierarchy(P, o, H));
+    DevMem tb, tu, upad;
+    const double *db = nullptr, *du = nullptr;
+    CKS(stage_in(dJdu, st_n(P), tb, db, s));
+    if (u) {
+        CKS(stage_in(u, st_n(P), tu, du, s));
+        CK(upad.alloc(sizeof(double) * P.g.len));
+        pack_fine(P, du, upad.as<double>(), s);
+    }
+    // time-reversed transposed system: f_rev[0] = 0, f_rev[j] = b[nt+1-j]
+    launch_reverse_pack(P.g, db, H->f.as<double>(), s);
+    mk_status st = run_solve(P, *H, o, nullptr, info, s);
+    if (st != MK_OK && st != MK_ERR_NOT_CONVERGED) return st;
+    OutStage o_lam, o_gu0, o_gg;
+    DevMem d_lam, d_gu0, d_gg;
+    if (lam_out) CKS(stage_out(lam_out, st_n(P), o_lam));
+    if (grad_u0) CKS(stage_out(grad_u0, space_n(P), o_gu0));
+    if (grad_g) CKS(stage_out(grad_g, st_n(P), o_gg));
+    Level &L0 = *H->lv[0];
+    launch_adjoint_grads(P.g, P.theta, P.dt, P.tau, L0.op64, H->u.as<double>(), db,
+                         u ? upad.as<double>() : nullptr, lam_out ? o_lam.dev : nullptr,
+                         grad_u0 ? o_gu0.dev : nullptr, grad_g ? o_gg.dev : nullptr, H->rs, L0.ks,
+                         s);
+    CK(cudaGetLastError());
+    if (grad_tau) {
+        double hmisc[8];
+        CK(cudaMemcpyAsync(hmisc, L0.ks.misc(), sizeof(hmisc), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double v = hmisc[5];
+        if (is_device_ptr(grad_tau)) CK(cudaMemcpy(grad_tau, &v, sizeof(double), cudaMemcpyHostToDevice));
+        else *grad_tau = v;
+    }
+    if (lam_out) CKS(finish_out(o_lam, s));
+    if (grad_u0) CKS(finish_out(o_gu0, s));
+    if (grad_g) CKS(finish_out(o_gg, s));
+    CK(cudaStreamSynchronize(s));
+    return st;
+}
+
+// ------------------------------------------------------------------------------------
+// operator-level entry points
+// ------------------------------------------------------------------------------------
+static mk_status get_level(mk_problem *p, const mk_solve_opts *opts, int level, Hierarchy *&H,
+                           mk_solve_opts &o) {
+    if (!p) return MK_ERR_INVALID;
+    o = resolve_opts(opts);
+    CKS(validate_opts(p->P, o));
+    CKS(build_hierarchy(p->P, o, H));
+    if (level < 1 || level > (int)H->lv.size()) return MK_ERR_INVALID;
+    return MK_OK;
+}
+
+mk_status mk_level_info(mk_problem *p, const mk_solve_opts *opts, int32_t level,
+                        mk_level_desc *d, double *xcoef, double *ycoef) {
+    Hierarchy *H = nullptr;
+    mk_solve_opts o;
+    CKS(get_level(p, opts, level, H, o));
+    Level &L = *H->lv[level - 1];
+    if (d) {
+        d->dim = L.g.dim;
+        d->nx = L.g.nx;
+        d->ny = L.g.ny;
+        d->nt = L.g.nt;
+        d->a = L.w.a;
+        d->b = L.w.b;
+        d->mu = L.w.mu;
+    }
+    auto put = [](const Tri &t, double *c) {
+        int n = t.n();
+        for (int i = 0; i < n; ++i) {
+            c[i] = t.lo[i];
+            c[n + i] = t.di[i];
+            c[2 * n + i] = t.up[i];
+        }
+    };
+    if (xcoef) put(L.Lx, xcoef);
+    if (ycoef && L.g.dim == 2) put(L.Ly, ycoef);
+    return MK_OK;
+}
+
+mk_status mk_op_rhs(mk_problem *p, const double *u0, double *f, void *stream) {
+    if (!p || !u0 || !f) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Problem &P = p->P;
+    DevMem tin, fp;
+    const double *du0 = nullptr;
+    CKS(stage_in(u0, space_n(P), tin, du0, s));
+    OutStage os;
+    CKS(stage_out(f, st_n(P), os));
+    CK(fp.alloc(sizeof(double) * P.g.len));
+    CK(cudaMemcpyAsync(fp.p, P.fsrc.p, sizeof(double) * P.g.len, cudaMemcpyDeviceToDevice, s));
+    Geom g0 = P.g;
+    g0.nt = 0;
+    launch_pack<double, double>(g0, du0, fp.as<double>(), s);
+    launch_unpack<double, double>(P.g, fp.as<double>(), os.dev, s);
+    CK(cudaGetLastError());
+    CKS(finish_out(os, s));
+    CK(cudaStreamSynchronize(s));
+    return MK_OK;
+}
+
+}  // extern "C"
+
+template <typename T>
+static mk_status op_apply_t(Level &L, const double *dx, double *dw, cudaStream_t s) {
+    DevMem xp, wp;
+    CK(xp.alloc(sizeof(T) * L.g.len));
+    CK(wp.alloc(sizeof(T) * L.g.len));
+    launch_pack<double, T>(L.g, dx, xp.as<T>(), s);
+    launch_apply<T, T, T>(L.g, L.w, op_of<T>(L),
+                          xp.as<T>(), wp.as<T>(), s);
+    launch_unpack<T, double>(L.g, wp.as<T>(), dw, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return MK_OK;
+}
+
+static size_t level_n(const Level &L) { return (size_t)L.g.nx * L.g.ny * (size_t)(L.g.nt + 1); }
+
+extern "C" {
+
+mk_status mk_op_apply(mk_problem *p, const mk_solve_opts *opts, int32_t level, int32_t precision,
+                      const double *x, double *w, void *stream) {
+    if (!x || !w || (precision != 0 && precision != 1)) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Hierarchy *H = nullptr;
+    mk_solve_opts o;
+    CKS(get_level(p, opts, level, H, o));
+    Level &L = *H->lv[level - 1];
+    DevMem tin;
+    const double *dx = nullptr;
+    CKS(stage_in(x, level_n(L), tin, dx, s));
+    OutStage os;
+    CKS(stage_out(w, level_n(L), os));
+    CKS(precision == 0 ? op_apply_t<double>(L, dx, os.dev, s) : op_apply_t<float>(L, dx, os.dev, s));
+    return finish_out(os, s);
+}
+
+mk_status mk_op_residual(mk_problem *p, const double *f, const double *u, double *r, double *rnorm,
+                         void *stream) {
+    if (!p || !f || !u || !r) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Problem &P = p->P;
+    // a standalone fine level (no hierarchy needed): coefficients, state, reduction scratch
+    Level L;
+    L.g = P.g;
+    L.w.a = P.theta * P.dt;
+    L.w.b = (1.0 - P.theta) * P.dt;
+    {
+        Tri Lx = fd_laplacian(P.nx, P.tau), Ly;
+        if (P.dim == 2) Ly = fd_laplacian(P.ny, P.tau);
+        std::vector<double> c(Lx.lo);
+        c.insert(c.end(), Lx.di.begin(), Lx.di.end());
+        c.insert(c.end(), Lx.up.begin(), Lx.up.end());
+        if (P.dim == 2) {
+            c.insert(c.end(), Ly.lo.begin(), Ly.lo.end());
+            c.insert(c.end(), Ly.di.begin(), Ly.di.end());
+            c.insert(c.end(), Ly.up.begin(), Ly.up.end());
+        }
+        CK(L.c64.alloc(sizeof(double) * c.size()));
+        CK(cudaMemcpy(L.c64.p, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice));
+        L.op64.x = L.c64.as<double>();
+        L.op64.y = P.dim == 2 ? L.c64.as<double>() + 3 * P.nx : nullptr;
+    }
+    CK(L.ksd.alloc(sizeof(double) * KState::ndoubles(1)));
+    CK(L.ksf.alloc(sizeof(int) * 8));
+    L.ks = KState{L.ksd.as<double>(), L.ksf.as<int>(), 1};
+    DevMem part, cnt;
+    ReduceScratch rs;
+    rs.max_blocks = 65536;
+    CK(part.alloc(sizeof(double) * rs.max_blocks));
+    CK(cnt.alloc(sizeof(unsigned) * 4));
+    rs.partials = part.as<double>();
+    rs.counter = cnt.as<unsigned>();
+    size_t n = st_n(P);
+    DevMem tf, tu, fp, up, rp;
+    const double *df = nullptr, *du = nullptr;
+    CKS(stage_in(f, n, tf, df, s));
+    CKS(stage_in(u, n, tu, du, s));
+    OutStage os;
+    CKS(stage_out(r, n, os));
+    CK(fp.alloc(sizeof(double) * L.g.len));
+    CK(up.alloc(sizeof(double) * L.g.len));
+    CK(rp.alloc(sizeof(double) * L.g.len));
+    launch_pack<double, double>(L.g, df, fp.as<double>(), s);
+    launch_pack<double, double>(L.g, du, up.as<double>(), s);
+    launch_residual(L.g, L.w, L.op64, fp.as<double>(), up.as<double>(), rp.as<double>(), rs, 0,
+                    L.ks, EPI_NONE, s);
+    launch_unpack<double, double>(L.g, rp.as<double>(), os.dev, s);
+    CK(cudaGetLastError());
+    double hm[8];
+    CK(cudaMemcpyAsync(hm, L.ks.misc(), sizeof(hm), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (rnorm) *rnorm = std::sqrt(hm[5]);
+    return finish_out(os, s);
+}
+
+}  // extern "C"
+
+template <typename T>
+static mk_status op_restrict_t(Hierarchy &H, int l, const double *dv, double *dvh, cudaStream_t s) {
+    Level &L = *H.lv[l];
+    Level &C = *H.lv[l + 1];
+    DevMem vp, cp;
+    CK(vp.alloc(sizeof(T) * L.g.len));
+    CK(cp.alloc(sizeof(T) * C.g.len));
+    launch_pack<double, T>(L.g, dv, vp.as<T>(), s);
+    SpaceOp<T> op = op_of<T>(L);
+    launch_restrict<T, T, T>(L.g, C.g, L.nu, L.space, L.w, op, vp.as<T>(), nullptr, cp.as<T>(),
+                             H.rs, 0, KState{nullptr, nullptr, 0}, nullptr, s);
+    launch_unpack<T, double>(C.g, cp.as<T>(), dvh, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return MK_OK;
+}
+
+extern "C" {
+
+mk_status mk_op_restrict(mk_problem *p, const mk_solve_opts *opts, int32_t level, int32_t precision,
+                         const double *v, double *vhat, void *stream) {
+    if (!v || !vhat || (precision != 0 && precision != 1)) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Hierarchy *H = nullptr;
+    mk_solve_opts o;
+    CKS(get_level(p, opts, level, H, o));
+    if (level >= (int)H->lv.size()) return MK_ERR_INVALID;
+    Level &L = *H->lv[level - 1];
+    Level &C = *H->lv[level];
+    DevMem tin;
+    const double *dv = nullptr;
+    CKS(stage_in(v, level_n(L), tin, dv, s));
+    OutStage os;
+    CKS(stage_out(vhat, level_n(C), os));
+    CKS(precision == 0 ? op_restrict_t<double>(*H, level - 1, dv, os.dev, s)
+                       : op_restrict_t<float>(*H, level - 1, dv, os.dev, s));
+    return finish_out(os, s);
+}
+
+}  // extern "C"
+
+template <typename T>
+static mk_status op_interp_t(Hierarchy &H, int l, const double *dv, const double *dvt, double *dx,
+                             double *dw, cudaStream_t s) {
+    Level &L = *H.lv[l];
+    Level &C = *H.lv[l + 1];
+    DevMem vp, cp, xp, wp;
+    CK(vp.alloc(sizeof(T) * L.g.len));
+    CK(cp.alloc(sizeof(T) * C.g.len));
+    CK(xp.alloc(sizeof(T) * L.g.len));
+    CK(wp.alloc(sizeof(T) * L.g.len));
+    launch_pack<double, T>(L.g, dv, vp.as<T>(), s);
+    launch_pack<double, T>(C.g, dvt, cp.as<T>(), s);
+    SpaceOp<T> op = op_of<T>(L);
+    launch_interp<T, T, T, T, T>(L.g, C.g, L.nu, L.space, L.w, op, vp.as<T>(), nullptr, cp.as<T>(),
+                                 1, C.stride, nullptr, xp.as<T>(), wp.as<T>(), nullptr, s);
+    launch_unpack<T, double>(L.g, xp.as<T>(), dx, s);
+    launch_unpack<T, double>(L.g, wp.as<T>(), dw, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return MK_OK;
+}
+
+extern "C" {
+
+mk_status mk_op_interp_correct(mk_problem *p, const mk_solve_opts *opts, int32_t level,
+                               int32_t precision, const double *v, const double *vt, double *x,
+                               double *w, void *stream) {
+    if (!v || !vt || !x || !w || (precision != 0 && precision != 1)) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Hierarchy *H = nullptr;
+    mk_solve_opts o;
+    CKS(get_level(p, opts, level, H, o));
+    if (level >= (int)H->lv.size()) return MK_ERR_INVALID;
+    Level &L = *H->lv[level - 1];
+    Level &C = *H->lv[level];
+    DevMem t1, t2;
+    const double *dv = nullptr, *dvt = nullptr;
+    CKS(stage_in(v, level_n(L), t1, dv, s));
+    CKS(stage_in(vt, level_n(C), t2, dvt, s));
+    OutStage ox, ow;
+    CKS(stage_out(x, level_n(L), ox));
+    CKS(stage_out(w, level_n(L), ow));
+    CKS(precision == 0 ? op_interp_t<double>(*H, level - 1, dv, dvt, ox.dev, ow.dev, s)
+                       : op_interp_t<float>(*H, level - 1, dv, dvt, ox.dev, ow.dev, s));
+    CKS(finish_out(ox, s));
+    return finish_out(ow, s);
+}
+
+}  // extern "C"
+
+template <typename T>
+static mk_status op_coarsest_t(Hierarchy &H, const double *dr, double *dx, cudaStream_t s) {
+    Level &C = *H.lv.back();
+    DevMem rp, xp, al, ga, bi, sx, sxi, lx, sy, syi, ly;
+    CK(rp.alloc(sizeof(T) * C.g.len));
+    CK(xp.alloc(sizeof(T) * C.g.len));
+    launch_pack<double, T>(C.g, dr, rp.as<T>(), s);
+    // tables in the requested precision (the hierarchy holds them in its own precision)
+    SpaceOp<T> op = op_of<T>(C);
+    auto up = [&](DevMem &m, const std::vector<double> &h) -> cudaError_t {
+        std::vector<T> t(h.begin(), h.end());
+        cudaError_t e = m.alloc(sizeof(T) * t.size());
+        if (e == cudaSuccess) e = cudaMemcpy(m.p, t.data(), sizeof(T) * t.size(), cudaMemcpyHostToDevice);
+        return e;
+    };
+    if (C.g.dim == 1) {
+        std::vector<double> a1, g1, b1;
+        pcr_tables(C.Lx, C.w.a, C.npad, a1, g1, b1);
+        if (a1.empty()) {
+            a1.assign(C.npad, 0.0);
+            g1.assign(C.npad, 0.0);
+        }
+        CK(up(al, a1));
+        CK(up(ga, g1));
+        CK(up(bi, b1));
+        launch_slab_1d<T>(C.g, C.w.b, op, al.as<T>(), ga.as<T>(), bi.as<T>(), C.npad, C.nlev,
+                          H.key.n_cgs, rp.as<T>(), xp.as<T>(), nullptr, s);
+    } else {
+        std::vector<double> lx1, Sx1, Sxi1, ly1, Sy1, Syi1;
+        tri_eigen(C.Lx, lx1, Sx1, Sxi1);
+        tri_eigen(C.Ly, ly1, Sy1, Syi1);
+        CK(up(sx, Sx1));
+        CK(up(sxi, Sxi1));
+        CK(up(lx, lx1));
+        CK(up(sy, Sy1));
+        CK(up(syi, Syi1));
+        CK(up(ly, ly1));
+        launch_slab_2d<T>(C.g, C.w.a, C.w.b, op, sx.as<T>(), sxi.as<T>(), lx.as<T>(), sy.as<T>(),
+                          syi.as<T>(), ly.as<T>(), H.key.n_cgs, rp.as<T>(), xp.as<T>(), nullptr, s);
+    }
+    launch_unpack<T, double>(C.g, xp.as<T>(), dx, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return MK_OK;
+}
+
+extern "C" {
+
+mk_status mk_op_coarsest(mk_problem *p, const mk_solve_opts *opts, int32_t precision,
+                         const double *r, double *x, void *stream) {
+    if (!r || !x || (precision != 0 && precision != 1)) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Hierarchy *H = nullptr;
+    mk_solve_opts o;
+    CKS(get_level(p, opts, 1, H, o));
+    Level &C = *H->lv.back();
+    DevMem t1;
+    const double *dr = nullptr;
+    CKS(stage_in(r, level_n(C), t1, dr, s));
+    OutStage ox;
+    CKS(stage_out(x, level_n(C), ox));
+    CKS(precision == 0 ? op_coarsest_t<double>(*H, dr, ox.dev, s)
+                       : op_coarsest_t<float>(*H, dr, ox.dev, s));
+    return finish_out(ox, s);
+}
+
+mk_status mk_op_precond(mk_problem *p, const mk_solve_opts *opts, int32_t level, const double *v,
+                        double *x, void *stream) {
+    if (!v || !x) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Hierarchy *H = nullptr;
+    mk_solve_opts o;
+    CKS(get_level(p, opts, level, H, o));
+    if (level >= (int)H->lv.size()) return MK_ERR_INVALID;
+    Level &L = *H->lv[level - 1];
+    DevMem t1;
+    const double *dv = nullptr;
+    CKS(stage_in(v, level_n(L), t1, dv, s));
+    OutStage ox;
+    CKS(stage_out(x, level_n(L), ox));
+    // v -> basis slot 0 of level l with sigma_0 = 1; flags cleared (not done)
+    const bool l0 = level == 1;
+    if (l0 || H->precision == 0) launch_pack<double, double>(L.g, dv, L.V.as<double>(), s);
+    else launch_pack<double, float>(L.g, dv, L.V.as<float>(), s);
+    double one = 1.0;
+    CK(cudaMemcpyAsync(L.ks.sigma(), &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(L.ks.flags, 0, sizeof(int) * 8, s));
+    enqueue_cycle_step(*H, level - 1, 0, L.ks.flags, s);
+    if (H->precision == 0 || l0) {
+        if (H->precision == 0) launch_unpack<double, double>(L.g, L.X.as<double>(), ox.dev, s);
+        else launch_unpack<float, double>(L.g, L.X.as<float>(), ox.dev, s);
+    } else {
+        launch_unpack<float, double>(L.g, L.X.as<float>(), ox.dev, s);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return finish_out(ox, s);
+}
+
+mk_status mk_op_orthogonalize(mk_problem *p, int32_t j, const double *V, double *w, double *h,
+                              void *stream) {
+    if (!p || j < 1 || j > MK_MAX_RESTART || !V || !w || !h) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Problem &P = p->P;
+    const Geom &g = P.g;
+    size_t n = st_n(P);
+    DevMem tV, tw, Vp, ksd, ksf;
+    const double *dV = nullptr, *dw = nullptr;
+    CKS(stage_in(V, n * j, tV, dV, s));
+    CKS(stage_in(w, n, tw, dw, s));
+    OutStage ow;
+    CKS(stage_out(w, n, ow));
+    CKS(ensure_device());
+    // basis (j vectors) followed by w, all padded
+    CK(Vp.alloc(sizeof(double) * g.len * (j + 1)));
+    for (int i = 0; i < j; ++i)
+        launch_pack<double, double>(g, dV + (size_t)i * n, Vp.as<double>() + (int64_t)i * g.len, s);
+    DevMem Wp;
+    CK(Wp.alloc(sizeof(double) * g.len));
+    launch_pack<double, double>(g, dw, Wp.as<double>(), s);
+    KState ks;
+    ks.m = j + 1;
+    CK(ksd.alloc(sizeof(double) * KState::ndoubles(ks.m)));
+    CK(ksf.alloc(sizeof(int) * 8));
+    ks.d = ksd.as<double>();
+    ks.flags = ksf.as<int>();
+    std::vector<double> ones(j + 1, 1.0);
+    CK(cudaMemcpyAsync(ks.sigma(), ones.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s));
+    DevMem part, cnt;
+    ReduceScratch rs;
+    rs.max_blocks = 65536;
+    CK(part.alloc(sizeof(double) * rs.max_blocks * (j + 3)));
+    CK(cnt.alloc(sizeof(unsigned) * 16));
+    rs.partials = part.as<double>();
+    rs.counter = cnt.as<unsigned>();
+    // first pass; second pass forced (CGS2)
+    launch_multidot<double, double>(g.len, Wp.as<double>(), Vp.as<double>(), g.len, j - 1, rs, ks,
+                                    false, nullptr, s);
+    launch_update<double, double>(g.len, Wp.as<double>(), Vp.as<double>(), g.len, j - 1, true, rs,
+                                  ks, UPD_REORTH, false, nullptr, s);
+    int one = 1;
+    CK(cudaMemcpyAsync(ks.flags + 2, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    launch_multidot<double, double>(g.len, Wp.as<double>(), Vp.as<double>(), g.len, j - 1, rs, ks,
+                                    true, nullptr, s);
+    launch_update<double, double>(g.len, Wp.as<double>(), Vp.as<double>(), g.len, j - 1, true, rs,
+                                  ks, 0, true, nullptr, s);
+    // w <- V_j / ||V_j||  (normalised output)
+    std::vector<double> hH((size_t)(ks.m + 1) * ks.m);
+    std::vector<double> sig(ks.m + 1);
+    CK(cudaMemcpyAsync(hH.data(), ks.H(), sizeof(double) * hH.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(sig.data(), ks.sigma(), sizeof(double) * sig.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double *col = hH.data() + (size_t)(j - 1) * (ks.m + 1);
+    for (int i = 0; i <= j; ++i) h[i] = col[i];
+    // scale V_j on the device by sigma_j via a pack of the unpacked vector
+    DevMem tmpd;
+    CK(tmpd.alloc(sizeof(double) * n));
+    launch_unpack<double, double>(g, Vp.as<double>() + (int64_t)j * g.len, tmpd.as<double>(), s);
+    std::vector<double> hv(n);
+    CK(cudaMemcpyAsync(hv.data(), tmpd.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (size_t e = 0; e < n; ++e) hv[e] *= sig[j];
+    CK(cudaMemcpy(ow.dev, hv.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    return finish_out(ow, s);
+}
+
+mk_status mk_op_lsq(int32_t j, const double *H, double beta, double *y, double *res, void *stream) {
+    if (j < 1 || j > MK_MAX_RESTART || !H || !y) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    CKS(ensure_device());
+    DevMem dH, dg, dy, dr;
+    size_t nh = (size_t)(j + 1) * j;
+    CK(dH.alloc(sizeof(double) * nh));
+    CK(dg.alloc(sizeof(double) * (j + 1)));
+    CK(dy.alloc(sizeof(double) * j));
+    CK(dr.alloc(sizeof(double)));
+    CK(cudaMemcpyAsync(dH.p, H, sizeof(double) * nh, is_device_ptr(H) ? cudaMemcpyDeviceToDevice
+                                                                      : cudaMemcpyHostToDevice, s));
+    launch_lsq(j, dH.as<double>(), beta, dg.as<double>(), dy.as<double>(), dr.as<double>(), s);
+    CK(cudaGetLastError());
+    double hr = 0.0;
+    std::vector<double> hy(j);
+    CK(cudaMemcpyAsync(hy.data(), dy.p, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hr, dr.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (is_device_ptr(y)) CK(cudaMemcpy(y, hy.data(), sizeof(double) * j, cudaMemcpyHostToDevice));
+    else std::memcpy(y, hy.data(), sizeof(double) * j);
+    if (res) *res = hr;
+    return MK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Kernel launchers of libmk (internal).  Each launcher checks nothing but launch
+// errors; argument validation happens at the ABI.
+#pragma once
+
+#include "mk_internal.h"
+
+namespace mk {
+
+// Per-level device scalars of an FGMRES process (one block of doubles + ints).
+//   sigma[i]  : 1/||V_i|| (basis stored unnormalised, v_i = sigma_i V_i)
+//   H         : (m+1) x m Hessenberg, column-major, ld = m+1
+//   cs, sn, g : Givens rotations and rotated right-hand side (level 1)
+//   y         : least-squares solution (combination of the X_i)
+//   beta      : ||r_0|| of the current (re)start
+struct KState {
+    double *d;     // doubles, layout below
+    int *flags;    // [0] done, [1] j_final, [2] reorth, [3] error, [4] iterations (total)
+    int m;         // capacity (iterations per cycle)
+    __host__ __device__ double *sigma() const { return d; }                       // m+1
+    __host__ __device__ double *H() const { return d + (m + 1); }                  // (m+1)*m
+    __host__ __device__ double *cs() const { return d + (m + 1) * (m + 1); }       // m
+    __host__ __device__ double *sn() const { return cs() + m; }                    // m
+    __host__ __device__ double *g() const { return sn() + m; }                     // m+1
+    __host__ __device__ double *y() const { return g() + (m + 1); }                // m
+    __host__ __device__ double *tmp() const { return y() + m; }                    // m+1
+    __host__ __device__ double *misc() const { return tmp() + (m + 1); }           // 8
+    // misc[0] = beta, misc[1] = tol * ||f|| (absolute target), misc[2] = ||w||^2 before
+    // orthogonalisation, misc[3] = ||f||, misc[4] = last true residual norm,
+    // misc[5] = raw result of the last reduction, misc[6] = last Givens residual estimate
+    static int ndoubles(int m) { return (m + 1) + (m + 1) * m + 2 * m + (m + 1) + m + (m + 1) + 8; }
+};
+
+enum EpilogueKind {
+    EPI_NONE = 0,
+    EPI_BETA = 1,        // result[0] = ||v||^2 -> misc[0] = beta, sigma[0] = 1/beta (inner start)
+    EPI_OUTER_START = 2, // same, and g = beta e1, done/j reset, level-1 convergence test
+    EPI_OUTER_INIT = 3,  // first residual (= f): also ||f|| -> misc[3], tol*||f|| -> misc[1]
+                         // (tol read from misc[7])
+};
+
+// ---- stencil family (stencil.cu) ------------------------------------------------------
+template <typename Tsrc, typename Tdst>
+void launch_pack(const Geom &g, const Tsrc *dense, Tdst *padded, cudaStream_t s);
+template <typename Tsrc, typename Tdst>
+void launch_unpack(const Geom &g, const Tsrc *padded, Tdst *dense, cudaStream_t s);
+template <typename Tsrc, typename Tdst>
+void launch_convert(int64_t n, const Tsrc *src, Tdst *dst, cudaStream_t s);
+
+// f_k = dt((1-theta) g_{k-1} + theta g_k), k >= 1 (g dense -> f padded).
+void launch_rhs_source(const Geom &g, double theta, double dt, const double *gdense, double *f,
+                       cudaStream_t s);
+
+// w = A x  (Tc = arithmetic type).
+template <typename Tin, typename Tout, typename Tc>
+void launch_apply(const Geom &g, const Weights &w, SpaceOp<Tc> L, const Tin *x, Tout *out,
+                  cudaStream_t s);
+
+// r = f - A u ; ||r||^2 reduced into the KState (epilogue kind as above); r may alias V_0.
+void launch_residual(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
+                     const double *u, double *r, const ReduceScratch &rs, int slot,
+                     KState ks, int epi, cudaStream_t s);
+
+// vhat = sigma * Y^T (A v - mu v) from level f to level c.  If ks_c.d != nullptr the
+// squared norm of vhat is reduced and the inner start epilogue (EPI_BETA) runs on ks_c.
+// skip_if_done: early exit when *done != 0.
+template <typename Tin, typename Tout, typename Tc>
+void launch_restrict(const Geom &gf, const Geom &gc, int nu, bool space, const Weights &w,
+                     SpaceOp<Tc> L, const Tin *v, const double *sigma, Tout *vhat,
+                     const ReduceScratch &rs, int slot, KState ks_c, const int *done,
+                     cudaStream_t s);
+
+// x = sigma v - Z (sum_m yc[m] Xc_m) ; w = A x.  yc == nullptr means a single Xc with
+// coefficient 1.
+template <typename Tv, typename Tz, typename Tx, typename Tw, typename Tc>
+void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Weights &w,
+                   SpaceOp<Tc> L, const Tv *v, const double *sigma, const Tz *Xc, int mc,
+                   int64_t xc_stride, const double *yc, Tx *x, Tw *wout, const int *done,
+                   cudaStream_t s);
+
+// ---- Krylov family (krylov.cu) --------------------------------------------------------
+// Arnoldi step j on a process with state ks, vectors of length len (padded):
+//   h_i = sigma_i <W, V_i>, i = 0..j   (multidot, partials + last block)
+template <typename TW, typename TV>
+void launch_multidot(int64_t len, const TW *W, const TV *V, int64_t vstride, int j,
+                     const ReduceScratch &rs, KState ks, bool second_pass, const int *done,
+                     cudaStream_t s);
+//   V_{j+1} = W - sum_i h_i sigma_i V_i, ||.||^2 -> h_{j+1,j}, sigma_{j+1};
+//   last block also runs the least-squares bookkeeping (Givens for the outer level,
+//   final solve on the last inner iteration).
+enum UpdateMode {
+    UPD_REORTH = 1,     // request a second Gram-Schmidt pass when ||w'|| < ||w|| / sqrt(2)
+    UPD_GIVENS = 2,     // outer level: Givens update, convergence test, y on completion
+    UPD_INNER_LSQ = 4,  // inner level: least squares on the last iteration
+    UPD_OUTER = UPD_REORTH | UPD_GIVENS,
+    UPD_INNER = UPD_INNER_LSQ
+};
+template <typename TW, typename TV>
+void launch_update(int64_t len, const TW *W, TV *V, int64_t vstride, int j, bool write_next,
+                   const ReduceScratch &rs, KState ks, int mode, bool second_pass,
+                   const int *done, cudaStream_t s);
+
+// u += sum_{i < jf} y_i X_i (FP64 u), jf = flags[1] (outer) -- skip when nothing to add.
+template <typename TX>
+void launch_combine(int64_t len, double *u, const TX *X, int64_t xstride, KState ks,
+                    cudaStream_t s);
+
+// Small solve on the device: least squares of an explicit (j+1) x j Hessenberg by Givens,
+// rotating H in place; gg: j+1 doubles of scratch.
+void launch_lsq(int j, double *H, double beta, double *gg, double *y, double *res,
+                cudaStream_t s);
+
+// ---- slab solvers (slab.cu) -----------------------------------------------------------
+// 1D coarsest: n_cgs slabs x s steps, tridiagonal I - aL by parallel cyclic reduction with
+// precomputed tables (alpha, gamma, binv in T); x_0 = r_0.
+template <typename T>
+void launch_slab_1d(const Geom &g, double b, SpaceOp<T> L, const T *alpha, const T *gamma,
+                    const T *binv, int npad, int nlev, int n_cgs, const T *r, T *x,
+                    const int *done, cudaStream_t s);
+// 2D coarsest: fast diagonalisation of I - a(Lx (+) Ly) with S, S^{-1} per direction.
+template <typename T>
+void launch_slab_2d(const Geom &g, double a, double b, SpaceOp<T> L, const T *Sx, const T *Sxi,
+                    const T *lamx, const T *Sy, const T *Syi, const T *lamy, int n_cgs,
+                    const T *r, T *x, const int *done, cudaStream_t s);
+
+// Sequential theta-march on the GPU (FP64): the same direct solvers, one slab of nt steps
+// with the coupling kept (1D: one CTA; 2D: one CTA per step-solve).
+void launch_march_1d(const Geom &g, double b, SpaceOp<double> L, const double *alpha,
+                     const double *gamma, const double *binv, int npad, int nlev,
+                     const double *f, double *u, cudaStream_t s);
+void launch_march_2d(const Geom &g, double a, double b, SpaceOp<double> L, const double *Sx,
+                     const double *Sxi, const double *lamx, const double *Sy, const double *Syi,
+                     const double *lamy, const double *f, double *u, cudaStream_t s);
+
+}  // namespace mk

@@ -1,0 +1,483 @@
+// Solver core: the level hierarchy (Sec. 3.2 Galerkin levels, Sec. 4 recursion), the MK
+// cycle of substeps 4.1-4.5, inner fixed-iteration FGMRES on intermediate levels
+// (Sec. 4.1/4.2), the decoupled coarsest level (Sec. 3.3.2) and the outer FGMRES of
+// Algorithm 2 with restarts.  Everything between host synchronisations is a fixed
+// sequence of kernel launches on one stream, captured once per hierarchy into a CUDA
+// graph that runs one restart cycle; convergence is decided on the device and the
+// remaining kernels of a converged cycle return immediately.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "solver.h"
+
+namespace mk {
+
+bool OptsKey::operator==(const OptsKey &o) const {
+    if (levels != o.levels || n_cgs != o.n_cgs || mu_mode != o.mu_mode ||
+        precision != o.precision || restart != o.restart || mu_value != o.mu_value)
+        return false;
+    for (int i = 0; i < MK_MAX_LEVELS; ++i)
+        if (nu[i] != o.nu[i] || space[i] != o.space[i] || m_inner[i] != o.m_inner[i]) return false;
+    return true;
+}
+
+static OptsKey make_key(const mk_solve_opts &o) {
+    OptsKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.levels = o.levels;
+    k.n_cgs = o.n_cgs;
+    k.mu_mode = o.mu_mode;
+    k.precision = o.precision;
+    k.restart = o.restart;
+    k.mu_value = o.mu_mode == 2 ? o.mu_value : 0.0;
+    for (int i = 0; i < o.levels - 1 && i < MK_MAX_LEVELS; ++i) {
+        k.nu[i] = o.nu[i];
+        k.space[i] = o.space[i] ? 1 : 0;
+    }
+    for (int i = 0; i < o.levels - 2 && i < MK_MAX_LEVELS; ++i) k.m_inner[i] = o.m_inner[i];
+    return k;
+}
+
+Hierarchy::~Hierarchy() {
+    if (graph) cudaGraphExecDestroy(graph);
+}
+
+mk_status validate_opts(const Problem &P, const mk_solve_opts &o) {
+    if (!(o.tol > 0.0) || o.restart < 1 || o.restart > MK_MAX_RESTART || o.max_iters < 1)
+        return MK_ERR_INVALID;
+    if (o.levels < 2 || o.levels > MK_MAX_LEVELS) return MK_ERR_INVALID;
+    if (o.precision != 0 && o.precision != 1) return MK_ERR_INVALID;
+    if (o.mu_mode < 0 || o.mu_mode > 2) return MK_ERR_INVALID;
+    if (o.n_cgs < 0) return MK_ERR_INVALID;
+    int nt = P.nt, nx = P.nx, ny = P.dim == 2 ? P.ny : 1;
+    for (int l = 0; l < o.levels - 1; ++l) {
+        if (o.nu[l] < 1) return MK_ERR_INVALID;
+        if (nt % o.nu[l]) return MK_ERR_INVALID;
+        nt /= o.nu[l];
+        if (o.space[l]) {
+            if (nx < 2 || (P.dim == 2 && ny < 2)) return MK_ERR_INVALID;
+            nx = (nx + 1) / 2;
+            if (P.dim == 2) ny = (ny + 1) / 2;
+        }
+    }
+    for (int l = 0; l < o.levels - 2; ++l)
+        if (o.m_inner[l] < 1 || o.m_inner[l] > MK_MAX_INNER) return MK_ERR_INVALID;
+    if (o.n_cgs > 0 && nt % o.n_cgs) return MK_ERR_INVALID;
+    if (nt < 1) return MK_ERR_INVALID;
+    if (P.dim == 1 && nx > 4096) return MK_ERR_INVALID;
+    // 2D coarsest: fast diagonalisation in one CTA's shared memory
+    const int lim2d = o.precision == 0 ? 48 : 64;
+    if (P.dim == 2 && (nx > lim2d || ny > lim2d)) return MK_ERR_INVALID;
+    return MK_OK;
+}
+
+#define MKCK(call)                                         \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) {                           \
+            set_cuda_error(e_);                            \
+            return e_ == cudaErrorMemoryAllocation ? MK_ERR_NOMEM : MK_ERR_CUDA; \
+        }                                                  \
+    } while (0)
+
+template <typename T>
+static cudaError_t upload(DevMem &m, const std::vector<double> &h) {
+    std::vector<T> t(h.begin(), h.end());
+    cudaError_t e = m.alloc(sizeof(T) * (t.empty() ? 1 : t.size()));
+    if (e != cudaSuccess) return e;
+    if (!t.empty()) e = cudaMemcpy(m.p, t.data(), sizeof(T) * t.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+static std::vector<double> coef_concat(const Tri &Lx, const Tri *Ly) {
+    std::vector<double> c;
+    c.insert(c.end(), Lx.lo.begin(), Lx.lo.end());
+    c.insert(c.end(), Lx.di.begin(), Lx.di.end());
+    c.insert(c.end(), Lx.up.begin(), Lx.up.end());
+    if (Ly) {
+        c.insert(c.end(), Ly->lo.begin(), Ly->lo.end());
+        c.insert(c.end(), Ly->di.begin(), Ly->di.end());
+        c.insert(c.end(), Ly->up.begin(), Ly->up.end());
+    }
+    return c;
+}
+
+static mk_status upload_coefs(Level &L, int dim) {
+    std::vector<double> c = coef_concat(L.Lx, dim == 2 ? &L.Ly : nullptr);
+    MKCK(upload<double>(L.c64, c));
+    MKCK(upload<float>(L.c32, c));
+    L.op64.x = L.c64.as<double>();
+    L.op64.y = dim == 2 ? L.c64.as<double>() + 3 * L.Lx.n() : nullptr;
+    L.op32.x = L.c32.as<float>();
+    L.op32.y = dim == 2 ? L.c32.as<float>() + 3 * L.Lx.n() : nullptr;
+    return MK_OK;
+}
+
+static mk_status alloc_kstate(Level &L, int m) {
+    MKCK(L.ksd.alloc(sizeof(double) * KState::ndoubles(m)));
+    MKCK(L.ksf.alloc(sizeof(int) * 8));
+    L.ks.d = L.ksd.as<double>();
+    L.ks.flags = L.ksf.as<int>();
+    L.ks.m = m;
+    return MK_OK;
+}
+
+// Coarsest-level direct solver tables.
+static mk_status build_coarsest_tables(Level &C, int dim, bool fp64) {
+    if (dim == 1) {
+        int n = C.Lx.n();
+        int np = 32;
+        while (np < n) np *= 2;
+        C.npad = np;
+        C.nlev = pcr_levels(n);
+        std::vector<double> al, ga, bi;
+        pcr_tables(C.Lx, C.w.a, np, al, ga, bi);
+        if (al.empty()) {
+            al.assign(np, 0.0);
+            ga.assign(np, 0.0);
+        }
+        if (fp64) {
+            MKCK(upload<double>(C.alpha, al));
+            MKCK(upload<double>(C.gamma, ga));
+            MKCK(upload<double>(C.binv, bi));
+        } else {
+            MKCK(upload<float>(C.alpha, al));
+            MKCK(upload<float>(C.gamma, ga));
+            MKCK(upload<float>(C.binv, bi));
+        }
+    } else {
+        std::vector<double> lx, Sx, Sxi, ly, Sy, Syi;
+        tri_eigen(C.Lx, lx, Sx, Sxi);
+        tri_eigen(C.Ly, ly, Sy, Syi);
+        if (fp64) {
+            MKCK(upload<double>(C.Sx, Sx));
+            MKCK(upload<double>(C.Sxi, Sxi));
+            MKCK(upload<double>(C.lamx, lx));
+            MKCK(upload<double>(C.Sy, Sy));
+            MKCK(upload<double>(C.Syi, Syi));
+            MKCK(upload<double>(C.lamy, ly));
+        } else {
+            MKCK(upload<float>(C.Sx, Sx));
+            MKCK(upload<float>(C.Sxi, Sxi));
+            MKCK(upload<float>(C.lamx, lx));
+            MKCK(upload<float>(C.Sy, Sy));
+            MKCK(upload<float>(C.Syi, Syi));
+            MKCK(upload<float>(C.lamy, ly));
+        }
+    }
+    return MK_OK;
+}
+
+mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out) {
+    OptsKey key = make_key(o);
+    if (P.H && P.H->key == key) {
+        out = P.H.get();
+        return MK_OK;
+    }
+    P.H.reset();
+    std::unique_ptr<Hierarchy> H(new Hierarchy());
+    H->key = key;
+    H->precision = o.precision;
+    const bool fp64 = o.precision == 0;
+    const size_t cs = fp64 ? sizeof(double) : sizeof(float);
+    const int L = o.levels;
+    for (int l = 0; l < L; ++l) {
+        std::unique_ptr<Level> lv(new Level());
+        if (l == 0) {
+            lv->Lx = fd_laplacian(P.nx, P.tau);
+            if (P.dim == 2) lv->Ly = fd_laplacian(P.ny, P.tau);
+            lv->w.a = P.theta * P.dt;
+            lv->w.b = (1.0 - P.theta) * P.dt;
+            lv->g = P.g;
+        } else {
+            Level &pv = *H->lv[l - 1];
+            int nu = o.nu[l - 1];
+            bool sp = o.space[l - 1] != 0;
+            lv->Lx = sp ? agglomerate(pv.Lx) : pv.Lx;
+            if (P.dim == 2) lv->Ly = sp ? agglomerate(pv.Ly) : pv.Ly;
+            // Galerkin coarse operator as a theta-scheme with a larger step (Eqs.
+            // (timecoarse1)-(timecoarse3), literal product nu psi - (nu-1) phi)
+            lv->w.a = nu * pv.w.a + (nu - 1) * pv.w.b;
+            lv->w.b = pv.w.b;
+            lv->g = make_geom(P.dim, lv->Lx.n(), P.dim == 2 ? lv->Ly.n() : 1, pv.g.nt / nu);
+        }
+        if (l < L - 1) {
+            lv->nu = o.nu[l];
+            lv->space = o.space[l] != 0;
+        }
+        lv->coarsest = (l == L - 1);
+        // shift mu_l = lambda_max(A_l) (Sec. 3.1), or 1, or a given value
+        double lam = tri_lambda_max_neg(lv->Lx);
+        if (P.dim == 2) lam += tri_lambda_max_neg(lv->Ly);
+        if (o.mu_mode == 0) lv->w.mu = std::max(1.0, 1.0 + lv->w.a * lam);
+        else if (o.mu_mode == 1) lv->w.mu = 1.0;
+        else lv->w.mu = o.mu_value;
+        mk_status st = upload_coefs(*lv, P.dim);
+        if (st != MK_OK) return st;
+        lv->stride = lv->g.len;
+        const size_t len = (size_t)lv->g.len;
+        if (l == 0) {
+            lv->m = o.restart;
+            MKCK(lv->V.alloc(sizeof(double) * len * (lv->m + 1)));
+            MKCK(lv->X.alloc(cs * len * lv->m));
+            MKCK(lv->W.alloc(sizeof(double) * len));
+            st = alloc_kstate(*lv, lv->m);
+            if (st != MK_OK) return st;
+        } else if (l < L - 1) {
+            lv->m = o.m_inner[l - 1];
+            MKCK(lv->V.alloc(cs * len * (lv->m + 1)));
+            MKCK(lv->X.alloc(cs * len * lv->m));
+            MKCK(lv->W.alloc(cs * len));
+            st = alloc_kstate(*lv, lv->m);
+            if (st != MK_OK) return st;
+        } else {
+            lv->m = 1;
+            MKCK(lv->R.alloc(cs * len));
+            MKCK(lv->X.alloc(cs * len));
+            st = build_coarsest_tables(*lv, P.dim, fp64);
+            if (st != MK_OK) return st;
+        }
+        H->lv.push_back(std::move(lv));
+    }
+    const size_t len0 = (size_t)P.g.len;
+    MKCK(H->f.alloc(sizeof(double) * len0));
+    MKCK(H->u.alloc(sizeof(double) * len0));
+    H->rs.max_blocks = 65536;
+    MKCK(H->partials.alloc(sizeof(double) * (size_t)H->rs.max_blocks *
+                           (std::max(o.restart, MK_MAX_INNER) + 4)));
+    MKCK(H->counters.alloc(sizeof(unsigned) * 16));
+    H->rs.partials = H->partials.as<double>();
+    H->rs.counter = H->counters.as<unsigned>();
+    P.H = std::move(H);
+    out = P.H.get();
+    return MK_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// MK cycle (enqueue only)
+// ---------------------------------------------------------------------------------------
+template <typename Tc>
+void enqueue_coarsest_t(Hierarchy &H, const int *done, cudaStream_t s) {
+    Level &C = *H.lv.back();
+    if (C.g.dim == 1)
+        launch_slab_1d<Tc>(C.g, C.w.b, op_of<Tc>(C), C.alpha.as<Tc>(), C.gamma.as<Tc>(),
+                           C.binv.as<Tc>(), C.npad, C.nlev, H.key.n_cgs, C.R.as<Tc>(), C.X.as<Tc>(),
+                           done, s);
+    else
+        launch_slab_2d<Tc>(C.g, C.w.a, C.w.b, op_of<Tc>(C), C.Sx.as<Tc>(), C.Sxi.as<Tc>(),
+                           C.lamx.as<Tc>(), C.Sy.as<Tc>(), C.Syi.as<Tc>(), C.lamy.as<Tc>(),
+                           H.key.n_cgs, C.R.as<Tc>(), C.X.as<Tc>(), done, s);
+}
+
+void enqueue_coarsest(Hierarchy &H, const int *done, cudaStream_t s) {
+    if (H.precision == 0) enqueue_coarsest_t<double>(H, done, s);
+    else enqueue_coarsest_t<float>(H, done, s);
+}
+
+template <typename Tc>
+static void enqueue_inner_solve(Hierarchy &H, int l, const int *done, cudaStream_t s);
+
+// x_j = Q_l v_j and w = A_l x_j; Tv = type of level l's basis, Tx = type of its X,
+// Tw/Tcw = type and arithmetic of w.
+template <typename Tc, typename Tv, typename Tx, typename Tw, typename Tcw>
+static void cycle_step_t(Hierarchy &H, int l, int j, const int *done, cudaStream_t s) {
+    Level &L = *H.lv[l];
+    Level &C = *H.lv[l + 1];
+    const Tv *vj = L.V.as<Tv>() + (int64_t)j * L.stride;
+    const double *sig = L.ks.sigma() + j;
+    // 4.1-4.2: restriction of the shifted residual of the basis vector
+    if (C.coarsest) {
+        launch_restrict<Tv, Tc, Tc>(L.g, C.g, L.nu, L.space, L.w, op_of<Tc>(L), vj, sig,
+                                    C.R.as<Tc>(), H.rs, 0, KState{nullptr, nullptr, 0}, done, s);
+        enqueue_coarsest_t<Tc>(H, done, s);                          // 4.3 (decoupled slabs)
+    } else {
+        launch_restrict<Tv, Tc, Tc>(L.g, C.g, L.nu, L.space, L.w, op_of<Tc>(L), vj, sig,
+                                    C.V.as<Tc>(), H.rs, 0, C.ks, done, s);
+        enqueue_inner_solve<Tc>(H, l + 1, done, s);                  // 4.3 (recursion)
+    }
+    // 4.4-4.5 and step 5: x = v - Z vt, w = A x
+    const Tc *Xc = C.X.as<Tc>();
+    const double *yc = C.coarsest ? nullptr : C.ks.y();
+    int mc = C.coarsest ? 1 : C.m;
+    launch_interp<Tv, Tc, Tx, Tw, Tcw>(L.g, C.g, L.nu, L.space, L.w, op_of<Tcw>(L), vj, sig, Xc, mc,
+                                       C.stride, yc, L.X.as<Tx>() + (int64_t)j * L.stride,
+                                       L.W.as<Tw>(), done, s);
+}
+
+template <typename Tc>
+static void enqueue_inner_solve(Hierarchy &H, int l, const int *done, cudaStream_t s) {
+    Level &L = *H.lv[l];
+    const int64_t len = L.g.len;
+    for (int j = 0; j < L.m; ++j) {
+        cycle_step_t<Tc, Tc, Tc, Tc, Tc>(H, l, j, done, s);
+        launch_multidot<Tc, Tc>(len, L.W.as<Tc>(), L.V.as<Tc>(), L.stride, j, H.rs, L.ks, false,
+                                done, s);
+        launch_update<Tc, Tc>(len, L.W.as<Tc>(), L.V.as<Tc>(), L.stride, j, j < L.m - 1, H.rs, L.ks,
+                              UPD_INNER, false, done, s);
+    }
+}
+
+void enqueue_cycle_step(Hierarchy &H, int l, int j, const int *done, cudaStream_t s) {
+    if (H.precision == 0) {
+        cycle_step_t<double, double, double, double, double>(H, l, j, done, s);
+    } else if (l == 0) {
+        cycle_step_t<float, double, float, double, double>(H, l, j, done, s);
+    } else {
+        cycle_step_t<float, float, float, float, float>(H, l, j, done, s);
+    }
+}
+
+// One restart cycle of the outer FGMRES (Algorithm 2), ending with the true residual of
+// the updated iterate, which also starts the next cycle.
+static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s) {
+    Level &L = *H.lv[0];
+    const int *done = L.ks.flags;
+    const int64_t len = L.g.len;
+    double *V = L.V.as<double>();
+    double *W = L.W.as<double>();
+    for (int j = 0; j < L.m; ++j) {
+        enqueue_cycle_step(H, 0, j, done, s);
+        launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, false, done, s);
+        launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, UPD_OUTER, false,
+                                      done, s);
+        launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, true, done, s);
+        launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, UPD_OUTER, true,
+                                      done, s);
+    }
+    if (H.precision == 0)
+        launch_combine<double>(len, H.u.as<double>(), L.X.as<double>(), L.stride, L.ks, s);
+    else
+        launch_combine<float>(len, H.u.as<double>(), L.X.as<float>(), L.stride, L.ks, s);
+    launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), V, H.rs, 0, L.ks,
+                    EPI_OUTER_START, s);
+}
+
+mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const double *f_padded,
+                    mk_solve_info *info, cudaStream_t s) {
+    Level &L = *H.lv[0];
+    const int64_t len = L.g.len;
+    int launches0 = 0;
+    (void)launches0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MKCK(cudaEventCreate(&e0));
+    MKCK(cudaEventCreate(&e1));
+    MKCK(cudaEventRecord(e0, s));
+    if (f_padded && f_padded != H.f.as<double>())
+        MKCK(cudaMemcpyAsync(H.f.p, f_padded, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    MKCK(cudaMemsetAsync(H.u.p, 0, sizeof(double) * len, s));
+    MKCK(cudaMemsetAsync(L.ks.flags, 0, sizeof(int) * 8, s));
+    static thread_local double tolbuf;
+    tolbuf = o.tol;
+    MKCK(cudaMemcpyAsync(L.ks.misc() + 7, &tolbuf, sizeof(double), cudaMemcpyHostToDevice, s));
+    // r_0 = f (u^0 = 0): ||f||, tol * ||f||, v_1
+    launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<double>(), H.rs,
+                    0, L.ks, EPI_OUTER_INIT, s);
+    // capture one restart cycle into a graph (once per hierarchy)
+    if (o.use_graph && !H.graph) {
+        cudaStream_t cs;
+        MKCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        MKCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        enqueue_outer_cycle(P, H, cs);
+        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (ce != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            set_cuda_error(ce);
+            return MK_ERR_CUDA;
+        }
+        ce = cudaGraphInstantiate(&H.graph, graph, 0);
+        cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (ce != cudaSuccess) {
+            set_cuda_error(ce);
+            H.graph = nullptr;
+            return MK_ERR_CUDA;
+        }
+    }
+    int hflags[8];
+    double hmisc[8];
+    mk_status status = MK_OK;
+    int cycles = 0;
+    int64_t launches_before = 0;
+    (void)launches_before;
+    for (;;) {
+        if (o.use_graph) {
+            MKCK(cudaGraphLaunch(H.graph, s));
+        } else {
+            enqueue_outer_cycle(P, H, s);
+        }
+        ++cycles;
+        MKCK(cudaMemcpyAsync(hflags, L.ks.flags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+        MKCK(cudaMemcpyAsync(hmisc, L.ks.misc(), sizeof(hmisc), cudaMemcpyDeviceToHost, s));
+        MKCK(cudaStreamSynchronize(s));
+        if (hflags[3]) {
+            status = MK_ERR_NONFINITE;
+            break;
+        }
+        if (hflags[0]) break;                 // true residual below tol * ||f||
+        if (hflags[4] >= o.max_iters) {
+            status = MK_ERR_NOT_CONVERGED;
+            break;
+        }
+    }
+    MKCK(cudaEventRecord(e1, s));
+    MKCK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) {
+        info->iterations = hflags[4];
+        info->restarts = cycles;
+        info->f_norm = hmisc[3];
+        info->rel_residual = hmisc[3] > 0.0 ? hmisc[4] / hmisc[3] : 0.0;
+        info->solve_ms = ms;
+        info->levels = (int)H.lv.size();
+    }
+    return status;
+}
+
+// ---------------------------------------------------------------------------------------
+// theta-march tables (fine level, FP64)
+// ---------------------------------------------------------------------------------------
+mk_status prepare_march(Problem &P) {
+    if (P.march_ready) return MK_OK;
+    Tri Lx = fd_laplacian(P.nx, P.tau);
+    Tri Ly;
+    if (P.dim == 2) Ly = fd_laplacian(P.ny, P.tau);
+    std::vector<double> c = coef_concat(Lx, P.dim == 2 ? &Ly : nullptr);
+    MKCK(upload<double>(P.m_c64, c));
+    const double a = P.theta * P.dt;
+    if (P.dim == 1) {
+        if (P.nx > 4096) return MK_ERR_INVALID;
+        int np = 32;
+        while (np < P.nx) np *= 2;
+        P.m_npad = np;
+        P.m_nlev = pcr_levels(P.nx);
+        std::vector<double> al, ga, bi;
+        pcr_tables(Lx, a, np, al, ga, bi);
+        if (al.empty()) {
+            al.assign(np, 0.0);
+            ga.assign(np, 0.0);
+        }
+        MKCK(upload<double>(P.m_alpha, al));
+        MKCK(upload<double>(P.m_gamma, ga));
+        MKCK(upload<double>(P.m_binv, bi));
+    } else {
+        if (P.nx > 48 || P.ny > 48) return MK_ERR_INVALID;
+        std::vector<double> lx, Sx, Sxi, ly, Sy, Syi;
+        tri_eigen(Lx, lx, Sx, Sxi);
+        tri_eigen(Ly, ly, Sy, Syi);
+        MKCK(upload<double>(P.m_Sx, Sx));
+        MKCK(upload<double>(P.m_Sxi, Sxi));
+        MKCK(upload<double>(P.m_lamx, lx));
+        MKCK(upload<double>(P.m_Sy, Sy));
+        MKCK(upload<double>(P.m_Syi, Syi));
+        MKCK(upload<double>(P.m_lamy, ly));
+    }
+    P.march_ready = true;
+    return MK_OK;
+}
+
+}  // namespace mk

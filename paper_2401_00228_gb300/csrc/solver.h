@@ -1,0 +1,109 @@
+// Solver core of libmk (internal): the level hierarchy, the MK cycle and FGMRES.
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "kernels.h"
+
+namespace mk {
+
+// Owning device allocation.
+struct DevMem {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+    ~DevMem() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t n) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = n;
+        cudaError_t e = cudaMalloc(&p, n > 0 ? n : 16);
+        if (e == cudaSuccess) e = cudaMemset(p, 0, n > 0 ? n : 16);
+        return e;
+    }
+    template <typename T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct OptsKey {
+    int levels, n_cgs, mu_mode, precision, restart;
+    int nu[MK_MAX_LEVELS], space[MK_MAX_LEVELS], m_inner[MK_MAX_LEVELS];
+    double mu_value;
+    bool operator==(const OptsKey &o) const;
+};
+
+struct Level {
+    Geom g;
+    Weights w;
+    Tri Lx, Ly;
+    int nu = 1;        // coarsening factor to the next level
+    bool space = false;
+    int m = 0;         // restart (level 1) or fixed iterations (intermediate levels)
+    bool coarsest = false;
+    DevMem c64, c32;   // [3nx | 3ny] coefficients
+    SpaceOp<double> op64{nullptr, nullptr};
+    SpaceOp<float> op32{nullptr, nullptr};
+    // vectors (level 1: V, W in FP64, X in the cycle precision; others in cycle precision)
+    DevMem V, X, W;
+    int64_t stride = 0;
+    // FGMRES state
+    DevMem ksd, ksf;
+    KState ks{nullptr, nullptr, 0};
+    // coarsest-level direct solver tables (cycle precision)
+    DevMem R;          // coarsest right-hand side
+    DevMem alpha, gamma, binv;
+    int npad = 0, nlev = 0;
+    DevMem Sx, Sxi, lamx, Sy, Syi, lamy;
+};
+
+struct Hierarchy {
+    OptsKey key;
+    int precision = 0;  // 0 FP64, 1 mixed
+    std::vector<std::unique_ptr<Level>> lv;
+    DevMem f, u;        // level-1 right-hand side and iterate (FP64)
+    DevMem partials, counters;
+    ReduceScratch rs{nullptr, nullptr, 0};
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    ~Hierarchy();
+};
+
+struct Problem {
+    int dim, nx, ny, nt;
+    double theta, dt, tau;
+    Geom g;                       // fine-level geometry
+    DevMem fsrc;                  // padded FP64 source blocks f_k (k >= 1), block 0 zero
+    bool has_source = false;
+    std::unique_ptr<Hierarchy> H; // cached for the last options
+    // march tables (fine level, FP64)
+    bool march_ready = false;
+    DevMem m_c64, m_alpha, m_gamma, m_binv, m_Sx, m_Sxi, m_lamx, m_Sy, m_Syi, m_lamy;
+    int m_npad = 0, m_nlev = 0;
+};
+
+template <typename T>
+inline SpaceOp<T> op_of(const Level &L);
+template <>
+inline SpaceOp<double> op_of<double>(const Level &L) { return L.op64; }
+template <>
+inline SpaceOp<float> op_of<float>(const Level &L) { return L.op32; }
+
+mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out);
+mk_status validate_opts(const Problem &P, const mk_solve_opts &o);
+
+// FGMRES + MK on f (padded FP64, level 1) -> H.u.  f is copied into H.f.
+mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const double *f_padded,
+                    mk_solve_info *info, cudaStream_t s);
+
+// x_j = Q_l v_j, w = A_l x_j for basis slot j of level l (enqueue only).
+void enqueue_cycle_step(Hierarchy &H, int l, int j, const int *done, cudaStream_t s);
+void enqueue_coarsest(Hierarchy &H, const int *done, cudaStream_t s);
+
+mk_status prepare_march(Problem &P);
+
+}  // namespace mk

@@ -1,0 +1,606 @@
+// Space-time stencil kernels: RHS assembly, layout conversion, matvec A_l x (K1),
+// residual f - A u (K2), fused matvec-shift-restriction (K3) and fused
+// interpolation-correction-matvec (K4).
+//
+// Operator (Sec. 2, Eq. (finesys), at any level of Sec. 3.2 / Sec. 4):
+//   (A x)_0 = x_0,   (A x)_k = (x_k - a L x_k) - (x_{k-1} + b L x_{k-1}),
+// with L = Lx (+) Ly a sum of per-direction tridiagonal operators.
+//
+// Mapping: one thread per spatial point (or per coarse aggregate), looping over a chunk of
+// consecutive time steps, so that x_{k-1} and L x_{k-1} are carried in registers and each
+// element is read from DRAM once (spatial neighbours come from L1/L2).  Loads are
+// coalesced along i (the contiguous direction of the padded layout).
+#include "kernels.h"
+#include "reduce.cuh"
+
+namespace mk {
+
+// ---------------------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------------------
+template <int DIM, typename Tc, typename Tin>
+__device__ __forceinline__ Tc lap_at(const Tin *__restrict__ x, int64_t idx, int i, int j,
+                                     const Geom &g, const Tc *__restrict__ cx,
+                                     const Tc *__restrict__ cy) {
+    Tc v = (Tc)x[idx];
+    Tc s = cx[g.nx + i] * v + cx[i] * (Tc)x[idx - 1] + cx[2 * g.nx + i] * (Tc)x[idx + 1];
+    if (DIM == 2) {
+        Tc sy = cy[g.ny + j] * v + cy[j] * (Tc)x[idx - g.ldx] + cy[2 * g.ny + j] * (Tc)x[idx + g.ldx];
+        s = s + sy;
+    }
+    return s;
+}
+
+static int choose_kc(int64_t npts, int nsteps) {
+    // enough threads to fill the GPU a few times over; at most 32 steps per thread
+    int64_t target = (int64_t)g_num_sms * 2048;
+    int64_t kc = (npts * nsteps) / (target > 0 ? target : 1);
+    if (kc < 1) kc = 1;
+    if (kc > 32) kc = 32;
+    return (int)kc;
+}
+
+struct Launch2 {
+    dim3 grid, block;
+};
+
+// thread -> spatial point (i, j); block/grid cover (nx, ny) x chunks
+static Launch2 point_launch(int dim, int nx, int ny, int nchunks) {
+    Launch2 L;
+    if (dim == 1) {
+        int bx = nx >= 256 ? 256 : ((nx + 31) / 32) * 32;
+        L.block = dim3(bx, 1, 1);
+        L.grid = dim3((nx + bx - 1) / bx, nchunks, 1);
+    } else {
+        L.block = dim3(32, 8, 1);
+        L.grid = dim3((nx + 31) / 32, (ny + 7) / 8, nchunks);
+    }
+    return L;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool point_index(int &i, int &j, int &chunk) {
+    i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (DIM == 1) {
+        j = 0;
+        chunk = blockIdx.y;
+    } else {
+        j = blockIdx.y * blockDim.y + threadIdx.y;
+        chunk = blockIdx.z;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// layout conversion
+// ---------------------------------------------------------------------------------------
+template <typename Tsrc, typename Tdst>
+__global__ void k_pack(Geom g, const Tsrc *__restrict__ dense, Tdst *__restrict__ padded) {
+    int64_t n = g.interior();
+    int64_t npts = g.npts();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = e / npts;
+        int64_t r = e - k * npts;
+        int j = (int)(r / g.nx), i = (int)(r - (int64_t)j * g.nx);
+        padded[g.at((int)k, j, i)] = (Tdst)dense[e];
+    }
+}
+
+template <typename Tsrc, typename Tdst>
+__global__ void k_unpack(Geom g, const Tsrc *__restrict__ padded, Tdst *__restrict__ dense) {
+    int64_t n = g.interior();
+    int64_t npts = g.npts();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = e / npts;
+        int64_t r = e - k * npts;
+        int j = (int)(r / g.nx), i = (int)(r - (int64_t)j * g.nx);
+        dense[e] = (Tdst)padded[g.at((int)k, j, i)];
+    }
+}
+
+template <typename Tsrc, typename Tdst>
+__global__ void k_convert(int64_t n, const Tsrc *__restrict__ src, Tdst *__restrict__ dst) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = (Tdst)src[e];
+}
+
+static int grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    int64_t cap = (int64_t)g_num_sms * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <typename Tsrc, typename Tdst>
+void launch_pack(const Geom &g, const Tsrc *dense, Tdst *padded, cudaStream_t s) {
+    k_pack<Tsrc, Tdst><<<grid_for(g.interior(), 256), 256, 0, s>>>(g, dense, padded);
+    count_launch();
+}
+template <typename Tsrc, typename Tdst>
+void launch_unpack(const Geom &g, const Tsrc *padded, Tdst *dense, cudaStream_t s) {
+    k_unpack<Tsrc, Tdst><<<grid_for(g.interior(), 256), 256, 0, s>>>(g, padded, dense);
+    count_launch();
+}
+template <typename Tsrc, typename Tdst>
+void launch_convert(int64_t n, const Tsrc *src, Tdst *dst, cudaStream_t s) {
+    k_convert<Tsrc, Tdst><<<grid_for(n, 256), 256, 0, s>>>(n, src, dst);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// RHS assembly (Eq. (finesys)): f_k = dt ((1-theta) g_{k-1} + theta g_k), k >= 1
+// ---------------------------------------------------------------------------------------
+__global__ void k_rhs_source(Geom g, double theta, double dt, const double *__restrict__ gd,
+                             double *__restrict__ f) {
+    int64_t npts = g.npts();
+    int64_t n = (int64_t)g.nt * npts;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t km1 = e / npts;
+        int64_t r = e - km1 * npts;
+        int j = (int)(r / g.nx), i = (int)(r - (int64_t)j * g.nx);
+        double gbar = (1.0 - theta) * gd[e] + theta * gd[e + npts];
+        f[g.at((int)km1 + 1, j, i)] = dt * gbar;
+    }
+}
+
+void launch_rhs_source(const Geom &g, double theta, double dt, const double *gdense, double *f,
+                       cudaStream_t s) {
+    k_rhs_source<<<grid_for((int64_t)g.nt * g.npts(), 256), 256, 0, s>>>(g, theta, dt, gdense, f);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// K1: w = A x
+// ---------------------------------------------------------------------------------------
+template <int DIM, typename Tin, typename Tout, typename Tc>
+__global__ void __launch_bounds__(256) k_apply(Geom g, Tc a, Tc b, SpaceOp<Tc> L,
+                                               const Tin *__restrict__ x,
+                                               Tout *__restrict__ w, int kc) {
+    int i, j, chunk;
+    point_index<DIM>(i, j, chunk);
+    if (i >= g.nx || j >= g.ny) return;
+    int k0 = chunk * kc;
+    int k1 = min(k0 + kc, g.nt + 1);
+    Tc prev = 0, Lprev = 0;
+    if (k0 > 0) {
+        int64_t idx = g.at(k0 - 1, j, i);
+        prev = (Tc)x[idx];
+        Lprev = lap_at<DIM, Tc>(x, idx, i, j, g, L.x, L.y);
+    }
+#pragma unroll 4
+    for (int k = k0; k < k1; ++k) {
+        int64_t idx = g.at(k, j, i);
+        Tc cur = (Tc)x[idx];
+        Tc Lc = lap_at<DIM, Tc>(x, idx, i, j, g, L.x, L.y);
+        Tc r = (k == 0) ? cur : (cur - a * Lc) - (prev + b * Lprev);
+        w[idx] = (Tout)r;
+        prev = cur;
+        Lprev = Lc;
+    }
+}
+
+template <typename Tin, typename Tout, typename Tc>
+void launch_apply(const Geom &g, const Weights &w, SpaceOp<Tc> L, const Tin *x, Tout *out,
+                  cudaStream_t s) {
+    int kc = choose_kc(g.npts(), g.nt + 1);
+    int nch = (g.nt + 1 + kc - 1) / kc;
+    Launch2 l = point_launch(g.dim, g.nx, g.ny, nch);
+    if (g.dim == 1)
+        k_apply<1, Tin, Tout, Tc><<<l.grid, l.block, 0, s>>>(g, (Tc)w.a, (Tc)w.b, L, x, out, kc);
+    else
+        k_apply<2, Tin, Tout, Tc><<<l.grid, l.block, 0, s>>>(g, (Tc)w.a, (Tc)w.b, L, x, out, kc);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// K2: r = f - A u, ||r||^2
+// ---------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(256) k_residual(Geom g, double a, double b, SpaceOp<double> L,
+                                                  const double *__restrict__ f,
+                                                  const double *__restrict__ u,
+                                                  double *__restrict__ r, int kc,
+                                                  ReduceScratch rs, int slot, KState ks, int epi) {
+    int i, j, chunk;
+    point_index<DIM>(i, j, chunk);
+    double acc = 0.0;
+    if (i < g.nx && j < g.ny) {
+        int k0 = chunk * kc;
+        int k1 = min(k0 + kc, g.nt + 1);
+        double prev = 0, Lprev = 0;
+        if (k0 > 0) {
+            int64_t idx = g.at(k0 - 1, j, i);
+            prev = u[idx];
+            Lprev = lap_at<DIM, double>(u, idx, i, j, g, L.x, L.y);
+        }
+        for (int k = k0; k < k1; ++k) {
+            int64_t idx = g.at(k, j, i);
+            double cur = u[idx];
+            double Lc = lap_at<DIM, double>(u, idx, i, j, g, L.x, L.y);
+            double Au = (k == 0) ? cur : (cur - a * Lc) - (prev + b * Lprev);
+            double rv = f[idx] - Au;
+            r[idx] = rv;
+            acc += rv * rv;
+            prev = cur;
+            Lprev = Lc;
+        }
+    }
+    block_partial_and_finish(acc, rs, slot, ks, epi);
+}
+
+void launch_residual(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
+                     const double *u, double *r, const ReduceScratch &rs, int slot, KState ks,
+                     int epi, cudaStream_t s) {
+    int kc = choose_kc(g.npts(), g.nt + 1);
+    int nch = (g.nt + 1 + kc - 1) / kc;
+    Launch2 l = point_launch(g.dim, g.nx, g.ny, nch);
+    if (g.dim == 1)
+        k_residual<1><<<l.grid, l.block, 0, s>>>(g, w.a, w.b, L, f, u, r, kc, rs, slot, ks, epi);
+    else
+        k_residual<2><<<l.grid, l.block, 0, s>>>(g, w.a, w.b, L, f, u, r, kc, rs, slot, ks, epi);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// K3: vhat = sigma Y^T (A v - mu v)   (substeps 4.1-4.2)
+//   Y^T sums the nu fine steps of each coarse block (Eq. (tcoarseZ), Y_k = Z_k) and, with
+//   space agglomeration, averages each aggregate (Eq. (constructY)).  Block 0 maps to
+//   block 0: (A v)_0 = v_0, so vhat_0 = sigma (1 - mu) Y^T v_0.
+//   Thread -> coarse spatial point (aggregate), loop over a chunk of coarse blocks; the
+//   fine points of the aggregate (1, 2 or 4) each carry their own (v_{k-1}, L v_{k-1}).
+// ---------------------------------------------------------------------------------------
+template <int DIM, bool SPACE, typename Tin, typename Tout, typename Tc>
+__global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu, Tc a, Tc b, Tc mu,
+                                                  SpaceOp<Tc> L, const Tin *__restrict__ v,
+                                                  const double *__restrict__ sigma,
+                                                  Tout *__restrict__ vhat, int kc,
+                                                  ReduceScratch rs, int slot, KState ks,
+                                                  const int *__restrict__ done) {
+    if (done && *done) return;
+    constexpr int PX = SPACE ? 2 : 1;
+    constexpr int PY = (SPACE && DIM == 2) ? 2 : 1;
+    int I, J, chunk;
+    point_index<DIM>(I, J, chunk);
+    double acc2 = 0.0;
+    const bool active = I < gc.nx && J < gc.ny;
+    if (active) {
+        const Tc scale = sigma ? (Tc)(*sigma) : (Tc)1;
+        // fine points of this aggregate
+        int ii[PX], jj[PY];
+        int npx = 0, npy = 0;
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+            ii[p] = PX * I + p;
+            if (ii[p] < gf.nx) npx = p + 1;
+        }
+#pragma unroll
+        for (int q = 0; q < PY; ++q) {
+            jj[q] = (DIM == 2) ? PY * J + q : 0;
+            if (jj[q] < gf.ny) npy = q + 1;
+        }
+        const Tc inv_count = (Tc)1 / (Tc)(npx * npy);
+        Tc prev[PY][PX], Lprev[PY][PX];
+        const int K0 = chunk * kc;
+        const int K1 = min(K0 + kc, gc.nt + 1);
+        // state at the fine step just before the chunk
+        if (K0 > 0) {
+            int kf = nu * (K0 - 1);
+#pragma unroll
+            for (int q = 0; q < PY; ++q)
+#pragma unroll
+                for (int p = 0; p < PX; ++p) {
+                    prev[q][p] = 0;
+                    Lprev[q][p] = 0;
+                    if (p < npx && q < npy) {
+                        int64_t idx = gf.at(kf, jj[q], ii[p]);
+                        prev[q][p] = (Tc)v[idx];
+                        Lprev[q][p] = lap_at<DIM, Tc>(v, idx, ii[p], jj[q], gf, L.x, L.y);
+                    }
+                }
+        }
+        for (int K = K0; K < K1; ++K) {
+            Tc sum = 0;
+            if (K == 0) {
+#pragma unroll
+                for (int q = 0; q < PY; ++q)
+#pragma unroll
+                    for (int p = 0; p < PX; ++p) {
+                        if (p < npx && q < npy) {
+                            int64_t idx = gf.at(0, jj[q], ii[p]);
+                            Tc cur = (Tc)v[idx];
+                            sum += cur - mu * cur;
+                            prev[q][p] = cur;
+                            Lprev[q][p] = lap_at<DIM, Tc>(v, idx, ii[p], jj[q], gf, L.x, L.y);
+                        }
+                    }
+            } else {
+                for (int s = 1; s <= nu; ++s) {
+                    int kf = nu * (K - 1) + s;
+#pragma unroll
+                    for (int q = 0; q < PY; ++q)
+#pragma unroll
+                        for (int p = 0; p < PX; ++p) {
+                            if (p < npx && q < npy) {
+                                int64_t idx = gf.at(kf, jj[q], ii[p]);
+                                Tc cur = (Tc)v[idx];
+                                Tc Lc = lap_at<DIM, Tc>(v, idx, ii[p], jj[q], gf, L.x, L.y);
+                                Tc Av = (cur - a * Lc) - (prev[q][p] + b * Lprev[q][p]);
+                                sum += Av - mu * cur;
+                                prev[q][p] = cur;
+                                Lprev[q][p] = Lc;
+                            }
+                        }
+                }
+            }
+            Tc outv = scale * (sum * inv_count);
+            vhat[gc.at(K, J, I)] = (Tout)outv;
+            acc2 += (double)outv * (double)outv;
+        }
+    }
+    if (ks.d) block_partial_and_finish(acc2, rs, slot, ks, EPI_BETA);
+}
+
+template <typename Tin, typename Tout, typename Tc>
+void launch_restrict(const Geom &gf, const Geom &gc, int nu, bool space, const Weights &w,
+                     SpaceOp<Tc> L, const Tin *v, const double *sigma, Tout *vhat,
+                     const ReduceScratch &rs, int slot, KState ks_c, const int *done,
+                     cudaStream_t s) {
+    int kc = choose_kc(gc.npts() * (space ? (gf.dim == 2 ? 4 : 2) : 1) * nu, gc.nt + 1);
+    int nch = (gc.nt + 1 + kc - 1) / kc;
+    Launch2 l = point_launch(gf.dim, gc.nx, gc.ny, nch);
+    Tc a = (Tc)w.a, b = (Tc)w.b, mu = (Tc)w.mu;
+#define MK_RESTRICT(D, S) \
+    k_restrict<D, S, Tin, Tout, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, nu, a, b, mu, L, v, sigma, \
+                                                                vhat, kc, rs, slot, ks_c, done)
+    if (gf.dim == 1) {
+        if (space) MK_RESTRICT(1, true); else MK_RESTRICT(1, false);
+    } else {
+        if (space) MK_RESTRICT(2, true); else MK_RESTRICT(2, false);
+    }
+#undef MK_RESTRICT
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// K4: x = sigma v - Z vt,  w = A x      (substeps 4.4-4.5 and step 5 of Algorithm 2)
+//   vt = sum_m yc[m] Xc_m (the inner FGMRES solution of the coarser level, combined on
+//   the fly).  (Z vt)_0 = Z vt_0, (Z vt)_k = Z vt_{ceil(k/nu)}; in space Z copies the
+//   aggregate value to its members (Eq. (constructZ)).
+// ---------------------------------------------------------------------------------------
+template <int DIM, bool SPACE, typename Tv, typename Tz, typename Tx>
+struct XEval {
+    const Tv *v;
+    Tx sigma;
+    const Tz *Xc;
+    int mc;
+    int64_t xc_stride;
+    const double *yc;
+    Geom gf, gc;
+    int nu;
+
+    // x at fine (k, j, i); zero outside the interior (Dirichlet)
+    __device__ __forceinline__ Tx operator()(int k, int j, int i) const {
+        if (i < 0 || i >= gf.nx || j < 0 || j >= gf.ny) return (Tx)0;
+        int K = (k == 0) ? 0 : (k - 1) / nu + 1;
+        int I = SPACE ? (i >> 1) : i;
+        int J = (SPACE && DIM == 2) ? (j >> 1) : j;
+        int64_t cidx = gc.at(K, J, I);
+        Tx zt;
+        if (yc == nullptr) {
+            zt = (Tx)Xc[cidx];
+        } else {
+            zt = (Tx)0;
+            for (int m = 0; m < mc; ++m) zt += (Tx)yc[m] * (Tx)Xc[cidx + m * xc_stride];
+        }
+        return sigma * (Tx)v[gf.at(k, j, i)] - zt;
+    }
+};
+
+template <int DIM, bool SPACE, typename Tv, typename Tz, typename Tx, typename Tw, typename Tc>
+__global__ void __launch_bounds__(256) k_interp(Geom gf, Geom gc, int nu, Tc a, Tc b,
+                                                SpaceOp<Tc> L, const Tv *__restrict__ v,
+                                                const double *__restrict__ sigma,
+                                                const Tz *__restrict__ Xc, int mc,
+                                                int64_t xc_stride,
+                                                const double *__restrict__ yc,
+                                                Tx *__restrict__ xout, Tw *__restrict__ wout,
+                                                int kc, const int *__restrict__ done) {
+    if (done && *done) return;
+    int i, j, chunk;
+    point_index<DIM>(i, j, chunk);
+    if (i >= gf.nx || j >= gf.ny) return;
+    XEval<DIM, SPACE, Tv, Tz, Tx> X{v, sigma ? (Tx)(*sigma) : (Tx)1, Xc, mc, xc_stride, yc, gf, gc, nu};
+    const Tc *cx = L.x;
+    const Tc *cy = L.y;
+    auto lap = [&](int k, Tc c) -> Tc {
+        Tc s = cx[gf.nx + i] * c + cx[i] * (Tc)X(k, j, i - 1) + cx[2 * gf.nx + i] * (Tc)X(k, j, i + 1);
+        if (DIM == 2) {
+            Tc sy = cy[gf.ny + j] * c + cy[j] * (Tc)X(k, j - 1, i) + cy[2 * gf.ny + j] * (Tc)X(k, j + 1, i);
+            s = s + sy;
+        }
+        return s;
+    };
+    int k0 = chunk * kc;
+    int k1 = min(k0 + kc, gf.nt + 1);
+    Tc prev = 0, Lprev = 0;
+    if (k0 > 0) {
+        prev = (Tc)X(k0 - 1, j, i);
+        Lprev = lap(k0 - 1, prev);
+    }
+    for (int k = k0; k < k1; ++k) {
+        Tx xs = X(k, j, i);
+        Tc cur = (Tc)xs;
+        Tc Lc = lap(k, cur);
+        Tc r = (k == 0) ? cur : (cur - a * Lc) - (prev + b * Lprev);
+        int64_t idx = gf.at(k, j, i);
+        xout[idx] = xs;
+        wout[idx] = (Tw)r;
+        prev = cur;
+        Lprev = Lc;
+    }
+}
+
+template <typename Tv, typename Tz, typename Tx, typename Tw, typename Tc>
+void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Weights &w,
+                   SpaceOp<Tc> L, const Tv *v, const double *sigma, const Tz *Xc, int mc,
+                   int64_t xc_stride, const double *yc, Tx *x, Tw *wout, const int *done,
+                   cudaStream_t s) {
+    int kc = choose_kc(gf.npts(), gf.nt + 1);
+    int nch = (gf.nt + 1 + kc - 1) / kc;
+    Launch2 l = point_launch(gf.dim, gf.nx, gf.ny, nch);
+    Tc a = (Tc)w.a, b = (Tc)w.b;
+#define MK_INTERP(D, S)                                                                        \
+    k_interp<D, S, Tv, Tz, Tx, Tw, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, nu, a, b, L, v, sigma, \
+                                                                  Xc, mc, xc_stride, yc, x, wout, \
+                                                                  kc, done)
+    if (gf.dim == 1) {
+        if (space) MK_INTERP(1, true); else MK_INTERP(1, false);
+    } else {
+        if (space) MK_INTERP(2, true); else MK_INTERP(2, false);
+    }
+#undef MK_INTERP
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// Adjoint of Eq. (finesys).  A_h^T is block upper bidiagonal (psi, phi symmetric), so
+// with y_j = lam_{nt+1-j} the system A_h^T lam = b becomes the forward system with
+// right-hand side f_rev[0] = 0, f_rev[j] = b[nt+1-j] (then y_0 = 0).
+// ---------------------------------------------------------------------------------------
+__global__ void k_reverse_pack(Geom g, const double *__restrict__ b, double *__restrict__ f) {
+    int64_t npts = g.npts();
+    int64_t n = (int64_t)(g.nt + 1) * npts;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = e / npts;
+        int64_t r = e - k * npts;
+        int j = (int)(r / g.nx), i = (int)(r - (int64_t)j * g.nx);
+        f[g.at((int)k, j, i)] = (k == 0) ? 0.0 : b[(g.nt + 1 - k) * npts + r];
+    }
+}
+
+void launch_reverse_pack(const Geom &g, const double *dense, double *padded, cudaStream_t s) {
+    k_reverse_pack<<<grid_for(g.interior(), 256), 256, 0, s>>>(g, dense, padded);
+    count_launch();
+}
+
+// lam_k = y_{nt+1-k} (k >= 1), lam_{nt+1} = 0, lam_0 = b_0 + phi lam_1;
+// dJ/dg_k = dt (theta lam_k + (1-theta) lam_{k+1}) (k >= 1), dJ/dg_0 = dt (1-theta) lam_1;
+// dJ/dtau = (dt/tau) sum_{k>=1} lam_k^T L (theta u_k + (1-theta) u_{k-1}).
+template <int DIM>
+__global__ void __launch_bounds__(256) k_adjoint_grads(Geom g, double theta, double dt, double tau,
+                                                       double bw, SpaceOp<double> L,
+                                                       const double *__restrict__ y,
+                                                       const double *__restrict__ b,
+                                                       const double *__restrict__ upad,
+                                                       double *__restrict__ lam,
+                                                       double *__restrict__ gu0,
+                                                       double *__restrict__ gg, int kc,
+                                                       ReduceScratch rs, KState ks) {
+    int i, j, chunk;
+    point_index<DIM>(i, j, chunk);
+    double acc = 0.0;
+    if (i < g.nx && j < g.ny) {
+        const int64_t npts = g.npts();
+        const int64_t r = (int64_t)j * g.nx + i;
+        int k0 = chunk * kc;
+        int k1 = min(k0 + kc, g.nt + 1);
+        double Luprev = 0.0;
+        if (upad && k0 > 0) Luprev = lap_at<DIM, double>(upad, g.at(k0 - 1, j, i), i, j, g, L.x, L.y);
+        for (int k = k0; k < k1; ++k) {
+            double lk;
+            if (k == 0) {
+                int64_t i1 = g.at(g.nt, j, i);   // lam_1 = y_nt
+                double l1 = y[i1];
+                double Ll1 = lap_at<DIM, double>(y, i1, i, j, g, L.x, L.y);
+                lk = b[r] + (l1 + bw * Ll1);
+                if (gu0) gu0[r] = lk;
+            } else {
+                lk = y[g.at(g.nt + 1 - k, j, i)];
+            }
+            double lnext = (k + 1 <= g.nt) ? y[g.at(g.nt - k, j, i)] : 0.0;
+            if (lam) lam[(int64_t)k * npts + r] = lk;
+            if (gg) gg[(int64_t)k * npts + r] = (k == 0) ? dt * (1.0 - theta) * lnext
+                                                         : dt * (theta * lk + (1.0 - theta) * lnext);
+            if (upad) {
+                double Lu = lap_at<DIM, double>(upad, g.at(k, j, i), i, j, g, L.x, L.y);
+                if (k >= 1) acc += lk * (theta * Lu + (1.0 - theta) * Luprev);
+                Luprev = Lu;
+            }
+        }
+    }
+    acc *= dt / tau;
+    block_partial_and_finish(acc, rs, 0, ks, EPI_NONE);
+}
+
+void launch_adjoint_grads(const Geom &g, double theta, double dt, double tau, SpaceOp<double> L,
+                          const double *y, const double *b, const double *upad, double *lam,
+                          double *grad_u0, double *grad_g, const ReduceScratch &rs, KState ks,
+                          cudaStream_t s) {
+    int kc = choose_kc(g.npts(), g.nt + 1);
+    int nch = (g.nt + 1 + kc - 1) / kc;
+    Launch2 l = point_launch(g.dim, g.nx, g.ny, nch);
+    double bw = (1.0 - theta) * dt;
+    if (g.dim == 1)
+        k_adjoint_grads<1><<<l.grid, l.block, 0, s>>>(g, theta, dt, tau, bw, L, y, b, upad, lam,
+                                                      grad_u0, grad_g, kc, rs, ks);
+    else
+        k_adjoint_grads<2><<<l.grid, l.block, 0, s>>>(g, theta, dt, tau, bw, L, y, b, upad, lam,
+                                                      grad_u0, grad_g, kc, rs, ks);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// explicit instantiations
+// ---------------------------------------------------------------------------------------
+template void launch_pack<double, double>(const Geom &, const double *, double *, cudaStream_t);
+template void launch_pack<double, float>(const Geom &, const double *, float *, cudaStream_t);
+template void launch_unpack<double, double>(const Geom &, const double *, double *, cudaStream_t);
+template void launch_unpack<float, double>(const Geom &, const float *, double *, cudaStream_t);
+template void launch_convert<double, float>(int64_t, const double *, float *, cudaStream_t);
+template void launch_convert<float, double>(int64_t, const float *, double *, cudaStream_t);
+
+template void launch_apply<double, double, double>(const Geom &, const Weights &, SpaceOp<double>,
+                                                   const double *, double *, cudaStream_t);
+template void launch_apply<float, float, float>(const Geom &, const Weights &, SpaceOp<float>,
+                                                const float *, float *, cudaStream_t);
+template void launch_apply<float, double, double>(const Geom &, const Weights &, SpaceOp<double>,
+                                                  const float *, double *, cudaStream_t);
+
+template void launch_restrict<double, double, double>(const Geom &, const Geom &, int, bool,
+                                                      const Weights &, SpaceOp<double>,
+                                                      const double *, const double *, double *,
+                                                      const ReduceScratch &, int, KState,
+                                                      const int *, cudaStream_t);
+template void launch_restrict<double, float, float>(const Geom &, const Geom &, int, bool,
+                                                    const Weights &, SpaceOp<float>,
+                                                    const double *, const double *, float *,
+                                                    const ReduceScratch &, int, KState,
+                                                    const int *, cudaStream_t);
+template void launch_restrict<float, float, float>(const Geom &, const Geom &, int, bool,
+                                                   const Weights &, SpaceOp<float>, const float *,
+                                                   const double *, float *, const ReduceScratch &,
+                                                   int, KState, const int *, cudaStream_t);
+
+// FP64 throughout
+template void launch_interp<double, double, double, double, double>(
+    const Geom &, const Geom &, int, bool, const Weights &, SpaceOp<double>, const double *,
+    const double *, const double *, int, int64_t, const double *, double *, double *,
+    const int *, cudaStream_t);
+// mixed, level 1: FP64 basis, FP32 coarse and x, FP64 w
+template void launch_interp<double, float, float, double, double>(
+    const Geom &, const Geom &, int, bool, const Weights &, SpaceOp<double>, const double *,
+    const double *, const float *, int, int64_t, const double *, float *, double *,
+    const int *, cudaStream_t);
+// mixed, inner levels: FP32 throughout
+template void launch_interp<float, float, float, float, float>(
+    const Geom &, const Geom &, int, bool, const Weights &, SpaceOp<float>, const float *,
+    const double *, const float *, int, int64_t, const double *, float *, float *, const int *,
+    cudaStream_t);
+
+}  // namespace mk

@@ -1,0 +1,383 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, step by step along the
+hot path and end to end.  Inputs are seeded; each comparison is element by element.
+
+Tolerances: FP64 kernels 1e-12 relative to the largest output (rounding order differs);
+FP32 kernels 1e-5 (1e-3 for the FP32 slab solves, whose matrices have condition numbers up
+to ~1e4); whole solves 1e-10 (FP64) / 1e-8 (mixed) max relative error, the targets of the
+method's specification.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+mk = pytest.importorskip("paper_2401_00228_gb300")
+
+
+def _opts(s: W.Schedule, precision="fp64", tol=1e-12, restart=40, mu="lambda_max", n_cgs=None):
+    return mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner,
+                        n_cgs=s.n_cgs if n_cgs is None else n_cgs, tol=tol, restart=restart,
+                        precision=precision, mu=mu)
+
+
+def _hier(P: W.Problem, mu_mode="lambda_max", n_cgs=None):
+    s = P.schedule
+    return O.make_hierarchy(P.dim, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, s.nu, s.space,
+                            s.m_inner, s.n_cgs if n_cgs is None else n_cgs, mu_mode=mu_mode)
+
+
+def _prob(P: W.Problem):
+    return mk.Problem(P.dim, P.nx, P.tau, P.theta, P.dt, P.nt, P.g, ny=P.ny)
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# Small seeded problems spanning several tiles and ragged tails (odd sizes, n not a
+# multiple of 32, n_t + 1 not a multiple of the time chunk).
+SMALL = {
+    "1d_n63_T": lambda: W.custom(1, 63, 256, 0.1, 1.0, 0.5, W.Schedule((2, 2), (False, False), (1,), 16),
+                                 seed=11, with_source=True),
+    "1d_n100_T3": lambda: W.custom(1, 100, 96, 0.2, 0.7, 1.0, W.Schedule((3, 2, 2), (False,) * 3, (2, 1), 4),
+                                   seed=12, with_source=True),
+    "1d_n101_TS": lambda: W.custom(1, 101, 64, 0.05, 1.3, 0.5, W.Schedule((2, 2), (True, True), (2,), 8),
+                                   seed=13, with_source=True),
+    "2d_15x13_TS": lambda: W.custom(2, 15, 32, 0.05, 1.0, 1.0, W.Schedule((2, 2), (True, True), (2,), 4),
+                                    seed=14, ny=13, with_source=True),
+    "2d_33x31_T": lambda: W.custom(2, 33, 16, 0.02, 0.5, 0.5, W.Schedule((2,), (False,), (), 4),
+                                   seed=15, ny=31),
+}
+
+
+@pytest.fixture(scope="module", params=list(SMALL))
+def case(request):
+    P = SMALL[request.param]()
+    H = _hier(P)
+    with _prob(P) as p:
+        yield P, H, p
+
+
+# --------------------------------------------------------------------------- a1
+def test_rhs_assembly(case):
+    P, H, p = case
+    f = np.empty((P.nt + 1,) + P.space_shape())
+    mk.mk_op_rhs(p.handle, P.u0, f)
+    ref = O.assemble_rhs(P.u0, P.g, P.nt, P.theta, P.dt)
+    assert _rel(f, ref) <= 1e-15
+
+
+# --------------------------------------------------------------------------- a4
+def test_level_setup_is_galerkin(case):
+    P, H, p = case
+    o = _opts(P.schedule)
+    for l, lv in enumerate(H.levels, start=1):
+        d, xc, yc = mk.mk_level_info(p.handle, o, l)
+        assert (d.nx, d.ny, d.nt) == (lv.nx, lv.ny, lv.nt)
+        assert abs(d.a - lv.a) <= 1e-15 * lv.a and abs(d.b - lv.b) <= 1e-15 * max(lv.b, 1e-300)
+        assert abs(d.mu - lv.mu) <= 1e-12 * lv.mu
+        for got, T in ((xc, lv.Lx), (yc, lv.Ly)):
+            if T is None:
+                continue
+            ref = np.stack([T.lo, T.di, T.up])
+            assert _rel(got, ref) <= 1e-14
+
+
+# --------------------------------------------------------------------------- a2
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_apply(case, precision, tol):
+    P, H, p = case
+    o = _opts(P.schedule)
+    rng = np.random.default_rng(21)
+    for l, lv in enumerate(H.levels, start=1):
+        x = rng.standard_normal(lv.shape())
+        w = np.empty_like(x)
+        mk.mk_op_apply(p.handle, o, l, precision, x, w)
+        assert _rel(w, lv.apply_A(x)) <= tol, l
+
+
+# --------------------------------------------------------------------------- a3
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_restrict(case, precision, tol):
+    P, H, p = case
+    o = _opts(P.schedule)
+    rng = np.random.default_rng(22)
+    for l in range(len(H.levels) - 1):
+        lv = H.levels[l]
+        v = rng.standard_normal(lv.shape())
+        vh = np.empty(H.levels[l + 1].shape())
+        mk.mk_op_restrict(p.handle, o, l + 1, precision, v, vh)
+        ref = O.restrict(lv, H.nu[l], H.space[l], lv.apply_A(v) - lv.mu * v)
+        assert _rel(vh, ref) <= tol, l
+
+
+# --------------------------------------------------------------------------- a7
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_interp_correct(case, precision, tol):
+    P, H, p = case
+    o = _opts(P.schedule)
+    rng = np.random.default_rng(23)
+    for l in range(len(H.levels) - 1):
+        lv = H.levels[l]
+        v = rng.standard_normal(lv.shape())
+        vt = rng.standard_normal(H.levels[l + 1].shape())
+        x = np.empty_like(v)
+        w = np.empty_like(v)
+        mk.mk_op_interp_correct(p.handle, o, l + 1, precision, v, vt, x, w)
+        xr = v - O.interpolate(lv, H.nu[l], H.space[l], vt)
+        assert _rel(x, xr) <= tol, l
+        assert _rel(w, lv.apply_A(xr)) <= tol, l
+
+
+# --------------------------------------------------------------------------- a6
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-3)])
+def test_coarsest_slabs(case, precision, tol):
+    P, H, p = case
+    o = _opts(P.schedule)
+    lv = H.levels[-1]
+    r = np.random.default_rng(24).standard_normal(lv.shape())
+    x = np.empty_like(r)
+    mk.mk_op_coarsest(p.handle, o, precision, r, x)
+    assert _rel(x, O.coarsest_solve(lv, r, H.n_cgs)) <= tol
+
+
+def test_coarsest_exact_coupled(case):
+    P, H, p = case
+    o = _opts(P.schedule, n_cgs=0)
+    lv = H.levels[-1]
+    r = np.random.default_rng(25).standard_normal(lv.shape())
+    x = np.empty_like(r)
+    mk.mk_op_coarsest(p.handle, o, 0, r, x)
+    assert _rel(x, O.march(lv, r)) <= 1e-11
+
+
+# --------------------------------------------------------------------------- a5
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-3)])
+def test_precondition_cycle(case, precision, tol):
+    """x = Q_l v: restriction, inner FGMRES recursion, decoupled slabs, interpolation."""
+    P, H, p = case
+    o = _opts(P.schedule, precision=precision)
+    rng = np.random.default_rng(26)
+    for l in range(len(H.levels) - 1):
+        lv = H.levels[l]
+        v = rng.standard_normal(lv.shape())
+        v /= np.linalg.norm(v)
+        x = np.empty_like(v)
+        mk.mk_op_precond(p.handle, o, l + 1, v, x)
+        assert _rel(x, O.precondition(H, l, v)) <= tol, l
+
+
+# --------------------------------------------------------------------------- a8, a9, a10
+def test_orthogonalize(case):
+    P, H, p = case
+    lv = H.levels[0]
+    N = int(np.prod(lv.shape()))
+    rng = np.random.default_rng(27)
+    j = 5
+    Q, _ = np.linalg.qr(rng.standard_normal((N, j)))
+    V = np.ascontiguousarray(Q.T)
+    w0 = rng.standard_normal(N) + 3.0 * V[0]
+    w = w0.copy()
+    h = np.empty(j + 1)
+    mk.mk_op_orthogonalize(p.handle, j, V, w, h)
+    proj = V @ w0
+    rest = w0 - V.T @ proj
+    assert np.max(np.abs(h[:j] - proj)) <= 1e-12 * np.max(np.abs(proj))
+    assert abs(h[j] - np.linalg.norm(rest)) <= 1e-12 * np.linalg.norm(rest)
+    assert np.max(np.abs(w - rest / np.linalg.norm(rest))) <= 1e-12
+    assert np.max(np.abs(V @ w)) <= 1e-13
+
+
+@pytest.mark.parametrize("j", [1, 2, 7, 40])
+def test_hessenberg_least_squares(j):
+    rng = np.random.default_rng(28 + j)
+    H = np.triu(rng.standard_normal((j + 1, j)), -1)
+    beta = 2.5
+    y = np.empty(j)
+    res = mk.mk_op_lsq(j, np.asfortranarray(H).ravel(order="F").copy(), beta, y)
+    e1 = np.zeros(j + 1)
+    e1[0] = beta
+    yr = np.linalg.lstsq(H, e1, rcond=None)[0]
+    cond = np.linalg.cond(H)
+    assert np.max(np.abs(y - yr)) <= 1e-14 * cond * max(1.0, np.max(np.abs(yr)))
+    assert abs(res - np.linalg.norm(e1 - H @ yr)) <= 1e-13 * beta
+
+
+def test_residual(case):
+    P, H, p = case
+    lv = H.levels[0]
+    rng = np.random.default_rng(29)
+    f = rng.standard_normal(lv.shape())
+    u = rng.standard_normal(lv.shape())
+    r = np.empty_like(f)
+    nrm = mk.mk_op_residual(p.handle, f, u, r)
+    ref = f - lv.apply_A(u)
+    assert _rel(r, ref) <= 1e-12
+    assert abs(nrm - np.linalg.norm(ref)) <= 1e-12 * np.linalg.norm(ref)
+
+
+# --------------------------------------------------------------------------- end to end
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_solve_small(case, precision, bound):
+    P, H, p = case
+    o = _opts(P.schedule, precision=precision)
+    u = np.empty((P.nt + 1,) + P.space_shape())
+    info = mk.mk_solve(p.handle, P.u0, u, o)
+    ref = O.theta_march(P.dim, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)
+    assert info.rel_residual < 1e-12
+    assert O.max_rel_error(u, ref) <= bound, (info.iterations, O.max_rel_error(u, ref))
+
+
+def test_march_small(case):
+    P, H, p = case
+    if P.dim == 2 and max(P.nx, P.ny) > 48:
+        pytest.skip("2D march limited to 48x48")
+    u = np.empty((P.nt + 1,) + P.space_shape())
+    mk.mk_march(p.handle, P.u0, u)
+    ref = O.theta_march(P.dim, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)
+    assert O.max_rel_error(u, ref) <= 1e-12
+
+
+def test_solve_is_deterministic_and_graph_independent(case):
+    P, H, p = case
+    u1 = np.empty((P.nt + 1,) + P.space_shape())
+    u2 = np.empty_like(u1)
+    u3 = np.empty_like(u1)
+    o = _opts(P.schedule, precision="mixed")
+    mk.mk_solve(p.handle, P.u0, u1, o)
+    mk.mk_solve(p.handle, P.u0, u2, o)
+    o2 = _opts(P.schedule, precision="mixed")
+    o2.use_graph = 0
+    o2.restart = o.restart
+    mk.mk_solve(p.handle, P.u0, u3, o2)
+    assert np.array_equal(u1, u2)
+    assert np.array_equal(u1, u3)
+
+
+# --------------------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("which", ["1d", "2d"])
+def test_adjoint_matches_oracle(which):
+    rng = np.random.default_rng(31)
+    if which == "1d":
+        P = W.custom(1, 47, 64, 0.05, 0.8, 0.5, W.Schedule((2, 2), (False, False), (1,), 8), seed=5,
+                     with_source=True)
+    else:
+        P = W.custom(2, 17, 32, 0.05, 1.1, 1.0, W.Schedule((2, 2), (True, True), (2,), 4), seed=6,
+                     with_source=True)
+    tgt = rng.standard_normal(P.space_shape())
+    J, gu0, gg, gtau, u = O.misfit_gradients(P.dim, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, P.u0,
+                                            P.g, tgt)
+    dJdu = np.zeros_like(u)
+    dJdu[-1] = 2.0 * (u[-1] - tgt)
+    o = _opts(P.schedule)
+    with _prob(P) as p:
+        g_u0 = np.empty(P.space_shape())
+        g_g = np.empty_like(u)
+        gt, info = mk.mk_adjoint(p.handle, u, dJdu, o, grad_u0=g_u0, grad_g=g_g, want_tau=True)
+    assert _rel(g_u0, gu0) <= 1e-9
+    assert _rel(g_g, gg) <= 1e-9
+    assert abs(gt - gtau) <= 1e-9 * abs(gtau)
+
+
+# --------------------------------------------------------------------------- edge cases
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(mk.MKError):
+        mk.Problem(1, 0, 1.0, 0.5, 0.01, 8)
+    with pytest.raises(mk.MKError):
+        mk.Problem(1, 8, 1.0, 1.5, 0.01, 8)
+    with pytest.raises(mk.MKError):
+        mk.Problem(1, 8, 1.0, 0.5, -0.01, 8)
+    with mk.Problem(1, 8, 1.0, 0.5, 0.01, 10) as p:
+        u = np.empty((11, 8))
+        o = mk.make_opts(levels=3, nu=(2, 2), m_inner=(1,), n_cgs=4)   # 10 not divisible by 4
+        with pytest.raises(mk.MKError):
+            mk.mk_solve(p.handle, np.ones(8), u, o)
+
+
+def test_nonfinite_input_is_reported():
+    with mk.Problem(1, 31, 1.0, 0.5, 0.001, 16) as p:
+        u0 = np.ones(31)
+        u0[5] = np.nan
+        u = np.empty((17, 31))
+        with pytest.raises(mk.MKError) as e:
+            mk.mk_solve(p.handle, u0, u, mk.make_opts(levels=2, nu=(2,), n_cgs=4))
+        assert e.value.code == 4
+
+
+@pytest.mark.parametrize("nx,nt,levels,nu,n_cgs", [(1, 4, 2, (2,), 2), (2, 1, 2, (1,), 1),
+                                                    (3, 8, 3, (2, 2), 2), (1, 1, 2, (1,), 0)])
+def test_degenerate_sizes(nx, nt, levels, nu, n_cgs):
+    P = W.custom(1, nx, nt, 0.01, 1.0, 0.5, W.Schedule(nu, (False,) * len(nu), (1,) * (levels - 2), n_cgs),
+                 seed=3, with_source=True)
+    ref = O.theta_march(1, nx, 1, nt, P.tau, P.theta, P.dt, P.u0, P.g)
+    with _prob(P) as p:
+        u = np.empty_like(ref)
+        mk.mk_solve(p.handle, P.u0, u, _opts(P.schedule))
+        assert O.max_rel_error(u, ref) <= 1e-10
+        mk.mk_march(p.handle, P.u0, u)
+        assert O.max_rel_error(u, ref) <= 1e-12
+
+
+def test_zero_rhs_gives_zero():
+    with mk.Problem(1, 31, 1.0, 0.5, 0.001, 16) as p:
+        u = np.full((17, 31), 7.0)
+        info = mk.mk_solve(p.handle, np.zeros(31), u, mk.make_opts(levels=2, nu=(2,), n_cgs=4))
+        assert not u.any() and info.iterations == 0
+
+
+def test_device_pointers_and_stream():
+    torch = pytest.importorskip("torch")
+    P = SMALL["1d_n63_T"]()
+    ref = O.theta_march(1, P.nx, 1, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)
+    s = torch.cuda.Stream()
+    with _prob(P) as p, torch.cuda.stream(s):
+        u0 = torch.from_numpy(P.u0).cuda()
+        u = torch.empty((P.nt + 1, P.nx), dtype=torch.float64, device="cuda")
+        mk.mk_solve(p.handle, u0, u, _opts(P.schedule, precision="mixed"))
+        s.synchronize()
+        assert O.max_rel_error(u.cpu().numpy(), ref) <= 1e-8
+
+
+# --------------------------------------------------------------------------- full sizes
+def test_full_size_1d_small_workload_fp64():
+    P = W.heat1d_small()
+    ref = O.theta_march(1, P.nx, 1, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)
+    with _prob(P) as p:
+        u = np.empty_like(ref)
+        info = mk.mk_solve(p.handle, P.u0, u, _opts(P.schedule, tol=P.tol))
+        assert O.max_rel_error(u, ref) <= 1e-10, info.iterations
+
+
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_full_size_1d_large_workload(precision, bound):
+    """n = 1023, n_t = 8192, theta = 1, 5 levels: the launch configuration the bench times."""
+    P = W.heat1d_large(precision=precision)
+    ref = O.theta_march(1, P.nx, 1, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)
+    with _prob(P) as p:
+        u = np.empty_like(ref)
+        info = mk.mk_solve(p.handle, P.u0, u, _opts(P.schedule, precision=precision, tol=1e-12))
+        assert O.max_rel_error(u, ref) <= bound, info.iterations
+        um = np.empty_like(ref)
+        mk.mk_march(p.handle, P.u0, um)
+        # 8192 dependent steps: PCR and the oracle's Thomas sweep round differently
+        assert O.max_rel_error(um, ref) <= 1e-11
+
+
+def test_full_size_2d_workload_sampled():
+    """255 x 255, n_t = 1024, TS coarsening, mixed precision.  The oracle marches the first
+    24 steps (sampled outputs) and checks the residual of the whole GPU solution."""
+    P = W.heat2d_large()
+    with _prob(P) as p:
+        u = np.empty((P.nt + 1, P.ny, P.nx))
+        info = mk.mk_solve(p.handle, P.u0, u, _opts(P.schedule, precision="mixed", tol=1e-12))
+    ks = 24
+    ref = O.theta_march(2, P.nx, P.ny, ks, P.tau, P.theta, P.dt, P.u0, None)
+    assert O.max_rel_error(u[:ks + 1], ref) <= 1e-8, info.iterations
+    lv = O.build_levels(2, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, (), (), "one")[0]
+    f = O.assemble_rhs(P.u0, None, P.nt, P.theta, P.dt)
+    assert np.linalg.norm(f - lv.apply_A(u)) / np.linalg.norm(f) <= 1e-11
