@@ -1,0 +1,320 @@
+"""Benchmark: MK time-to-solution on one GB300 (or N replicas, one per GPU).
+
+Workload: 1D heat equation, n = 1023 interior points, theta = 1, n_t = 8192, T = 1, tau = 1,
+seeded u_0 (8 smooth modes) and a 4-mode space-time source; 5 time levels (nu = 2),
+16 decoupled coarsest slabs, inner FGMRES iterations 2,2,1, mixed precision (FP32 cycle,
+FP64 outer).  One step = one complete solve A_h u = f_h to the tolerance, inputs resident in
+HBM, L2 flushed (256 MB write) between steps.
+
+Printed: one JSON line (rank 0).  Beside the headline (mixed MK) it reports the FP64 MK and
+the GPU sequential theta-march on the same problem, the error of each against the CPU
+oracle, a kernel-class roofline from CUDA events, the oracle's own time on the host cores,
+and an end-to-end figure through host buffers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "MK time-to-solution at 1e-8 rel err vs GPU θ-march; HBM GB/s vs roofline"
+WORKLOAD = "heat1d_n1023_nt8192_theta1_T1_L5_nu2_ncgs16"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = max(smax, float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args, world, rank):
+    """The oracle (sequential FP64 theta-march in plain C) on the host cores."""
+    if rank != 0:
+        return
+    import oracle as O
+    P = W.heat1d_large()
+    f = O.assemble_rhs(P.u0, P.g, P.nt, P.theta, P.dt)
+    lv = O.build_levels(1, P.nx, 1, P.nt, P.tau, P.theta, P.dt, (), (), "one")[0]
+    for _ in range(args.warmup):
+        O.march(lv, f)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.theta_march(1, P.nx, 1, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)
+        times.append(time.perf_counter() - t0)
+    v = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "solver": "sequential theta-march (Thomas)"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": "full workload (RHS assembly + 8192 Thomas steps) per step"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mk", choices=["mk", "reference"])
+    ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--restart", type=int, default=40)
+    ap.add_argument("--no-aux", action="store_true", help="skip the secondary paths")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = _dist()
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import paper_2401_00228_gb300 as mk
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    P = W.heat1d_large(seed=1)
+    s = P.schedule
+
+    def opts(precision):
+        return mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner,
+                            n_cgs=s.n_cgs, tol=args.tol, restart=args.restart, precision=precision)
+
+    o_mixed, o_fp64 = opts("mixed"), opts("fp64")
+    g_dev = torch.from_numpy(P.g).to(dev)
+    u0_dev = torch.from_numpy(P.u0).to(dev)
+    u_dev = torch.empty((P.nt + 1, P.nx), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    prob = mk.Problem(1, P.nx, P.tau, P.theta, P.dt, P.nt, g_dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(o, steps, warm):
+        infos = []
+        for _ in range(warm):
+            mk.mk_solve(prob.handle, u0_dev, u_dev, o)
+        barrier()
+        times = []
+        l0 = mk.mk_kernel_launch_count()
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(mk.mk_solve(prob.handle, u0_dev, u_dev, o))
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        barrier()
+        launches = mk.mk_kernel_launch_count() - l0
+        return times, infos, launches
+
+    # ---------------- headline: mixed-precision MK ----------------
+    clocks = Clocks(local)
+    clocks.start()
+    t_mixed, inf_mixed, launches = timed(o_mixed, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms_mixed = statistics.mean(t_mixed)
+    if dist is not None:
+        t = torch.tensor([ms_mixed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_mixed = float(t.item())
+    u_mixed = u_dev.cpu().numpy().copy()
+
+    line = {"metric": METRIC, "value": ms_mixed / 1e3, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 cycle + f64 outer", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": P.nx, "nt": P.nt, "theta": P.theta,
+                       "levels": s.levels, "nu": list(s.nu), "m_inner": list(s.m_inner),
+                       "n_cgs": s.n_cgs, "restart": args.restart, "tol": args.tol,
+                       "precision": "mixed", "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MB write)"},
+            "gpu_launches": int(launches),
+            "iterations": int(inf_mixed[-1].iterations)}
+    if clk:
+        line["clocks"] = clk
+
+    if rank == 0 and not args.no_aux:
+        # ---------------- secondary paths ----------------
+        t_fp64, inf_fp64, _ = timed(o_fp64, 2, 1)
+        u_fp64 = u_dev.cpu().numpy().copy()
+        tm = []
+        for i in range(4):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mk.mk_march(prob.handle, u0_dev, u_dev)
+            e1.record(stream)
+            e1.synchronize()
+            if i > 0:
+                tm.append(e0.elapsed_time(e1))
+        u_march = u_dev.cpu().numpy().copy()
+
+        # ---------------- roofline: kernel-class timing of one profiled solve ----------------
+        lib = mk.lib()
+        lib.mk_set_profiling(1)
+        mk.mk_solve(prob.handle, u0_dev, u_dev, o_mixed)     # capture with timing events
+        lib.mk_profile_reset()
+        mk.mk_solve(prob.handle, u0_dev, u_dev, o_mixed)
+        torch.cuda.synchronize(dev)
+        import ctypes
+        rows = []
+        for cls in range(9):
+            for lvl in range(0, 13):
+                ms_, by_, n_ = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+                lib.mk_profile_read(cls, lvl, ctypes.byref(ms_), ctypes.byref(by_), ctypes.byref(n_))
+                if n_.value:
+                    rows.append((ms_.value, by_.value, n_.value, lib.mk_profile_class_name(cls).decode(), lvl))
+        lib.mk_set_profiling(0)
+        rows.sort(reverse=True)
+        total_ms = sum(r[0] for r in rows)
+        peak, peak_kind = _peaks()
+        top = rows[0]
+        ach = top[1] / (top[0] * 1e-3) / 1e9
+        line["roofline"] = {"bound": "hbm", "kernel": f"{top[3]}@level{top[4]}",
+                            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                            "peak_kind": peak_kind, "traffic": None,
+                            "launches": int(top[2]), "avg_launch_us": top[0] / top[2] * 1e3}
+        line["kernel_classes"] = [
+            {"kernel": f"{r[3]}@level{r[4]}", "ms": round(r[0], 4), "share": round(r[0] / total_ms, 4),
+             "launches": int(r[2]), "GBps": round(r[1] / (r[0] * 1e-3) / 1e9, 1)} for r in rows[:10]]
+
+        # ---------------- e2e through host buffers ----------------
+        g_h = torch.from_numpy(P.g).pin_memory()
+        u0_h = torch.from_numpy(P.u0).pin_memory()
+        u_h = torch.empty((P.nt + 1, P.nx), dtype=torch.float64).pin_memory()
+        te = []
+        for i in range(args.warmup + args.steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            mk.mk_set_source(prob.handle, g_h)
+            mk.mk_solve(prob.handle, u0_h, u_h, o_mixed)
+            t1 = time.perf_counter()
+            if i >= args.warmup:
+                te.append(t1 - t0)
+        line["e2e"] = {"value": statistics.mean(te), "unit": "s",
+                       "h2d_bytes_per_step": int(P.g.nbytes + P.u0.nbytes),
+                       "d2h_bytes_per_step": int(u_h.numel() * 8)}
+
+        # ---------------- CPU oracle (host cores) and errors ----------------
+        import oracle as O
+        tc = []
+        ref = None
+        for _ in range(3):
+            t0 = time.perf_counter()
+            ref = O.theta_march(1, P.nx, 1, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)
+            tc.append(time.perf_counter() - t0)
+        line["cpu_baseline"] = {"value": statistics.median(tc), "unit": "s", "cores": 1, "kind": "oracle",
+                                "sample": "full workload solved 3 times (sequential FP64 theta-march, "
+                                          "Thomas algorithm, plain C)"}
+        line["paths"] = {
+            "mk_mixed": {"s": ms_mixed / 1e3, "iterations": int(inf_mixed[-1].iterations),
+                         "rel_residual": inf_mixed[-1].rel_residual,
+                         "max_rel_err": O.max_rel_error(u_mixed, ref)},
+            "mk_fp64": {"s": statistics.mean(t_fp64) / 1e3, "iterations": int(inf_fp64[-1].iterations),
+                        "rel_residual": inf_fp64[-1].rel_residual,
+                        "max_rel_err": O.max_rel_error(u_fp64, ref)},
+            "march_gpu_fp64": {"s": statistics.mean(tm) / 1e3, "max_rel_err": O.max_rel_error(u_march, ref)},
+            "oracle_cpu": {"s": statistics.median(tc)},
+        }
+    prob.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

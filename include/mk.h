@@ -106,8 +106,21 @@ const char *mk_status_string(mk_status s);
 /* Last CUDA error string seen by the library on this thread ("" if none). */
 const char *mk_last_cuda_error(void);
 
-/* Number of library kernels launched since the library was loaded (all threads). */
+/* Number of library kernels launched since the library was loaded (all threads).  Kernels
+   replayed from a captured CUDA graph count once per replay. */
 int64_t mk_kernel_launch_count(void);
+
+/* Kernel-class timing (no counterpart in the paper; measurement support).  When on, every
+   library kernel launch is bracketed by a pair of CUDA events on its stream (inside captured
+   graphs as event nodes), and the device time, algorithmic bytes and launch count are
+   accumulated per (class, level) for launches that did work.  Classes: 0 restrict,
+   1 interp_correct, 2 multidot, 3 update, 4 slab, 5 residual, 6 combine, 7 march, 8 other.
+   Level is 1-based (the level the kernel runs on; 0 when not level-specific).
+   Toggling invalidates captured graphs (they are re-captured on the next solve). */
+void mk_set_profiling(int32_t on);
+void mk_profile_reset(void);
+mk_status mk_profile_read(int32_t cls, int32_t level, double *ms, double *bytes, int64_t *launches);
+const char *mk_profile_class_name(int32_t cls);
 
 /*
  * mk_create_problem -- set up A_h (Eq. (finesys)) for the theta-scheme with step dt over

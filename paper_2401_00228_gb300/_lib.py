@@ -50,6 +50,11 @@ SIGNATURES = {
     "mk_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mk_last_cuda_error": (ctypes.c_char_p, []),
     "mk_kernel_launch_count": (ctypes.c_int64, []),
+    "mk_set_profiling": (None, [_I]),
+    "mk_profile_reset": (None, []),
+    "mk_profile_read": (ctypes.c_int, [_I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    "mk_profile_class_name": (ctypes.c_char_p, [_I]),
     "mk_create_problem": (ctypes.c_int, [ctypes.POINTER(mk_stencil), _D, _D, _I, _P, ctypes.POINTER(_P)]),
     "mk_set_source": (ctypes.c_int, [_P, _P, _P]),
     "mk_destroy": (None, [_P]),

@@ -10,11 +10,14 @@
 namespace mk {
 
 int g_num_sms = 0;
-static std::atomic<int64_t> g_launches{0};
 static thread_local std::string g_last_err;
 
-void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 void set_cuda_error(cudaError_t e) { g_last_err = cudaGetErrorString(e); }
+
+int64_t launches_total();
+void prof_set_enabled(bool on);
+void prof_reset();
+bool prof_read(int cls, int level, double &ms, double &bytes, int64_t &n);
 
 cudaError_t slab_set_attributes();
 
@@ -155,7 +158,28 @@ const char *mk_status_string(mk_status s) {
 
 const char *mk_last_cuda_error(void) { return g_last_err.c_str(); }
 
-int64_t mk_kernel_launch_count(void) { return g_launches.load(); }
+int64_t mk_kernel_launch_count(void) { return launches_total(); }
+
+void mk_set_profiling(int32_t on) { prof_set_enabled(on != 0); }
+
+void mk_profile_reset(void) { prof_reset(); }
+
+mk_status mk_profile_read(int32_t cls, int32_t level, double *ms, double *bytes, int64_t *launches) {
+    double a = 0.0, b = 0.0;
+    int64_t n = 0;
+    if (!prof_read(cls, level, a, b, n)) return MK_ERR_INVALID;
+    if (ms) *ms = a;
+    if (bytes) *bytes = b;
+    if (launches) *launches = n;
+    return MK_OK;
+}
+
+const char *mk_profile_class_name(int32_t cls) {
+    static const char *names[] = {"restrict", "interp_correct", "multidot", "update", "slab",
+                                  "residual", "combine", "march", "other"};
+    if (cls < 0 || cls >= PROF_NCLASS) return "";
+    return names[cls];
+}
 
 mk_status mk_problem_shape(const mk_problem *p, int32_t *dim, int32_t *nx, int32_t *ny,
                            int32_t *nt, double *theta, double *dt, double *tau) {

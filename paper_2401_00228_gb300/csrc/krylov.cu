@@ -49,33 +49,36 @@ __global__ void __launch_bounds__(KR_THREADS) k_multidot(int64_t len, const TW *
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = threadIdx.x; t < nslots * KR_WARPS; t += KR_THREADS) acc[t] = 0.0;
     __syncthreads();
+    // arithmetic in the storage type (FP32 for the inner levels of the mixed cycle); the
+    // per-warp results are accumulated across tiles in FP64
+    using Ta = TV;
     const TW *src = second ? (const TW *)(V + (int64_t)(j + 1) * vstride) : W;
     for (int64_t base = (int64_t)blockIdx.x * MD_TILE; base < len;
          base += (int64_t)gridDim.x * MD_TILE) {
-        double w[MD_EPT];
+        Ta w[MD_EPT];
 #pragma unroll
         for (int q = 0; q < MD_EPT; ++q) {
             int64_t e = base + threadIdx.x + q * KR_THREADS;
-            w[q] = (e < len) ? (double)src[e] : 0.0;
+            w[q] = (e < len) ? (Ta)src[e] : (Ta)0;
         }
         if (!second) {
-            double s = 0.0;
+            Ta s = 0;
 #pragma unroll
             for (int q = 0; q < MD_EPT; ++q) s += w[q] * w[q];
-            s = warp_sum(s);
-            if (lane == 0) acc[nv * KR_WARPS + warp] += s;
+            s = warp_sum_t(s);
+            if (lane == 0) acc[nv * KR_WARPS + warp] += (double)s;
         }
         for (int i = 0; i < nv; ++i) {
             const TV *vi = V + (int64_t)i * vstride;
-            double s = 0.0;
+            Ta s = 0;
 #pragma unroll
             for (int q = 0; q < MD_EPT; ++q) {
                 int64_t e = base + threadIdx.x + q * KR_THREADS;
-                double vv = (e < len) ? (double)vi[e] : 0.0;
+                Ta vv = (e < len) ? vi[e] : (Ta)0;
                 s += w[q] * vv;
             }
-            s = warp_sum(s);
-            if (lane == 0) acc[i * KR_WARPS + warp] += s;
+            s = warp_sum_t(s);
+            if (lane == 0) acc[i * KR_WARPS + warp] += (double)s;
         }
     }
     __syncthreads();
@@ -197,20 +200,22 @@ __global__ void __launch_bounds__(KR_THREADS) k_update(int64_t len, const TW *__
                                                        const int *__restrict__ done) {
     if (done && *done) return;
     if (second && !ks.flags[2]) return;
-    __shared__ double c[MK_MAX_RESTART + 1];
+    // arithmetic in the storage type (FP32 on the inner levels of the mixed cycle)
+    using Ta = TV;
+    __shared__ Ta c[MK_MAX_RESTART + 1];
     const int nv = j + 1;
-    for (int i = threadIdx.x; i < nv; i += KR_THREADS) c[i] = ks.tmp()[i] * ks.sigma()[i];
+    for (int i = threadIdx.x; i < nv; i += KR_THREADS) c[i] = (Ta)(ks.tmp()[i] * ks.sigma()[i]);
     __syncthreads();
     TV *out = V + (int64_t)(j + 1) * vstride;
-    double acc = 0.0;
+    Ta acc = 0;
     for (int64_t e = (int64_t)blockIdx.x * KR_THREADS + threadIdx.x; e < len;
          e += (int64_t)gridDim.x * KR_THREADS) {
-        double val = second ? (double)out[e] : (double)W[e];
-        for (int i = 0; i < nv; ++i) val -= c[i] * (double)V[(int64_t)i * vstride + e];
+        Ta val = second ? (Ta)out[e] : (Ta)W[e];
+        for (int i = 0; i < nv; ++i) val -= c[i] * (Ta)V[(int64_t)i * vstride + e];
         if (write_next) out[e] = (TV)val;
         acc += val * val;
     }
-    double bs = block_sum(acc);
+    double bs = block_sum((double)acc);
     if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
     if (last_block_ticket(rs.counter)) {
         double tot = sum_partials(rs.partials, gridDim.x);
@@ -261,10 +266,13 @@ void launch_multidot(int64_t len, const TW *W, const TV *V, int64_t vstride, int
                      const ReduceScratch &rs, KState ks, bool second_pass, const int *done,
                      cudaStream_t s) {
     int grid = krylov_grid(len, MD_TILE);
+    const double alg_n = prof_alg_n() > 0 ? prof_alg_n() : (double)len;
     size_t shm = sizeof(double) * (size_t)(j + 2) * KR_WARPS;
     if (shm < sizeof(double) * (size_t)(j + 2)) shm = sizeof(double) * (size_t)(j + 2);
+    prof_begin(s);
     k_multidot<TW, TV><<<grid, KR_THREADS, shm, s>>>(len, W, V, vstride, j, rs, ks,
                                                       second_pass ? 1 : 0, done);
+    prof_end(s, PROF_MULTIDOT, (double)(j + 2) * alg_n * sizeof(TV));
     count_launch();
 }
 
@@ -272,17 +280,23 @@ template <typename TW, typename TV>
 void launch_update(int64_t len, const TW *W, TV *V, int64_t vstride, int j, bool write_next,
                    const ReduceScratch &rs, KState ks, int mode, bool second_pass,
                    const int *done, cudaStream_t s) {
+    const double alg_n = prof_alg_n() > 0 ? prof_alg_n() : (double)len;
     int grid = krylov_grid(len, (int64_t)KR_THREADS * 8);
+    prof_begin(s);
     k_update<TW, TV><<<grid, KR_THREADS, 0, s>>>(len, W, V, vstride, j, write_next ? 1 : 0, rs,
                                                   ks, mode, second_pass ? 1 : 0, done);
+    prof_end(s, PROF_UPDATE, (double)(j + 2 + (write_next ? 1 : 0)) * alg_n * sizeof(TV));
     count_launch();
 }
 
 template <typename TX>
 void launch_combine(int64_t len, double *u, const TX *X, int64_t xstride, KState ks,
                     cudaStream_t s) {
+    const double alg_n = prof_alg_n() > 0 ? prof_alg_n() : (double)len;
     int grid = krylov_grid(len, (int64_t)KR_THREADS * 8);
+    prof_begin(s);
     k_combine<TX><<<grid, KR_THREADS, 0, s>>>(len, u, X, xstride, ks);
+    prof_end(s, PROF_COMBINE, (double)alg_n * (16.0 + (double)ks.m * sizeof(TX)));
     count_launch();
 }
 

@@ -76,11 +76,39 @@ void tri_eigen(const Tri &L, std::vector<double> &lam, std::vector<double> &S,
                std::vector<double> &Sinv);
 
 // ---------------------------------------------------------------------------------------
-// Launch bookkeeping.
+// Launch bookkeeping and kernel-class timing.
+//   count_launch(): one library kernel launched (or captured into a graph: captured
+//   launches are counted once per replay of the graph).
+//   prof_begin()/prof_end(): when profiling is on, a pair of CUDA events brackets the
+//   launch on its stream (inside a captured graph the events become graph nodes); the
+//   pair carries the kernel class, the level, the Arnoldi index j of the enclosing outer
+//   iteration (-1 outside iterations) and the launch's algorithmic bytes.
 // ---------------------------------------------------------------------------------------
 extern int g_num_sms;
 void count_launch(int n = 1);
 void set_cuda_error(cudaError_t e);
+
+enum ProfClass {
+    PROF_RESTRICT = 0, PROF_INTERP, PROF_MULTIDOT, PROF_UPDATE, PROF_SLAB, PROF_RESIDUAL,
+    PROF_COMBINE, PROF_MARCH, PROF_OTHER, PROF_NCLASS
+};
+struct ProfPair {
+    cudaEvent_t a, b;
+    int cls, level, j;
+    double bytes;
+};
+bool prof_enabled();
+void prof_begin(cudaStream_t s);
+void prof_end(cudaStream_t s, int cls, double bytes);
+void prof_set_context(int level, int j, double alg_n = 0.0);
+double prof_alg_n();   // interior element count of the current level (0 = unknown)
+// destination of the pairs recorded by this thread (nullptr: the transient list)
+void prof_set_sink(std::vector<ProfPair> *sink);
+// accumulate pairs whose outer iteration index j < j_limit (j = -1 always counts)
+void prof_accumulate(const std::vector<ProfPair> &pairs, int j_limit);
+void prof_accumulate_transient();
+// while capturing, launches are counted into *c instead of the global counter
+void set_capture_counter(int64_t *c);
 
 // Two-stage deterministic reduction scratch: per-block partials + arrival counter.
 struct ReduceScratch {

@@ -17,6 +17,13 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Sum over the block; result valid in thread 0.  Works for any blockDim <= 1024.
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double red_smem[32];

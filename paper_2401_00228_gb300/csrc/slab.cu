@@ -128,6 +128,7 @@ static void slab_1d_launch(const Geom &g, double b, SpaceOp<T> L, const T *alpha
     if (nt_threads < 32) nt_threads = 32;
     int U = (npad + nt_threads - 1) / nt_threads;
     size_t shm = sizeof(T) * (size_t)(3 * npad + 2);
+    prof_begin(s);
     if (U == 1)
         k_slab_1d<T, 1><<<nslabs, nt_threads, shm, s>>>(g, (T)b, L, alpha, gamma, binv, npad, nlev,
                                                        steps, coupled, r, x, done);
@@ -137,6 +138,7 @@ static void slab_1d_launch(const Geom &g, double b, SpaceOp<T> L, const T *alpha
     else
         k_slab_1d<T, 4><<<nslabs, nt_threads, shm, s>>>(g, (T)b, L, alpha, gamma, binv, npad, nlev,
                                                        steps, coupled, r, x, done);
+    prof_end(s, done ? PROF_SLAB : PROF_MARCH, 2.0 * sizeof(T) * (double)g.interior());
     count_launch();
 }
 
@@ -284,8 +286,10 @@ static void slab_2d_launch(const Geom &g, double a, double b, SpaceOp<T> L, cons
     int threads = g.nx * g.ny;
     threads = ((threads + 31) / 32) * 32;
     if (threads > 1024) threads = 1024;
+    prof_begin(s);
     k_slab_2d<T><<<nslabs, threads, shm, s>>>(g, (T)a, (T)b, L, Sx, Sxi, lamx, Sy, Syi, lamy, steps,
                                               coupled, r, x, done);
+    prof_end(s, done ? PROF_SLAB : PROF_MARCH, 2.0 * sizeof(T) * (double)g.interior());
     count_launch();
 }
 

@@ -13,6 +13,8 @@
 
 namespace mk {
 
+int64_t launches_total();
+
 bool OptsKey::operator==(const OptsKey &o) const {
     if (levels != o.levels || n_cgs != o.n_cgs || mu_mode != o.mu_mode ||
         precision != o.precision || restart != o.restart || mu_value != o.mu_value)
@@ -37,10 +39,6 @@ static OptsKey make_key(const mk_solve_opts &o) {
     }
     for (int i = 0; i < o.levels - 2 && i < MK_MAX_LEVELS; ++i) k.m_inner[i] = o.m_inner[i];
     return k;
-}
-
-Hierarchy::~Hierarchy() {
-    if (graph) cudaGraphExecDestroy(graph);
 }
 
 mk_status validate_opts(const Problem &P, const mk_solve_opts &o) {
@@ -280,6 +278,14 @@ static void enqueue_inner_solve(Hierarchy &H, int l, const int *done, cudaStream
 
 // x_j = Q_l v_j and w = A_l x_j; Tv = type of level l's basis, Tx = type of its X,
 // Tw/Tcw = type and arithmetic of w.
+// Index of the outer FGMRES iteration being enqueued (-1 outside iterations); every kernel
+// launched for it, on any level, is attributed to it by the kernel-class timing.
+static thread_local int t_outer_j = -1;
+
+static void set_ctx(const Level &L, int level) {
+    prof_set_context(level + 1, t_outer_j, (double)L.g.interior());
+}
+
 template <typename Tc, typename Tv, typename Tx, typename Tw, typename Tcw>
 static void cycle_step_t(Hierarchy &H, int l, int j, const int *done, cudaStream_t s) {
     Level &L = *H.lv[l];
@@ -287,9 +293,11 @@ static void cycle_step_t(Hierarchy &H, int l, int j, const int *done, cudaStream
     const Tv *vj = L.V.as<Tv>() + (int64_t)j * L.stride;
     const double *sig = L.ks.sigma() + j;
     // 4.1-4.2: restriction of the shifted residual of the basis vector
+    set_ctx(L, l);
     if (C.coarsest) {
         launch_restrict<Tv, Tc, Tc>(L.g, C.g, L.nu, L.space, L.w, op_of<Tc>(L), vj, sig,
                                     C.R.as<Tc>(), H.rs, 0, KState{nullptr, nullptr, 0}, done, s);
+        set_ctx(C, l + 1);
         enqueue_coarsest_t<Tc>(H, done, s);                          // 4.3 (decoupled slabs)
     } else {
         launch_restrict<Tv, Tc, Tc>(L.g, C.g, L.nu, L.space, L.w, op_of<Tc>(L), vj, sig,
@@ -297,6 +305,7 @@ static void cycle_step_t(Hierarchy &H, int l, int j, const int *done, cudaStream
         enqueue_inner_solve<Tc>(H, l + 1, done, s);                  // 4.3 (recursion)
     }
     // 4.4-4.5 and step 5: x = v - Z vt, w = A x
+    set_ctx(L, l);
     const Tc *Xc = C.X.as<Tc>();
     const double *yc = C.coarsest ? nullptr : C.ks.y();
     int mc = C.coarsest ? 1 : C.m;
@@ -311,6 +320,7 @@ static void enqueue_inner_solve(Hierarchy &H, int l, const int *done, cudaStream
     const int64_t len = L.g.len;
     for (int j = 0; j < L.m; ++j) {
         cycle_step_t<Tc, Tc, Tc, Tc, Tc>(H, l, j, done, s);
+        set_ctx(L, l);
         launch_multidot<Tc, Tc>(len, L.W.as<Tc>(), L.V.as<Tc>(), L.stride, j, H.rs, L.ks, false,
                                 done, s);
         launch_update<Tc, Tc>(len, L.W.as<Tc>(), L.V.as<Tc>(), L.stride, j, j < L.m - 1, H.rs, L.ks,
@@ -337,7 +347,9 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s) {
     double *V = L.V.as<double>();
     double *W = L.W.as<double>();
     for (int j = 0; j < L.m; ++j) {
+        t_outer_j = j;
         enqueue_cycle_step(H, 0, j, done, s);
+        set_ctx(L, 0);
         launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, false, done, s);
         launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, UPD_OUTER, false,
                                       done, s);
@@ -345,6 +357,8 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s) {
         launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, UPD_OUTER, true,
                                       done, s);
     }
+    t_outer_j = -1;
+    set_ctx(L, 0);
     if (H.precision == 0)
         launch_combine<double>(len, H.u.as<double>(), L.X.as<double>(), L.stride, L.ks, s);
     else
@@ -353,12 +367,53 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s) {
                     EPI_OUTER_START, s);
 }
 
+void release_pairs(std::vector<ProfPair> &pairs);
+void add_launches(int64_t n);
+
+Hierarchy::~Hierarchy() {
+    if (graph) cudaGraphExecDestroy(graph);
+    release_pairs(graph_pairs);
+}
+
+static mk_status capture_cycle(Problem &P, Hierarchy &H) {
+    if (H.graph) {
+        cudaGraphExecDestroy(H.graph);
+        H.graph = nullptr;
+    }
+    release_pairs(H.graph_pairs);
+    H.graph_kernels = 0;
+    H.graph_profiled = prof_enabled();
+    cudaStream_t cs;
+    MKCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    MKCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    set_capture_counter(&H.graph_kernels);
+    prof_set_sink(&H.graph_pairs);
+    enqueue_outer_cycle(P, H, cs);
+    prof_set_sink(nullptr);
+    set_capture_counter(nullptr);
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (ce != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        set_cuda_error(ce);
+        return MK_ERR_CUDA;
+    }
+    ce = cudaGraphInstantiate(&H.graph, graph, 0);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (ce != cudaSuccess) {
+        set_cuda_error(ce);
+        H.graph = nullptr;
+        return MK_ERR_CUDA;
+    }
+    return MK_OK;
+}
+
 mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const double *f_padded,
                     mk_solve_info *info, cudaStream_t s) {
     Level &L = *H.lv[0];
     const int64_t len = L.g.len;
-    int launches0 = 0;
-    (void)launches0;
+    const int64_t launches_start = launches_total();
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     MKCK(cudaEventCreate(&e0));
     MKCK(cudaEventCreate(&e1));
@@ -371,46 +426,44 @@ mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const doub
     tolbuf = o.tol;
     MKCK(cudaMemcpyAsync(L.ks.misc() + 7, &tolbuf, sizeof(double), cudaMemcpyHostToDevice, s));
     // r_0 = f (u^0 = 0): ||f||, tol * ||f||, v_1
+    t_outer_j = -1;
+    set_ctx(L, 0);
     launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<double>(), H.rs,
                     0, L.ks, EPI_OUTER_INIT, s);
-    // capture one restart cycle into a graph (once per hierarchy)
-    if (o.use_graph && !H.graph) {
-        cudaStream_t cs;
-        MKCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t graph;
-        MKCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        enqueue_outer_cycle(P, H, cs);
-        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-        if (ce != cudaSuccess) {
-            cudaStreamDestroy(cs);
-            set_cuda_error(ce);
-            return MK_ERR_CUDA;
-        }
-        ce = cudaGraphInstantiate(&H.graph, graph, 0);
-        cudaGraphDestroy(graph);
-        cudaStreamDestroy(cs);
-        if (ce != cudaSuccess) {
-            set_cuda_error(ce);
-            H.graph = nullptr;
-            return MK_ERR_CUDA;
-        }
+    // one restart cycle as a CUDA graph (captured once per hierarchy and profiling mode)
+    if (o.use_graph && (!H.graph || H.graph_profiled != prof_enabled())) {
+        mk_status st = capture_cycle(P, H);
+        if (st != MK_OK) return st;
     }
-    int hflags[8];
-    double hmisc[8];
+    int hflags[8] = {0};
+    double hmisc[8] = {0};
     mk_status status = MK_OK;
     int cycles = 0;
-    int64_t launches_before = 0;
-    (void)launches_before;
+    int iters_before = 0;
+    std::vector<ProfPair> cycle_pairs;
     for (;;) {
         if (o.use_graph) {
             MKCK(cudaGraphLaunch(H.graph, s));
+            add_launches(H.graph_kernels);
         } else {
+            prof_set_sink(&cycle_pairs);
             enqueue_outer_cycle(P, H, s);
+            prof_set_sink(nullptr);
         }
         ++cycles;
         MKCK(cudaMemcpyAsync(hflags, L.ks.flags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
         MKCK(cudaMemcpyAsync(hmisc, L.ks.misc(), sizeof(hmisc), cudaMemcpyDeviceToHost, s));
         MKCK(cudaStreamSynchronize(s));
+        // kernel-class timing: only the iterations of this cycle that did work
+        const int worked = hflags[4] - iters_before;
+        iters_before = hflags[4];
+        if (prof_enabled()) {
+            if (o.use_graph) prof_accumulate(H.graph_pairs, worked);
+            else {
+                prof_accumulate(cycle_pairs, worked);
+                release_pairs(cycle_pairs);
+            }
+        }
         if (hflags[3]) {
             status = MK_ERR_NONFINITE;
             break;
@@ -423,6 +476,7 @@ mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const doub
     }
     MKCK(cudaEventRecord(e1, s));
     MKCK(cudaEventSynchronize(e1));
+    if (prof_enabled()) prof_accumulate_transient();
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
@@ -434,6 +488,7 @@ mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const doub
         info->rel_residual = hmisc[3] > 0.0 ? hmisc[4] / hmisc[3] : 0.0;
         info->solve_ms = ms;
         info->levels = (int)H.lv.size();
+        info->kernel_launches = (int32_t)(launches_total() - launches_start);
     }
     return status;
 }

@@ -69,7 +69,9 @@ struct Hierarchy {
     DevMem partials, counters;
     ReduceScratch rs{nullptr, nullptr, 0};
     cudaGraphExec_t graph = nullptr;
-    cudaStream_t graph_stream = nullptr;
+    bool graph_profiled = false;        // captured with kernel-class timing events
+    int64_t graph_kernels = 0;          // kernels in one replay of the graph
+    std::vector<ProfPair> graph_pairs;  // timing events inside the graph
     ~Hierarchy();
 };
 

@@ -32,11 +32,14 @@ __device__ __forceinline__ Tc lap_at(const Tin *__restrict__ x, int64_t idx, int
 }
 
 static int choose_kc(int64_t npts, int nsteps) {
-    // enough threads to fill the GPU a few times over; at most 32 steps per thread
+    // enough threads to fill the GPU a few times over; at most 32 steps per thread, and
+    // never more than 60000 blocks in a launch (the reduction partials hold 65536)
     int64_t target = (int64_t)g_num_sms * 2048;
     int64_t kc = (npts * nsteps) / (target > 0 ? target : 1);
     if (kc < 1) kc = 1;
     if (kc > 32) kc = 32;
+    int64_t blocks_per_chunk = (npts + 255) / 256 + 1;
+    while (blocks_per_chunk * ((nsteps + kc - 1) / kc) > 60000) ++kc;
     return (int)kc;
 }
 
@@ -239,10 +242,12 @@ void launch_residual(const Geom &g, const Weights &w, SpaceOp<double> L, const d
     int kc = choose_kc(g.npts(), g.nt + 1);
     int nch = (g.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(g.dim, g.nx, g.ny, nch);
+    prof_begin(s);
     if (g.dim == 1)
         k_residual<1><<<l.grid, l.block, 0, s>>>(g, w.a, w.b, L, f, u, r, kc, rs, slot, ks, epi);
     else
         k_residual<2><<<l.grid, l.block, 0, s>>>(g, w.a, w.b, L, f, u, r, kc, rs, slot, ks, epi);
+    prof_end(s, PROF_RESIDUAL, 3.0 * 8.0 * (double)g.interior());
     count_launch();
 }
 
@@ -357,12 +362,14 @@ void launch_restrict(const Geom &gf, const Geom &gc, int nu, bool space, const W
 #define MK_RESTRICT(D, S) \
     k_restrict<D, S, Tin, Tout, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, nu, a, b, mu, L, v, sigma, \
                                                                 vhat, kc, rs, slot, ks_c, done)
+    prof_begin(s);
     if (gf.dim == 1) {
         if (space) MK_RESTRICT(1, true); else MK_RESTRICT(1, false);
     } else {
         if (space) MK_RESTRICT(2, true); else MK_RESTRICT(2, false);
     }
 #undef MK_RESTRICT
+    prof_end(s, PROF_RESTRICT, (double)gf.interior() * sizeof(Tin) + (double)gc.interior() * sizeof(Tout));
     count_launch();
 }
 
@@ -377,9 +384,9 @@ struct XEval {
     const Tv *v;
     Tx sigma;
     const Tz *Xc;
-    int mc;
+    int mc;             // 0: a single coarse vector with coefficient 1
     int64_t xc_stride;
-    const double *yc;
+    Tx y[MK_MAX_INNER]; // combination coefficients, converted once per thread
     Geom gf, gc;
     int nu;
 
@@ -391,11 +398,11 @@ struct XEval {
         int J = (SPACE && DIM == 2) ? (j >> 1) : j;
         int64_t cidx = gc.at(K, J, I);
         Tx zt;
-        if (yc == nullptr) {
+        if (mc == 0) {
             zt = (Tx)Xc[cidx];
         } else {
             zt = (Tx)0;
-            for (int m = 0; m < mc; ++m) zt += (Tx)yc[m] * (Tx)Xc[cidx + m * xc_stride];
+            for (int m = 0; m < mc; ++m) zt += y[m] * (Tx)Xc[cidx + m * xc_stride];
         }
         return sigma * (Tx)v[gf.at(k, j, i)] - zt;
     }
@@ -414,7 +421,16 @@ __global__ void __launch_bounds__(256) k_interp(Geom gf, Geom gc, int nu, Tc a, 
     int i, j, chunk;
     point_index<DIM>(i, j, chunk);
     if (i >= gf.nx || j >= gf.ny) return;
-    XEval<DIM, SPACE, Tv, Tz, Tx> X{v, sigma ? (Tx)(*sigma) : (Tx)1, Xc, mc, xc_stride, yc, gf, gc, nu};
+    XEval<DIM, SPACE, Tv, Tz, Tx> X;
+    X.v = v;
+    X.sigma = sigma ? (Tx)(*sigma) : (Tx)1;
+    X.Xc = Xc;
+    X.mc = yc ? mc : 0;
+    X.xc_stride = xc_stride;
+    for (int m = 0; m < MK_MAX_INNER; ++m) X.y[m] = (yc && m < mc) ? (Tx)yc[m] : (Tx)0;
+    X.gf = gf;
+    X.gc = gc;
+    X.nu = nu;
     const Tc *cx = L.x;
     const Tc *cy = L.y;
     auto lap = [&](int k, Tc c) -> Tc {
@@ -458,12 +474,15 @@ void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Wei
     k_interp<D, S, Tv, Tz, Tx, Tw, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, nu, a, b, L, v, sigma, \
                                                                   Xc, mc, xc_stride, yc, x, wout, \
                                                                   kc, done)
+    prof_begin(s);
     if (gf.dim == 1) {
         if (space) MK_INTERP(1, true); else MK_INTERP(1, false);
     } else {
         if (space) MK_INTERP(2, true); else MK_INTERP(2, false);
     }
 #undef MK_INTERP
+    prof_end(s, PROF_INTERP, (double)gf.interior() * (sizeof(Tv) + sizeof(Tx) + sizeof(Tw)) +
+                                 (double)mc * gc.interior() * sizeof(Tz));
     count_launch();
 }
 
