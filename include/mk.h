@@ -83,6 +83,9 @@ typedef struct mk_solve_opts {
                             coarsest slabs in FP32; level-1 residual, Arnoldi, least squares and the
                             true-residual check in FP64. */
     int32_t use_graph;   /* 1: capture each restart cycle in a CUDA graph (default 1) */
+    int32_t orth;        /* level-1 Arnoldi: 0 = one classical Gram-Schmidt pass; 1 = a second
+                            pass when the norm drops below 1/sqrt(2) of its value (default);
+                            2 = always two passes */
 } mk_solve_opts;
 
 typedef struct mk_solve_info {

@@ -141,6 +141,7 @@ void mk_default_opts(mk_solve_opts *o) {
     o->mu_value = 1.0;
     o->precision = 0;
     o->use_graph = 1;
+    o->orth = 1;
 }
 
 const char *mk_status_string(mk_status s) {

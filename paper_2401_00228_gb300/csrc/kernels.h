@@ -91,6 +91,7 @@ enum UpdateMode {
     UPD_REORTH = 1,     // request a second Gram-Schmidt pass when ||w'|| < ||w|| / sqrt(2)
     UPD_GIVENS = 2,     // outer level: Givens update, convergence test, y on completion
     UPD_INNER_LSQ = 4,  // inner level: least squares on the last iteration
+    UPD_REORTH_ALWAYS = 8,  // always request the second Gram-Schmidt pass
     UPD_OUTER = UPD_REORTH | UPD_GIVENS,
     UPD_INNER = UPD_INNER_LSQ
 };

@@ -147,7 +147,8 @@ __device__ void update_epilogue(double nrm2, KState ks, int j, int mode, int sec
         ks.flags[1] = 0;
         return;
     }
-    if (!second && (mode & UPD_REORTH) && nrm < 0.70710678118654752 * sqrt(misc[2])) {
+    if (!second && ((mode & UPD_REORTH_ALWAYS) ||
+                    ((mode & UPD_REORTH) && nrm < 0.70710678118654752 * sqrt(misc[2])))) {
         ks.flags[2] = 1;  // a second Gram-Schmidt pass follows
         return;
     }

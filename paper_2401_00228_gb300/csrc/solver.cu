@@ -17,7 +17,7 @@ int64_t launches_total();
 
 bool OptsKey::operator==(const OptsKey &o) const {
     if (levels != o.levels || n_cgs != o.n_cgs || mu_mode != o.mu_mode ||
-        precision != o.precision || restart != o.restart || mu_value != o.mu_value)
+        precision != o.precision || restart != o.restart || mu_value != o.mu_value || orth != o.orth)
         return false;
     for (int i = 0; i < MK_MAX_LEVELS; ++i)
         if (nu[i] != o.nu[i] || space[i] != o.space[i] || m_inner[i] != o.m_inner[i]) return false;
@@ -32,6 +32,7 @@ static OptsKey make_key(const mk_solve_opts &o) {
     k.mu_mode = o.mu_mode;
     k.precision = o.precision;
     k.restart = o.restart;
+    k.orth = o.orth;
     k.mu_value = o.mu_mode == 2 ? o.mu_value : 0.0;
     for (int i = 0; i < o.levels - 1 && i < MK_MAX_LEVELS; ++i) {
         k.nu[i] = o.nu[i];
@@ -47,6 +48,7 @@ mk_status validate_opts(const Problem &P, const mk_solve_opts &o) {
     if (o.levels < 2 || o.levels > MK_MAX_LEVELS) return MK_ERR_INVALID;
     if (o.precision != 0 && o.precision != 1) return MK_ERR_INVALID;
     if (o.mu_mode < 0 || o.mu_mode > 2) return MK_ERR_INVALID;
+    if (o.orth < 0 || o.orth > 2) return MK_ERR_INVALID;
     if (o.n_cgs < 0) return MK_ERR_INVALID;
     int nt = P.nt, nx = P.nx, ny = P.dim == 2 ? P.ny : 1;
     for (int l = 0; l < o.levels - 1; ++l) {
@@ -350,12 +352,15 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s) {
         t_outer_j = j;
         enqueue_cycle_step(H, 0, j, done, s);
         set_ctx(L, 0);
+        const int orth = H.key.orth;
+        const int mode = orth == 0 ? UPD_GIVENS : (orth == 2 ? UPD_GIVENS | UPD_REORTH_ALWAYS : UPD_OUTER);
         launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, false, done, s);
-        launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, UPD_OUTER, false,
-                                      done, s);
-        launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, true, done, s);
-        launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, UPD_OUTER, true,
-                                      done, s);
+        launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, mode, false, done, s);
+        if (orth != 0) {
+            launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, true, done, s);
+            launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, UPD_GIVENS, true,
+                                          done, s);
+        }
     }
     t_outer_j = -1;
     set_ctx(L, 0);
