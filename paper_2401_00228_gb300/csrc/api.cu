@@ -325,7 +325,10 @@ mk_status mk_march(mk_problem *p, const double *u0, double *u_out, void *stream)
     launch_pack<double, double>(g0, du0, fbuf.as<double>(), s);
     SpaceOp<double> op{P.m_c64.as<double>(), P.dim == 2 ? P.m_c64.as<double>() + 3 * P.nx : nullptr};
     const double a = P.theta * P.dt, b = (1.0 - P.theta) * P.dt;
-    if (P.dim == 1)
+    if (P.dim == 1 && P.m_spikeU > 0)
+        launch_slab_1d_warp<double>(P.g, b, P.m_spike.as<double>(), P.m_spikeU, 0, fbuf.as<double>(),
+                                    ubuf.as<double>(), nullptr, s, PROF_MARCH);
+    else if (P.dim == 1)
         launch_march_1d(P.g, b, op, P.m_alpha.as<double>(), P.m_gamma.as<double>(),
                         P.m_binv.as<double>(), P.m_npad, P.m_nlev, fbuf.as<double>(),
                         ubuf.as<double>(), s);
@@ -666,6 +669,19 @@ static mk_status op_coarsest_t(Hierarchy &H, const double *dr, double *dx, cudaS
         CK(up(al, a1));
         CK(up(ga, g1));
         CK(up(bi, b1));
+        if (slab_warp_supported<T>(C.g.nx)) {
+            const int U = spike_block_size(C.g.nx);
+            std::vector<double> tab;
+            spike_tables(C.Lx, C.w.a, U, tab);
+            DevMem sp;
+            CK(up(sp, tab));
+            launch_slab_1d_warp<T>(C.g, C.w.b, sp.as<T>(), U, H.key.n_cgs, rp.as<T>(), xp.as<T>(),
+                                   nullptr, s, PROF_SLAB);
+            launch_unpack<T, double>(C.g, xp.as<T>(), dx, s);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(s));
+            return MK_OK;
+        }
         launch_slab_1d<T>(C.g, C.w.b, op, al.as<T>(), ga.as<T>(), bi.as<T>(), C.npad, C.nlev,
                           H.key.n_cgs, rp.as<T>(), xp.as<T>(), nullptr, s);
     } else {
@@ -723,7 +739,8 @@ mk_status mk_op_precond(mk_problem *p, const mk_solve_opts *opts, int32_t level,
     CKS(stage_out(x, level_n(L), ox));
     // v -> basis slot 0 of level l with sigma_0 = 1; flags cleared (not done)
     const bool l0 = level == 1;
-    if (l0 || H->precision == 0) launch_pack<double, double>(L.g, dv, L.V.as<double>(), s);
+    if (H->precision == 0) launch_pack<double, double>(L.g, dv, L.V.as<double>(), s);
+    else if (l0) launch_pack<double, float2>(L.g, dv, L.V.as<float2>(), s);   // double-float basis
     else launch_pack<double, float>(L.g, dv, L.V.as<float>(), s);
     double one = 1.0;
     CK(cudaMemcpyAsync(L.ks.sigma(), &one, sizeof(double), cudaMemcpyHostToDevice, s));

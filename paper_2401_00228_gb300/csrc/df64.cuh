@@ -1,0 +1,89 @@
+// Double-float ("df64") arithmetic on the FP32 pipe.
+//
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2, which
+// carries a 48-bit significand.  GB300 issues FP32 instructions at 58x the rate of FP64
+// ones (measured), so level-1 vectors of the mixed-precision solve are stored as (hi, lo)
+// pairs -- 8 bytes per element, as FP64 -- and their Arnoldi arithmetic runs in FP32.
+//
+// The building blocks are the classical error-free transformations: Knuth's TwoSum (the
+// rounding error of a sum is itself a float), Dekker's Fast2Sum for |a| >= |b|, and the
+// FMA form of TwoProduct (fmaf(a, b, -a*b) is the exact error of a*b).  Products drop the
+// lo*lo term (relative 2^-48).  nvcc does not reassociate float arithmetic, and the only
+// contractions used are the explicit fmaf calls.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mk {
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    float s = a + b;
+    float e = b - (s - a);
+    return {s, e};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+    float p = a * b;
+    float e = fmaf(a, b, -p);
+    return {p, e};
+}
+
+// x + y (both double-float), error O(2^-46) relative
+__device__ __forceinline__ df df_add(df x, df y) {
+    df s = two_sum(x.hi, y.hi);
+    s.lo += x.lo + y.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+
+// x * y with y a float
+__device__ __forceinline__ df df_mul_f(df x, float y) {
+    df p = two_prod(x.hi, y);
+    p.lo = fmaf(x.lo, y, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+
+// x * y (both double-float)
+__device__ __forceinline__ df df_mul(df x, df y) {
+    df p = two_prod(x.hi, y.hi);
+    p.lo = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo));
+    return fast_two_sum(p.hi, p.lo);
+}
+
+// a + b for floats (exact)
+__device__ __forceinline__ df df_from_sum(float a, float b) { return two_sum(a, b); }
+
+__device__ __forceinline__ df df_from_float(float a) { return {a, 0.f}; }
+
+__host__ __device__ __forceinline__ float2 df_pack(df x) { return make_float2(x.hi, x.lo); }
+__host__ __device__ __forceinline__ df df_unpack(float2 v) { return {v.x, v.y}; }
+
+// conversions with FP64 (FP64 pipe; used once per restart, not in the inner loops)
+__device__ __forceinline__ df df_from_double(double d) {
+    float hi = (float)d;
+    float lo = (float)(d - (double)hi);
+    return {hi, lo};
+}
+__device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
+
+inline float2 df_pack_host(double d) {
+    float hi = (float)d;
+    float lo = (float)(d - (double)hi);
+    return make_float2(hi, lo);
+}
+
+}  // namespace mk

@@ -1,0 +1,506 @@
+// Level-1 kernels of the mixed-precision solve with the FGMRES basis in double-float pairs
+// (see df64.cuh): the Arnoldi orthogonalisation of Algorithm 2 (classical Gram-Schmidt:
+// multidot and update), the fused interpolation-correction-matvec of substeps 4.4-4.5 and
+// step 5 with w = A x evaluated in double-float, and the true residual r = f - A u (FP64
+// arithmetic, stored as a pair).  Storage is 8 bytes per element as in FP64, but the
+// arithmetic runs on the FP32 pipe, so these kernels are bound by HBM rather than by
+// GB300's FP64 rate.
+#include "df64.cuh"
+#include "kernels.h"
+#include "krylov_epilogue.cuh"
+#include "reduce.cuh"
+#include "stencil_common.cuh"
+
+namespace mk {
+
+constexpr int DF_THREADS = 256;
+constexpr int DF_WARPS = DF_THREADS / 32;
+constexpr int DF_EPT = 16;
+constexpr int DF_TILE = DF_THREADS * DF_EPT;
+
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        df w;
+        w.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, w);
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------------------
+// K2: r = f - A u in FP64; r stored as a double-float pair (the basis vector V_0)
+// ---------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(256) k_residual_df(Geom g, double a, double b, SpaceOp<double> L,
+                                                     const double *__restrict__ f,
+                                                     const double *__restrict__ u,
+                                                     float2 *__restrict__ r, int kc,
+                                                     ReduceScratch rs, int slot, KState ks, int epi) {
+    int i, j, chunk;
+    point_index<DIM>(i, j, chunk);
+    double acc = 0.0;
+    if (i < g.nx && j < g.ny) {
+        int k0 = chunk * kc;
+        int k1 = min(k0 + kc, g.nt + 1);
+        double prev = 0, Lprev = 0;
+        if (k0 > 0) {
+            int64_t idx = g.at(k0 - 1, j, i);
+            prev = u[idx];
+            Lprev = lap_at<DIM, double>(u, idx, i, j, g, L.x, L.y);
+        }
+        for (int k = k0; k < k1; ++k) {
+            int64_t idx = g.at(k, j, i);
+            double cur = u[idx];
+            double Lc = lap_at<DIM, double>(u, idx, i, j, g, L.x, L.y);
+            double Au = (k == 0) ? cur : (cur - a * Lc) - (prev + b * Lprev);
+            double rv = f[idx] - Au;
+            r[idx] = df_pack(df_from_double(rv));
+            acc += rv * rv;
+            prev = cur;
+            Lprev = Lc;
+        }
+    }
+    block_partial_and_finish(acc, rs, slot, ks, epi);
+}
+
+void launch_residual_df(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
+                        const double *u, float2 *r, const ReduceScratch &rs, int slot, KState ks,
+                        int epi, cudaStream_t s) {
+    int kc = choose_kc(g.npts(), g.nt + 1);
+    int nch = (g.nt + 1 + kc - 1) / kc;
+    Launch2 l = point_launch(g.dim, g.nx, g.ny, nch);
+    prof_begin(s);
+    if (g.dim == 1)
+        k_residual_df<1><<<l.grid, l.block, 0, s>>>(g, w.a, w.b, L, f, u, r, kc, rs, slot, ks, epi);
+    else
+        k_residual_df<2><<<l.grid, l.block, 0, s>>>(g, w.a, w.b, L, f, u, r, kc, rs, slot, ks, epi);
+    prof_end(s, PROF_RESIDUAL, (double)g.interior() * 24.0);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// K4 (level 1, mixed): x = sigma v - Z vt in FP32, w = A x in double-float.
+//   v: basis vector (pairs; its leading float is used), Xc: coarse FGMRES directions
+//   (FP32) combined with yc on the fly.  The spatial operator enters as per-index
+//   double-float coefficients a*L and b*L: aL = [lo|di|up] (x) then (y).
+// ---------------------------------------------------------------------------------------
+template <int DIM, bool SPACE>
+struct XEvalDF {
+    const float2 *v;
+    float sigma;
+    const float *Xc;
+    int mc;
+    int64_t xc_stride;
+    float y[MK_MAX_INNER];
+    Geom gf, gc;
+    int nu;
+
+    __device__ __forceinline__ float operator()(int k, int j, int i) const {
+        if (i < 0 || i >= gf.nx || j < 0 || j >= gf.ny) return 0.f;
+        int K = (k == 0) ? 0 : (k - 1) / nu + 1;
+        int I = SPACE ? (i >> 1) : i;
+        int J = (SPACE && DIM == 2) ? (j >> 1) : j;
+        int64_t cidx = gc.at(K, J, I);
+        float zt;
+        if (mc == 0) {
+            zt = Xc[cidx];
+        } else {
+            zt = 0.f;
+#pragma unroll
+            for (int m = 0; m < MK_MAX_INNER; ++m)
+                if (m < mc) zt += y[m] * Xc[cidx + m * xc_stride];
+        }
+        return sigma * v[gf.at(k, j, i)].x - zt;
+    }
+};
+
+template <int DIM>
+__device__ __forceinline__ df lap_df(const float2 *__restrict__ cx, const float2 *__restrict__ cy,
+                                     int nx, int ny, int i, int j, float c, float l, float r,
+                                     float d, float u) {
+    df s = df_mul_f(df_unpack(cx[nx + i]), c);
+    s = df_add(s, df_mul_f(df_unpack(cx[i]), l));
+    s = df_add(s, df_mul_f(df_unpack(cx[2 * nx + i]), r));
+    if (DIM == 2) {
+        s = df_add(s, df_mul_f(df_unpack(cy[ny + j]), c));
+        s = df_add(s, df_mul_f(df_unpack(cy[j]), d));
+        s = df_add(s, df_mul_f(df_unpack(cy[2 * ny + j]), u));
+    }
+    return s;
+}
+
+template <int DIM, bool SPACE>
+__global__ void __launch_bounds__(256) k_interp_df(Geom gf, Geom gc, int nu,
+                                                   const float2 *__restrict__ ca,
+                                                   const float2 *__restrict__ cb, int has_b,
+                                                   const float2 *__restrict__ v,
+                                                   const double *__restrict__ sigma,
+                                                   const float *__restrict__ Xc, int mc,
+                                                   int64_t xc_stride,
+                                                   const double *__restrict__ yc,
+                                                   float *__restrict__ xout,
+                                                   float2 *__restrict__ wout, int kc,
+                                                   const int *__restrict__ done) {
+    if (done && *done) return;
+    int i, j, chunk;
+    point_index<DIM>(i, j, chunk);
+    if (i >= gf.nx || j >= gf.ny) return;
+    XEvalDF<DIM, SPACE> X;
+    X.v = v;
+    X.sigma = sigma ? (float)(*sigma) : 1.f;
+    X.Xc = Xc;
+    X.mc = yc ? mc : 0;
+    X.xc_stride = xc_stride;
+    for (int m = 0; m < MK_MAX_INNER; ++m) X.y[m] = (yc && m < mc) ? (float)yc[m] : 0.f;
+    X.gf = gf;
+    X.gc = gc;
+    X.nu = nu;
+    // coefficient rows: a*L in ca, b*L in cb; x block first (3 nx), then y (3 ny)
+    const float2 *cax = ca, *cay = ca + 3 * gf.nx;
+    const float2 *cbx = cb, *cby = cb + 3 * gf.nx;
+    int k0 = chunk * kc;
+    int k1 = min(k0 + kc, gf.nt + 1);
+    float prev = 0.f;
+    df bLprev = {0.f, 0.f};
+    auto eval = [&](int k, float &c, df &aL, df &bL) {
+        c = X(k, j, i);
+        float l = X(k, j, i - 1), r = X(k, j, i + 1);
+        float d = 0.f, u = 0.f;
+        if (DIM == 2) {
+            d = X(k, j - 1, i);
+            u = X(k, j + 1, i);
+        }
+        aL = lap_df<DIM>(cax, cay, gf.nx, gf.ny, i, j, c, l, r, d, u);
+        bL = has_b ? lap_df<DIM>(cbx, cby, gf.nx, gf.ny, i, j, c, l, r, d, u) : df{0.f, 0.f};
+    };
+    if (k0 > 0) {
+        df aL;
+        eval(k0 - 1, prev, aL, bLprev);
+    }
+    for (int k = k0; k < k1; ++k) {
+        float c;
+        df aL, bL;
+        eval(k, c, aL, bL);
+        df w;
+        if (k == 0) {
+            w = df_from_float(c);
+        } else {
+            // (x_k - a L x_k) - (x_{k-1} + b L x_{k-1})
+            w = df_sub(df_sub(df_from_sum(c, -prev), aL), bLprev);
+        }
+        int64_t idx = gf.at(k, j, i);
+        xout[idx] = c;
+        wout[idx] = df_pack(w);
+        prev = c;
+        bLprev = bL;
+    }
+}
+
+// 1D specialisation: x once per point, neighbours from the adjacent lanes, the point's
+// double-float coefficients held in registers, row pointers and the coarse block index
+// advanced once per step, the coarse combination specialised on its size MC (see the FP32
+// version in stencil.cu).
+template <bool SPACE, int MC>
+__global__ void __launch_bounds__(256) k_interp_df_1d(Geom gf, Geom gc, int nu,
+                                                      const float2 *__restrict__ ca,
+                                                      const float2 *__restrict__ cb, int has_b,
+                                                      const float2 *__restrict__ v,
+                                                      const double *__restrict__ sigma,
+                                                      const float *__restrict__ Xc, int mc,
+                                                      int64_t xc_stride,
+                                                      const double *__restrict__ yc,
+                                                      float *__restrict__ xout,
+                                                      float2 *__restrict__ wout, int kc,
+                                                      const int *__restrict__ done) {
+    if (done && *done) return;
+    const unsigned FULL = 0xffffffffu;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int nx = gf.nx;
+    const bool act = i < nx;
+    const float sig = sigma ? (float)(*sigma) : 1.f;
+    constexpr int NY = MC > 0 ? MC : MK_MAX_INNER;
+    float y[NY];
+#pragma unroll
+    for (int m = 0; m < NY; ++m) y[m] = (yc && m < mc) ? (float)yc[m] : 0.f;
+    const df z = {0.f, 0.f};
+    const df alo = act ? df_unpack(ca[i]) : z, adi = act ? df_unpack(ca[nx + i]) : z,
+             aup = act ? df_unpack(ca[2 * nx + i]) : z;
+    const df blo = (act && has_b) ? df_unpack(cb[i]) : z,
+             bdi = (act && has_b) ? df_unpack(cb[nx + i]) : z,
+             bup = (act && has_b) ? df_unpack(cb[2 * nx + i]) : z;
+    auto xval = [&](const float2 *vr, const float *zr, int ii) -> float {
+        if (ii < 0 || ii >= nx) return 0.f;
+        const float *zp = zr + (SPACE ? (ii >> 1) : ii);
+        float zt;
+        if (MC == 0) {
+            zt = zp[0];
+        } else if (MC == 1) {
+            zt = y[0] * zp[0];
+        } else if (MC == 2) {
+            zt = y[0] * zp[0] + y[NY > 1 ? 1 : 0] * zp[xc_stride];
+        } else {
+            zt = 0.f;
+#pragma unroll
+            for (int m = 0; m < NY; ++m)
+                if (m < mc) zt += y[m] * zp[m * xc_stride];
+        }
+        return sig * vr[ii].x - zt;
+    };
+    const int k0 = blockIdx.y * kc;
+    const int k1 = min(k0 + kc, gf.nt + 1);
+    const int kstart = k0 > 0 ? k0 - 1 : 0;
+    int K = (kstart == 0) ? 0 : (kstart - 1) / nu + 1;
+    int ph = (kstart == 0) ? nu - 1 : (kstart - 1) % nu;
+    float prev = 0.f;
+    df bLprev = z;
+    for (int k = kstart; k < k1; ++k) {
+        if (k > kstart) {
+            if (ph == nu - 1) {
+                ++K;
+                ph = 0;
+            } else {
+                ++ph;
+            }
+        }
+        const float2 *vr = v + gf.guard + (int64_t)k * gf.plane;
+        const float *zr = Xc + gc.guard + (int64_t)K * gc.plane;
+        float c = xval(vr, zr, i);
+        float l = __shfl_up_sync(FULL, c, 1), r = __shfl_down_sync(FULL, c, 1);
+        if (lane == 0) l = xval(vr, zr, i - 1);
+        if (lane == 31) r = xval(vr, zr, i + 1);
+        df aL = df_add(df_add(df_mul_f(adi, c), df_mul_f(alo, l)), df_mul_f(aup, r));
+        df bL = has_b ? df_add(df_add(df_mul_f(bdi, c), df_mul_f(blo, l)), df_mul_f(bup, r)) : z;
+        if (k >= k0) {
+            df w = (k == 0) ? df_from_float(c) : df_sub(df_sub(df_from_sum(c, -prev), aL), bLprev);
+            if (act) {
+                int64_t idx = gf.guard + (int64_t)k * gf.plane + i;
+                xout[idx] = c;
+                wout[idx] = df_pack(w);
+            }
+        }
+        prev = c;
+        bLprev = bL;
+    }
+}
+
+void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const float2 *ca,
+                      const float2 *cb, bool has_b, const float2 *v, const double *sigma,
+                      const float *Xc, int mc, int64_t xc_stride, const double *yc, float *x,
+                      float2 *wout, const int *done, cudaStream_t s) {
+    int kc = choose_kc(gf.npts(), gf.nt + 1);
+    int nch = (gf.nt + 1 + kc - 1) / kc;
+    Launch2 l = point_launch(gf.dim, gf.nx, gf.ny, nch);
+    const int hb = has_b ? 1 : 0;
+#define MK_IDF(D, S)                                                                          \
+    k_interp_df<D, S><<<l.grid, l.block, 0, s>>>(gf, gc, nu, ca, cb, hb, v, sigma, Xc, mc,    \
+                                                 xc_stride, yc, x, wout, kc, done)
+#define MK_IDF1M(S, M)                                                                        \
+    k_interp_df_1d<S, M><<<l.grid, l.block, 0, s>>>(gf, gc, nu, ca, cb, hb, v, sigma, Xc, mc, \
+                                                    xc_stride, yc, x, wout, kc, done)
+#define MK_IDF1(S)                                                                            \
+    do {                                                                                      \
+        if (!yc) MK_IDF1M(S, 0);                                                              \
+        else if (mc == 1) MK_IDF1M(S, 1);                                                     \
+        else if (mc == 2) MK_IDF1M(S, 2);                                                     \
+        else MK_IDF1M(S, -1);                                                                 \
+    } while (0)
+    prof_begin(s);
+    if (gf.dim == 1) {
+        if (space) MK_IDF1(true); else MK_IDF1(false);
+    } else {
+        if (space) MK_IDF(2, true); else MK_IDF(2, false);
+    }
+#undef MK_IDF
+#undef MK_IDF1
+#undef MK_IDF1M
+    prof_end(s, PROF_INTERP, (double)gf.interior() * (8.0 + 4.0 + 8.0) + (double)mc * gc.interior() * 4.0);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// Arnoldi with double-float vectors (first and second classical Gram-Schmidt pass).
+// multidot: d_i = <W, V_i> (i <= j) and, on the first pass, ||W||^2.
+//
+// Compensated dot product (the "Dot2" scheme of Ogita, Rump and Oishi): each product is
+// split exactly by TwoProduct, the high parts are summed with TwoSum and every rounding
+// error goes into a float compensation, so the dependent chain per element is a single
+// addition.  Two basis vectors are processed per sweep with independent accumulators, and
+// the W tile is re-read from L1 instead of being held in registers.  Vector lengths are a
+// whole number of tiles (padding is zero), so the sweep has no bounds checks.
+// ---------------------------------------------------------------------------------------
+struct Dot2 {
+    float s, c;
+    __device__ __forceinline__ void init() { s = 0.f; c = 0.f; }
+    // accumulate (ah + al)(bh + bl) without the al*bl term
+    __device__ __forceinline__ void add(float2 a, float2 b) {
+        df p = two_prod(a.x, b.x);
+        float low = fmaf(a.x, b.y, fmaf(a.y, b.x, p.lo));
+        df t = two_sum(s, p.hi);
+        s = t.hi;
+        c += t.lo + low;
+    }
+    __device__ __forceinline__ df value() const { return fast_two_sum(s, c); }
+};
+
+__global__ void __launch_bounds__(DF_THREADS) k_multidot_df(int64_t len, const float2 *__restrict__ W,
+                                                            const float2 *__restrict__ V,
+                                                            int64_t vstride, int j,
+                                                            ReduceScratch rs, KState ks,
+                                                            int second,
+                                                            const int *__restrict__ done) {
+    if (done && *done) return;
+    if (second && !ks.flags[2]) return;
+    extern __shared__ double smem_md[];
+    const int nv = j + 1;
+    const int nslots = second ? nv : nv + 1;
+    double *acc = smem_md;                      // [nslots][DF_WARPS]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < nslots * DF_WARPS; t += DF_THREADS) acc[t] = 0.0;
+    __syncthreads();
+    const float2 *src = second ? V + (int64_t)(j + 1) * vstride : W;
+    for (int64_t base = (int64_t)blockIdx.x * DF_TILE + threadIdx.x; base < len;
+         base += (int64_t)gridDim.x * DF_TILE) {
+        if (!second) {
+            Dot2 d0, d1;
+            d0.init();
+            d1.init();
+#pragma unroll
+            for (int q = 0; q < DF_EPT; q += 2) {
+                float2 w0 = src[base + q * DF_THREADS], w1 = src[base + (q + 1) * DF_THREADS];
+                d0.add(w0, w0);
+                d1.add(w1, w1);
+            }
+            df r = warp_sum_df(df_add(d0.value(), d1.value()));
+            if (lane == 0) acc[nv * DF_WARPS + warp] += df_to_double(r);
+        }
+        for (int i = 0; i < nv; i += 2) {
+            const bool pair = (i + 1 < nv);
+            const float2 *va = V + (int64_t)i * vstride;
+            const float2 *vb = pair ? va + vstride : va;
+            Dot2 a0, a1, b0, b1;
+            a0.init();
+            a1.init();
+            b0.init();
+            b1.init();
+#pragma unroll
+            for (int q = 0; q < DF_EPT; q += 2) {
+                const int64_t e0 = base + q * DF_THREADS, e1 = e0 + DF_THREADS;
+                float2 w0 = src[e0], w1 = src[e1];
+                float2 x0 = va[e0], x1 = va[e1];
+                float2 y0 = vb[e0], y1 = vb[e1];
+                a0.add(w0, x0);
+                a1.add(w1, x1);
+                b0.add(w0, y0);
+                b1.add(w1, y1);
+            }
+            df ra = warp_sum_df(df_add(a0.value(), a1.value()));
+            df rb = warp_sum_df(df_add(b0.value(), b1.value()));
+            if (lane == 0) {
+                acc[i * DF_WARPS + warp] += df_to_double(ra);
+                if (pair) acc[(i + 1) * DF_WARPS + warp] += df_to_double(rb);
+            }
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nslots; t += DF_THREADS) {
+        double s = 0.0;
+        for (int w2 = 0; w2 < DF_WARPS; ++w2) s += acc[t * DF_WARPS + w2];
+        rs.partials[(int64_t)t * rs.max_blocks + blockIdx.x] = s;
+    }
+    if (last_block_ticket(rs.counter)) {
+        const int lane2 = threadIdx.x & 31, warp2 = threadIdx.x >> 5;
+        double *res = smem_md;
+        for (int t = warp2; t < nslots; t += DF_WARPS) {
+            const volatile double *p = rs.partials + (int64_t)t * rs.max_blocks;
+            double a = 0.0;
+            for (int b = lane2; b < (int)gridDim.x; b += 32) a += p[b];
+            a = warp_sum(a);
+            if (lane2 == 0) res[t] = a;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double *H = ks.H() + (int64_t)j * (ks.m + 1);
+            for (int i = 0; i < nv; ++i) {
+                double hc = ks.sigma()[i] * res[i];
+                ks.tmp()[i] = hc;
+                H[i] = second ? H[i] + hc : hc;
+            }
+            if (!second) ks.misc()[2] = res[nv];
+            rs.counter[0] = 0u;
+        }
+    }
+}
+
+// update: V_{j+1} = src - sum_i c_i V_i, c_i = tmp_i sigma_i, ||.||^2, epilogue
+__global__ void __launch_bounds__(DF_THREADS) k_update_df(int64_t len, const float2 *__restrict__ W,
+                                                          float2 *__restrict__ V, int64_t vstride,
+                                                          int j, ReduceScratch rs, KState ks,
+                                                          int mode, int second,
+                                                          const int *__restrict__ done) {
+    if (done && *done) return;
+    if (second && !ks.flags[2]) return;
+    __shared__ float2 c[MK_MAX_RESTART + 1];
+    const int nv = j + 1;
+    for (int i = threadIdx.x; i < nv; i += DF_THREADS)
+        c[i] = df_pack(df_from_double(ks.tmp()[i] * ks.sigma()[i]));
+    __syncthreads();
+    float2 *out = V + (int64_t)(j + 1) * vstride;
+    df acc = {0.f, 0.f};
+    for (int64_t e = (int64_t)blockIdx.x * DF_THREADS + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * DF_THREADS) {
+        df val = df_unpack(second ? out[e] : W[e]);
+        for (int i = 0; i < nv; ++i)
+            val = df_sub(val, df_mul(df_unpack(c[i]), df_unpack(V[(int64_t)i * vstride + e])));
+        out[e] = df_pack(val);
+        df p = two_prod(val.hi, val.hi);
+        p.lo = fmaf(2.f * val.hi, val.lo, p.lo);
+        acc = df_add(acc, p);
+    }
+    double bs = block_sum(df_to_double(acc));
+    if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
+    if (last_block_ticket(rs.counter)) {
+        double tot = sum_partials(rs.partials, gridDim.x);
+        if (threadIdx.x == 0) {
+            update_epilogue(tot, ks, j, mode, second);
+            rs.counter[0] = 0u;
+        }
+    }
+}
+
+static int df_grid(int64_t len, int64_t per_block) {
+    int64_t g = (len + per_block - 1) / per_block;
+    int64_t cap = (int64_t)g_num_sms * 4;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+void launch_multidot_df(int64_t len, const float2 *W, const float2 *V, int64_t vstride, int j,
+                        const ReduceScratch &rs, KState ks, bool second_pass, const int *done,
+                        cudaStream_t s) {
+    int grid = df_grid(len, DF_TILE);
+    size_t shm = sizeof(double) * (size_t)(j + 2) * DF_WARPS;
+    const double alg_n = prof_alg_n() > 0 ? prof_alg_n() : (double)len;
+    prof_begin(s);
+    k_multidot_df<<<grid, DF_THREADS, shm, s>>>(len, W, V, vstride, j, rs, ks, second_pass ? 1 : 0,
+                                                done);
+    prof_end(s, PROF_MULTIDOT, (double)(j + 2) * alg_n * 8.0);
+    count_launch();
+}
+
+void launch_update_df(int64_t len, const float2 *W, float2 *V, int64_t vstride, int j,
+                      const ReduceScratch &rs, KState ks, int mode, bool second_pass,
+                      const int *done, cudaStream_t s) {
+    int grid = df_grid(len, (int64_t)DF_THREADS * 8);
+    const double alg_n = prof_alg_n() > 0 ? prof_alg_n() : (double)len;
+    prof_begin(s);
+    k_update_df<<<grid, DF_THREADS, 0, s>>>(len, W, V, vstride, j, rs, ks, mode,
+                                            second_pass ? 1 : 0, done);
+    prof_end(s, PROF_UPDATE, (double)(j + 3) * alg_n * 8.0);
+    count_launch();
+}
+
+}  // namespace mk

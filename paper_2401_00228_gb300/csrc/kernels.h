@@ -110,6 +110,22 @@ void launch_combine(int64_t len, double *u, const TX *X, int64_t xstride, KState
 void launch_lsq(int j, double *H, double beta, double *gg, double *y, double *res,
                 cudaStream_t s);
 
+// ---- level-1 kernels of the mixed solve with double-float vectors (dfkernels.cu) --------
+void launch_residual_df(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
+                        const double *u, float2 *r, const ReduceScratch &rs, int slot, KState ks,
+                        int epi, cudaStream_t s);
+// ca, cb: double-float a*L and b*L coefficient rows, [x: lo|di|up (3 nx) | y: (3 ny)]
+void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const float2 *ca,
+                      const float2 *cb, bool has_b, const float2 *v, const double *sigma,
+                      const float *Xc, int mc, int64_t xc_stride, const double *yc, float *x,
+                      float2 *wout, const int *done, cudaStream_t s);
+void launch_multidot_df(int64_t len, const float2 *W, const float2 *V, int64_t vstride, int j,
+                        const ReduceScratch &rs, KState ks, bool second_pass, const int *done,
+                        cudaStream_t s);
+void launch_update_df(int64_t len, const float2 *W, float2 *V, int64_t vstride, int j,
+                      const ReduceScratch &rs, KState ks, int mode, bool second_pass,
+                      const int *done, cudaStream_t s);
+
 // ---- slab solvers (slab.cu) -----------------------------------------------------------
 // 1D coarsest: n_cgs slabs x s steps, tridiagonal I - aL by parallel cyclic reduction with
 // precomputed tables (alpha, gamma, binv in T); x_0 = r_0.
@@ -117,6 +133,14 @@ template <typename T>
 void launch_slab_1d(const Geom &g, double b, SpaceOp<T> L, const T *alpha, const T *gamma,
                     const T *binv, int npad, int nlev, int n_cgs, const T *r, T *x,
                     const int *done, cudaStream_t s);
+// 1D, one warp per slab: partitioned solver with the tables of spike_tables() in T.
+// cls: PROF_SLAB or PROF_MARCH for the kernel-class timing.
+int spike_block_size(int n);
+template <typename T>
+bool slab_warp_supported(int n);
+template <typename T>
+void launch_slab_1d_warp(const Geom &g, double b, const T *tab, int U, int n_cgs, const T *r, T *x,
+                         const int *done, cudaStream_t s, int cls);
 // 2D coarsest: fast diagonalisation of I - a(Lx (+) Ly) with S, S^{-1} per direction.
 template <typename T>
 void launch_slab_2d(const Geom &g, double a, double b, SpaceOp<T> L, const T *Sx, const T *Sxi,

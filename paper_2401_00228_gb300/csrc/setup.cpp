@@ -8,6 +8,7 @@
 //  * pcr_tables:   coefficient tables of parallel cyclic reduction on I - aL.
 //  * tri_eigen:    L = S diag(lam) S^{-1} for the fast-diagonalisation slab solver.
 #include <algorithm>
+#include <array>
 #include <cmath>
 
 #include "mk_internal.h"
@@ -24,7 +25,9 @@ Geom make_geom(int dim, int nx, int ny, int nt) {
     g.plane = dim == 1 ? (int64_t)g.ldx : (int64_t)(g.ny + 1) * g.ldx;
     g.guard = g.ldx;
     int64_t len = g.guard + (int64_t)(nt + 1) * g.plane + g.ldx;
-    g.len = ((len + 63) / 64) * 64;
+    // a whole number of 4096-element tiles: the Krylov kernels then sweep tiles without
+    // bounds checks (the extra elements are zero like the rest of the padding)
+    g.len = ((len + 4095) / 4096) * 4096;
     return g;
 }
 
@@ -156,6 +159,112 @@ void pcr_tables(const Tri &L, double a, int npad, std::vector<double> &alpha,
     }
     binv.assign(npad, 0.0);
     for (int i = 0; i < npad; ++i) binv[i] = 1.0 / B[i];
+}
+
+// Tables of the one-warp partitioned solver for M = I - aL (see slab.cu, k_slab_1d_warp).
+// The system is padded to 32*U rows (identity beyond n) and split into 32 blocks of U
+// rows, one per lane.  Per lane p (rows pU .. pU+U-1), stored item-major (item*32 + p):
+//   m[U]     Thomas multipliers (m[0] unused)      uinv[U]  1 / pivots
+//   sup[U]   super-diagonal of the block            v[U], w[U]  spikes M_p^{-1} e_0, e_{U-1}
+//   lo, di, up [U each]  the rows of L (for the explicit part (I + bL) x_{k-1})
+//   A, C     couplings M[pU, pU-1], M[pU+U-1, pU+U]
+//   alpha[5][4], gamma[5][4]  2x2 block-PCR multipliers on the interface unknowns
+//                             (F_p, G_p) = (x[pU], x[pU+U-1]), strides 1, 2, 4, 8, 16
+//   dinv[4]  inverse of the final 2x2 diagonal block
+int spike_items(int U) { return 8 * U + 46; }
+
+void spike_tables(const Tri &L, double a, int U, std::vector<double> &tab) {
+    const int n = L.n();
+    const int P = 32;
+    const int N = P * U;
+    std::vector<double> sub(N, 0.0), dia(N, 1.0), sup(N, 0.0);
+    for (int i = 0; i < n; ++i) {
+        sub[i] = (i > 0) ? -a * L.lo[i] : 0.0;
+        dia[i] = 1.0 - a * L.di[i];
+        sup[i] = (i < n - 1) ? -a * L.up[i] : 0.0;
+    }
+    const int items = spike_items(U);
+    tab.assign((size_t)items * P, 0.0);
+    auto T = [&](int item, int p) -> double & { return tab[(size_t)item * P + p]; };
+    typedef std::array<double, 4> M2;   // row-major 2x2
+    std::vector<M2> D(P), E(P), Hm(P);
+    for (int p = 0; p < P; ++p) {
+        const int r0 = p * U;
+        std::vector<double> m(U, 0.0), u(U), c(U, 0.0);
+        u[0] = dia[r0];
+        for (int q = 0; q < U; ++q) c[q] = (q < U - 1) ? sup[r0 + q] : 0.0;
+        for (int q = 1; q < U; ++q) {
+            m[q] = sub[r0 + q] / u[q - 1];
+            u[q] = dia[r0 + q] - m[q] * c[q - 1];
+        }
+        auto solve = [&](std::vector<double> d) {
+            for (int q = 1; q < U; ++q) d[q] -= m[q] * d[q - 1];
+            std::vector<double> y(U);
+            y[U - 1] = d[U - 1] / u[U - 1];
+            for (int q = U - 2; q >= 0; --q) y[q] = (d[q] - c[q] * y[q + 1]) / u[q];
+            return y;
+        };
+        std::vector<double> e0(U, 0.0), e1(U, 0.0);
+        e0[0] = 1.0;
+        e1[U - 1] = 1.0;
+        std::vector<double> v = solve(e0), w = solve(e1);
+        for (int q = 0; q < U; ++q) {
+            T(q, p) = m[q];
+            T(U + q, p) = 1.0 / u[q];
+            T(2 * U + q, p) = c[q];
+            T(3 * U + q, p) = v[q];
+            T(4 * U + q, p) = w[q];
+            const int i = r0 + q;
+            T(5 * U + q, p) = (i < n) ? L.lo[i] : 0.0;
+            T(6 * U + q, p) = (i < n) ? L.di[i] : 0.0;
+            T(7 * U + q, p) = (i < n) ? L.up[i] : 0.0;
+        }
+        const double A = (p > 0) ? sub[r0] : 0.0;
+        const double C = (p < P - 1) ? sup[r0 + U - 1] : 0.0;
+        T(8 * U, p) = A;
+        T(8 * U + 1, p) = C;
+        // interface equations: z_p + E_p z_{p-1} + H_p z_{p+1} = (y_p[0], y_p[U-1])
+        D[p] = {1.0, 0.0, 0.0, 1.0};
+        E[p] = {0.0, A * v[0], 0.0, A * v[U - 1]};
+        Hm[p] = {C * w[0], 0.0, C * w[U - 1], 0.0};
+    }
+    auto mul = [](const M2 &x, const M2 &y) {
+        return M2{x[0] * y[0] + x[1] * y[2], x[0] * y[1] + x[1] * y[3],
+                  x[2] * y[0] + x[3] * y[2], x[2] * y[1] + x[3] * y[3]};
+    };
+    auto inv = [](const M2 &x) {
+        double det = x[0] * x[3] - x[1] * x[2];
+        return M2{x[3] / det, -x[1] / det, -x[2] / det, x[0] / det};
+    };
+    auto add = [](const M2 &x, const M2 &y) {
+        return M2{x[0] + y[0], x[1] + y[1], x[2] + y[2], x[3] + y[3]};
+    };
+    auto neg = [](const M2 &x) { return M2{-x[0], -x[1], -x[2], -x[3]}; };
+    const M2 Z = {0.0, 0.0, 0.0, 0.0};
+    for (int l = 0; l < 5; ++l) {
+        const int s = 1 << l;
+        std::vector<M2> D2(P), E2(P), H2(P);
+        for (int p = 0; p < P; ++p) {
+            M2 al = (p - s >= 0) ? neg(mul(E[p], inv(D[p - s]))) : Z;
+            M2 ga = (p + s < P) ? neg(mul(Hm[p], inv(D[p + s]))) : Z;
+            for (int e = 0; e < 4; ++e) {
+                T(8 * U + 2 + l * 4 + e, p) = al[e];
+                T(8 * U + 22 + l * 4 + e, p) = ga[e];
+            }
+            D2[p] = D[p];
+            if (p - s >= 0) D2[p] = add(D2[p], mul(al, Hm[p - s]));
+            if (p + s < P) D2[p] = add(D2[p], mul(ga, E[p + s]));
+            E2[p] = (p - s >= 0) ? mul(al, E[p - s]) : Z;
+            H2[p] = (p + s < P) ? mul(ga, Hm[p + s]) : Z;
+        }
+        D.swap(D2);
+        E.swap(E2);
+        Hm.swap(H2);
+    }
+    for (int p = 0; p < P; ++p) {
+        M2 di = inv(D[p]);
+        for (int e = 0; e < 4; ++e) T(8 * U + 42 + e, p) = di[e];
+    }
 }
 
 // Cyclic Jacobi eigenvalue iteration for a dense symmetric matrix (row-major n x n).

@@ -142,6 +142,191 @@ static void slab_1d_launch(const Geom &g, double b, SpaceOp<T> L, const T *alpha
     count_launch();
 }
 
+// ---------------------------------------------------------------------------------------
+// 1D, one warp per slab: partitioned (spike) solver for the constant tridiagonal I - aL.
+// Lane p owns rows pU .. pU+U-1 (the system padded to 32U rows with identity rows):
+//   1. right-hand side r_k + (I + bL) x_{k-1} from the lane's own x_{k-1} values and one
+//      neighbour from each adjacent lane;
+//   2. Thomas on the lane's U x U block (precomputed multipliers and pivots): y = M_p^{-1} d;
+//   3. the interface unknowns (F_p, G_p) = (x[pU], x[pU+U-1]) satisfy a block-tridiagonal
+//      system with 2x2 blocks, solved by block parallel cyclic reduction over the 32 lanes
+//      in five shuffle steps (strides 1..16, precomputed multipliers);
+//   4. x = y - A_p G_{p-1} v_p - C_p F_{p+1} w_p with the precomputed spikes v_p, w_p.
+// No block barrier is needed.  Rows are read and written coalesced through a padded shared
+// staging buffer, and the next right-hand side is prefetched during the current step.
+// Tables: spike_tables() in setup.cpp (item-major, 32 lanes per item).
+// ---------------------------------------------------------------------------------------
+template <typename T, int U>
+__global__ void __launch_bounds__(32) k_slab_1d_warp(Geom g, T b, const T *__restrict__ tab,
+                                                     int steps, int coupled,
+                                                     const T *__restrict__ r,
+                                                     T *__restrict__ x,
+                                                     const int *__restrict__ done) {
+    if (done && *done) return;
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int ITEMS = 8 * U + 46;
+    extern __shared__ unsigned char smem_raw[];
+    T *tb = reinterpret_cast<T *>(smem_raw);   // ITEMS x 32
+    T *buf = tb + ITEMS * 32;                  // 32U values, one pad slot per 32
+    const int lane = threadIdx.x;
+    const int n = g.nx;
+    const int slab = blockIdx.x;
+    const int kbeg = 1 + slab * steps;
+    for (int e = lane; e < ITEMS * 32; e += 32) tb[e] = tab[e];
+    auto TB = [&](int item) -> T { return tb[item * 32 + lane]; };
+    auto sidx = [](int e) { return e + (e >> 5); };
+    T pre[U];
+    auto load_row = [&](int k) {
+        const T *row = r + g.guard + (int64_t)k * g.plane;
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int e = q * 32 + lane;
+            pre[q] = (e < n) ? row[e] : (T)0;
+        }
+    };
+    auto stage = [&]() {
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < U; ++q) buf[sidx(q * 32 + lane)] = pre[q];
+        __syncwarp();
+    };
+    T xp[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) xp[q] = (T)0;
+    if (slab == 0 || coupled) {
+        load_row(0);
+        if (slab == 0) {
+            T *row0 = x + g.guard;
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int e = q * 32 + lane;
+                if (e < n) row0[e] = pre[q];
+            }
+        }
+        if (coupled) {
+            stage();
+#pragma unroll
+            for (int q = 0; q < U; ++q) xp[q] = buf[sidx(lane * U + q)];
+        }
+    }
+    load_row(kbeg);
+    for (int s = 0; s < steps; ++s) {
+        const int k = kbeg + s;
+        stage();
+        if (s + 1 < steps) load_row(k + 1);
+        const bool first = (s == 0) && !coupled;
+        T xl = __shfl_up_sync(FULL, xp[U - 1], 1);
+        T xr = __shfl_down_sync(FULL, xp[0], 1);
+        if (lane == 0) xl = (T)0;
+        if (lane == 31) xr = (T)0;
+        T d[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            T rv = buf[sidx(lane * U + q)];
+            if (!first) {
+                const T left = q ? xp[q - 1] : xl;
+                const T right = (q < U - 1) ? xp[q + 1] : xr;
+                const T lx = TB(6 * U + q) * xp[q] + TB(5 * U + q) * left + TB(7 * U + q) * right;
+                rv = rv + (xp[q] + b * lx);
+            }
+            d[q] = rv;
+        }
+        // Thomas on the lane's block
+#pragma unroll
+        for (int q = 1; q < U; ++q) d[q] -= TB(q) * d[q - 1];
+        d[U - 1] *= TB(U + U - 1);
+#pragma unroll
+        for (int q = U - 2; q >= 0; --q) d[q] = (d[q] - TB(2 * U + q) * d[q + 1]) * TB(U + q);
+        // interface unknowns: block PCR across the lanes
+        T rF = d[0], rG = d[U - 1];
+#pragma unroll
+        for (int l = 0; l < 5; ++l) {
+            const int st = 1 << l;
+            T lF = __shfl_up_sync(FULL, rF, st), lG = __shfl_up_sync(FULL, rG, st);
+            T hF = __shfl_down_sync(FULL, rF, st), hG = __shfl_down_sync(FULL, rG, st);
+            if (lane < st) {
+                lF = (T)0;
+                lG = (T)0;
+            }
+            if (lane + st >= 32) {
+                hF = (T)0;
+                hG = (T)0;
+            }
+            const int ia = 8 * U + 2 + 4 * l, ig = 8 * U + 22 + 4 * l;
+            T nF = rF + TB(ia) * lF + TB(ia + 1) * lG + TB(ig) * hF + TB(ig + 1) * hG;
+            T nG = rG + TB(ia + 2) * lF + TB(ia + 3) * lG + TB(ig + 2) * hF + TB(ig + 3) * hG;
+            rF = nF;
+            rG = nG;
+        }
+        const int idv = 8 * U + 42;
+        const T F = TB(idv) * rF + TB(idv + 1) * rG;
+        const T G = TB(idv + 2) * rF + TB(idv + 3) * rG;
+        T Gm = __shfl_up_sync(FULL, G, 1), Fp = __shfl_down_sync(FULL, F, 1);
+        if (lane == 0) Gm = (T)0;
+        if (lane == 31) Fp = (T)0;
+        const T cA = TB(8 * U) * Gm, cC = TB(8 * U + 1) * Fp;
+#pragma unroll
+        for (int q = 0; q < U; ++q) xp[q] = d[q] - cA * TB(3 * U + q) - cC * TB(4 * U + q);
+        // write x_k coalesced
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < U; ++q) buf[sidx(lane * U + q)] = xp[q];
+        __syncwarp();
+        T *xrow = x + g.guard + (int64_t)k * g.plane;
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int e = q * 32 + lane;
+            if (e < n) xrow[e] = buf[sidx(e)];
+        }
+    }
+}
+
+int spike_block_size(int n) {
+    int U = 1;
+    while (32 * U < n) U *= 2;
+    return U;
+}
+
+template <typename T>
+size_t slab_warp_smem(int U) {
+    return sizeof(T) * ((size_t)(8 * U + 46) * 32 + 32 * U + U);
+}
+
+template <typename T>
+bool slab_warp_supported(int n) {
+    const int U = spike_block_size(n);
+    return sizeof(T) == 4 ? U <= 64 : U <= 32;
+}
+
+template <typename T>
+void launch_slab_1d_warp(const Geom &g, double b, const T *tab, int U, int n_cgs, const T *r, T *x,
+                         const int *done, cudaStream_t s, int cls) {
+    const int nslabs = n_cgs <= 0 ? 1 : n_cgs;
+    const int steps = n_cgs <= 0 ? g.nt : g.nt / n_cgs;
+    const int coupled = n_cgs <= 0 ? 1 : 0;
+    const size_t shm = slab_warp_smem<T>(U);
+    prof_begin(s);
+#define MK_SW(UU)                                                                              \
+    case UU:                                                                                   \
+        k_slab_1d_warp<T, UU><<<nslabs, 32, shm, s>>>(g, (T)b, tab, steps, coupled, r, x, done); \
+        break
+    switch (U) {
+        MK_SW(1);
+        MK_SW(2);
+        MK_SW(4);
+        MK_SW(8);
+        MK_SW(16);
+        MK_SW(32);
+        default:
+            if constexpr (sizeof(T) == 4)
+                k_slab_1d_warp<T, 64><<<nslabs, 32, shm, s>>>(g, (T)b, tab, steps, coupled, r, x, done);
+            break;
+    }
+#undef MK_SW
+    prof_end(s, cls, 2.0 * sizeof(T) * (double)g.interior());
+    count_launch();
+}
+
 template <typename T>
 void launch_slab_1d(const Geom &g, double b, SpaceOp<T> L, const T *alpha, const T *gamma,
                     const T *binv, int npad, int nlev, int n_cgs, const T *r, T *x,
@@ -326,9 +511,28 @@ cudaError_t slab_set_attributes() {
     set((const void *)k_slab_1d<double, 1>);
     set((const void *)k_slab_1d<double, 2>);
     set((const void *)k_slab_1d<double, 4>);
+    set((const void *)k_slab_1d_warp<float, 1>);
+    set((const void *)k_slab_1d_warp<float, 2>);
+    set((const void *)k_slab_1d_warp<float, 4>);
+    set((const void *)k_slab_1d_warp<float, 8>);
+    set((const void *)k_slab_1d_warp<float, 16>);
+    set((const void *)k_slab_1d_warp<float, 32>);
+    set((const void *)k_slab_1d_warp<float, 64>);
+    set((const void *)k_slab_1d_warp<double, 1>);
+    set((const void *)k_slab_1d_warp<double, 2>);
+    set((const void *)k_slab_1d_warp<double, 4>);
+    set((const void *)k_slab_1d_warp<double, 8>);
+    set((const void *)k_slab_1d_warp<double, 16>);
+    set((const void *)k_slab_1d_warp<double, 32>);
     return e;
 }
 
+template void launch_slab_1d_warp<float>(const Geom &, double, const float *, int, int,
+                                         const float *, float *, const int *, cudaStream_t, int);
+template void launch_slab_1d_warp<double>(const Geom &, double, const double *, int, int,
+                                          const double *, double *, const int *, cudaStream_t, int);
+template bool slab_warp_supported<float>(int);
+template bool slab_warp_supported<double>(int);
 template void launch_slab_1d<double>(const Geom &, double, SpaceOp<double>, const double *,
                                      const double *, const double *, int, int, int,
                                      const double *, double *, const int *, cudaStream_t);

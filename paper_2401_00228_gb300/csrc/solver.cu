@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "df64.cuh"
 #include "solver.h"
 
 namespace mk {
@@ -146,6 +147,14 @@ static mk_status build_coarsest_tables(Level &C, int dim, bool fp64) {
             MKCK(upload<float>(C.gamma, ga));
             MKCK(upload<float>(C.binv, bi));
         }
+        // one-warp partitioned solver where the block per lane fits in registers
+        if (fp64 ? slab_warp_supported<double>(n) : slab_warp_supported<float>(n)) {
+            C.spikeU = spike_block_size(n);
+            std::vector<double> tab;
+            spike_tables(C.Lx, C.w.a, C.spikeU, tab);
+            if (fp64) MKCK(upload<double>(C.spike, tab));
+            else MKCK(upload<float>(C.spike, tab));
+        }
     } else {
         std::vector<double> lx, Sx, Sxi, ly, Sy, Syi;
         tri_eigen(C.Lx, lx, Sx, Sxi);
@@ -214,6 +223,15 @@ mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out) {
         else if (o.mu_mode == 1) lv->w.mu = 1.0;
         else lv->w.mu = o.mu_value;
         mk_status st = upload_coefs(*lv, P.dim);
+        if (st == MK_OK && l == 0 && !fp64) {
+            // double-float a*L and b*L rows for the level-1 matvec of the mixed solve
+            std::vector<double> c = coef_concat(lv->Lx, P.dim == 2 ? &lv->Ly : nullptr);
+            std::vector<float2> t;
+            for (double v : c) t.push_back(df_pack_host(lv->w.a * v));
+            for (double v : c) t.push_back(df_pack_host(lv->w.b * v));
+            MKCK(lv->cdf.alloc(sizeof(float2) * t.size()));
+            MKCK(cudaMemcpy(lv->cdf.p, t.data(), sizeof(float2) * t.size(), cudaMemcpyHostToDevice));
+        }
         if (st != MK_OK) return st;
         lv->stride = lv->g.len;
         const size_t len = (size_t)lv->g.len;
@@ -260,7 +278,10 @@ mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out) {
 template <typename Tc>
 void enqueue_coarsest_t(Hierarchy &H, const int *done, cudaStream_t s) {
     Level &C = *H.lv.back();
-    if (C.g.dim == 1)
+    if (C.g.dim == 1 && C.spikeU > 0)
+        launch_slab_1d_warp<Tc>(C.g, C.w.b, C.spike.as<Tc>(), C.spikeU, H.key.n_cgs, C.R.as<Tc>(),
+                                C.X.as<Tc>(), done, s, PROF_SLAB);
+    else if (C.g.dim == 1)
         launch_slab_1d<Tc>(C.g, C.w.b, op_of<Tc>(C), C.alpha.as<Tc>(), C.gamma.as<Tc>(),
                            C.binv.as<Tc>(), C.npad, C.nlev, H.key.n_cgs, C.R.as<Tc>(), C.X.as<Tc>(),
                            done, s);
@@ -288,6 +309,34 @@ static void set_ctx(const Level &L, int level) {
     prof_set_context(level + 1, t_outer_j, (double)L.g.interior());
 }
 
+// x_j = sigma_j V_j - Z vt and w = A x_j (K4).  Level 1 of the mixed solve keeps V and w as
+// double-float pairs and evaluates w in double-float arithmetic.
+template <typename Tv, typename Tc, typename Tx, typename Tw, typename Tcw>
+struct InterpStep {
+    static void run(Level &L, Level &C, const Tv *vj, const double *sig, const Tc *Xc, int mc,
+                    const double *yc, int j, const int *done, cudaStream_t s) {
+        launch_interp<Tv, Tc, Tx, Tw, Tcw>(L.g, C.g, L.nu, L.space, L.w, op_of<Tcw>(L), vj, sig, Xc,
+                                           mc, C.stride, yc, L.X.as<Tx>() + (int64_t)j * L.stride,
+                                           L.W.as<Tw>(), done, s);
+    }
+};
+template <>
+struct InterpStep<float2, float, float, float2, double> {
+    static void run(Level &L, Level &C, const float2 *vj, const double *sig, const float *Xc,
+                    int mc, const double *yc, int j, const int *done, cudaStream_t s) {
+        const int64_t nc = 3 * (int64_t)L.g.nx + (L.g.dim == 2 ? 3 * (int64_t)L.g.ny : 0);
+        const float2 *ca = L.cdf.as<float2>();
+        launch_interp_df(L.g, C.g, L.nu, L.space, ca, ca + nc, L.w.b != 0.0, vj, sig, Xc, mc,
+                         C.stride, yc, L.X.as<float>() + (int64_t)j * L.stride, L.W.as<float2>(),
+                         done, s);
+    }
+};
+template <typename Tv, typename Tc, typename Tx, typename Tw, typename Tcw>
+static void interp_step(Level &L, Level &C, const Tv *vj, const double *sig, const Tc *Xc, int mc,
+                        const double *yc, int j, const int *done, cudaStream_t s) {
+    InterpStep<Tv, Tc, Tx, Tw, Tcw>::run(L, C, vj, sig, Xc, mc, yc, j, done, s);
+}
+
 template <typename Tc, typename Tv, typename Tx, typename Tw, typename Tcw>
 static void cycle_step_t(Hierarchy &H, int l, int j, const int *done, cudaStream_t s) {
     Level &L = *H.lv[l];
@@ -311,9 +360,7 @@ static void cycle_step_t(Hierarchy &H, int l, int j, const int *done, cudaStream
     const Tc *Xc = C.X.as<Tc>();
     const double *yc = C.coarsest ? nullptr : C.ks.y();
     int mc = C.coarsest ? 1 : C.m;
-    launch_interp<Tv, Tc, Tx, Tw, Tcw>(L.g, C.g, L.nu, L.space, L.w, op_of<Tcw>(L), vj, sig, Xc, mc,
-                                       C.stride, yc, L.X.as<Tx>() + (int64_t)j * L.stride,
-                                       L.W.as<Tw>(), done, s);
+    interp_step<Tv, Tc, Tx, Tw, Tcw>(L, C, vj, sig, Xc, mc, yc, j, done, s);
 }
 
 template <typename Tc>
@@ -334,7 +381,7 @@ void enqueue_cycle_step(Hierarchy &H, int l, int j, const int *done, cudaStream_
     if (H.precision == 0) {
         cycle_step_t<double, double, double, double, double>(H, l, j, done, s);
     } else if (l == 0) {
-        cycle_step_t<float, double, float, double, double>(H, l, j, done, s);
+        cycle_step_t<float, float2, float, float2, double>(H, l, j, done, s);
     } else {
         cycle_step_t<float, float, float, float, float>(H, l, j, done, s);
     }
@@ -346,30 +393,47 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s) {
     Level &L = *H.lv[0];
     const int *done = L.ks.flags;
     const int64_t len = L.g.len;
+    const bool fp64 = H.precision == 0;
     double *V = L.V.as<double>();
     double *W = L.W.as<double>();
+    float2 *Vd = L.V.as<float2>();
+    float2 *Wd = L.W.as<float2>();
     for (int j = 0; j < L.m; ++j) {
         t_outer_j = j;
         enqueue_cycle_step(H, 0, j, done, s);
         set_ctx(L, 0);
         const int orth = H.key.orth;
         const int mode = orth == 0 ? UPD_GIVENS : (orth == 2 ? UPD_GIVENS | UPD_REORTH_ALWAYS : UPD_OUTER);
-        launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, false, done, s);
-        launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, mode, false, done, s);
+        if (fp64) {
+            launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, false, done, s);
+            launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, mode, false, done,
+                                          s);
+        } else {
+            launch_multidot_df(len, Wd, Vd, L.stride, j, H.rs, L.ks, false, done, s);
+            launch_update_df(len, Wd, Vd, L.stride, j, H.rs, L.ks, mode, false, done, s);
+        }
         if (orth != 0) {
-            launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, true, done, s);
-            launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, UPD_GIVENS, true,
-                                          done, s);
+            if (fp64) {
+                launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, true, done, s);
+                launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, UPD_GIVENS,
+                                              true, done, s);
+            } else {
+                launch_multidot_df(len, Wd, Vd, L.stride, j, H.rs, L.ks, true, done, s);
+                launch_update_df(len, Wd, Vd, L.stride, j, H.rs, L.ks, UPD_GIVENS, true, done, s);
+            }
         }
     }
     t_outer_j = -1;
     set_ctx(L, 0);
-    if (H.precision == 0)
+    if (fp64) {
         launch_combine<double>(len, H.u.as<double>(), L.X.as<double>(), L.stride, L.ks, s);
-    else
+        launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), V, H.rs, 0, L.ks,
+                        EPI_OUTER_START, s);
+    } else {
         launch_combine<float>(len, H.u.as<double>(), L.X.as<float>(), L.stride, L.ks, s);
-    launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), V, H.rs, 0, L.ks,
-                    EPI_OUTER_START, s);
+        launch_residual_df(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), Vd, H.rs, 0, L.ks,
+                           EPI_OUTER_START, s);
+    }
 }
 
 void release_pairs(std::vector<ProfPair> &pairs);
@@ -433,8 +497,12 @@ mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const doub
     // r_0 = f (u^0 = 0): ||f||, tol * ||f||, v_1
     t_outer_j = -1;
     set_ctx(L, 0);
-    launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<double>(), H.rs,
-                    0, L.ks, EPI_OUTER_INIT, s);
+    if (H.precision == 0)
+        launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<double>(),
+                        H.rs, 0, L.ks, EPI_OUTER_INIT, s);
+    else
+        launch_residual_df(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<float2>(),
+                           H.rs, 0, L.ks, EPI_OUTER_INIT, s);
     // one restart cycle as a CUDA graph (captured once per hierarchy and profiling mode)
     if (o.use_graph && (!H.graph || H.graph_profiled != prof_enabled())) {
         mk_status st = capture_cycle(P, H);
@@ -524,6 +592,12 @@ mk_status prepare_march(Problem &P) {
         MKCK(upload<double>(P.m_alpha, al));
         MKCK(upload<double>(P.m_gamma, ga));
         MKCK(upload<double>(P.m_binv, bi));
+        if (slab_warp_supported<double>(P.nx)) {
+            P.m_spikeU = spike_block_size(P.nx);
+            std::vector<double> tab;
+            spike_tables(Lx, a, P.m_spikeU, tab);
+            MKCK(upload<double>(P.m_spike, tab));
+        }
     } else {
         if (P.nx > 48 || P.ny > 48) return MK_ERR_INVALID;
         std::vector<double> lx, Sx, Sxi, ly, Sy, Syi;

@@ -46,6 +46,7 @@ struct Level {
     int m = 0;         // restart (level 1) or fixed iterations (intermediate levels)
     bool coarsest = false;
     DevMem c64, c32;   // [3nx | 3ny] coefficients
+    DevMem cdf;        // mixed level 1: double-float a*L then b*L, each [3nx | 3ny]
     SpaceOp<double> op64{nullptr, nullptr};
     SpaceOp<float> op32{nullptr, nullptr};
     // vectors (level 1: V, W in FP64, X in the cycle precision; others in cycle precision)
@@ -58,6 +59,8 @@ struct Level {
     DevMem R;          // coarsest right-hand side
     DevMem alpha, gamma, binv;
     int npad = 0, nlev = 0;
+    DevMem spike;      // one-warp partitioned solver tables (1D), spikeU = rows per lane
+    int spikeU = 0;
     DevMem Sx, Sxi, lamx, Sy, Syi, lamy;
 };
 
@@ -86,6 +89,8 @@ struct Problem {
     bool march_ready = false;
     DevMem m_c64, m_alpha, m_gamma, m_binv, m_Sx, m_Sxi, m_lamx, m_Sy, m_Syi, m_lamy;
     int m_npad = 0, m_nlev = 0;
+    DevMem m_spike;
+    int m_spikeU = 0;
 };
 
 template <typename T>

@@ -12,67 +12,9 @@
 // coalesced along i (the contiguous direction of the padded layout).
 #include "kernels.h"
 #include "reduce.cuh"
+#include "stencil_common.cuh"
 
 namespace mk {
-
-// ---------------------------------------------------------------------------------------
-// helpers
-// ---------------------------------------------------------------------------------------
-template <int DIM, typename Tc, typename Tin>
-__device__ __forceinline__ Tc lap_at(const Tin *__restrict__ x, int64_t idx, int i, int j,
-                                     const Geom &g, const Tc *__restrict__ cx,
-                                     const Tc *__restrict__ cy) {
-    Tc v = (Tc)x[idx];
-    Tc s = cx[g.nx + i] * v + cx[i] * (Tc)x[idx - 1] + cx[2 * g.nx + i] * (Tc)x[idx + 1];
-    if (DIM == 2) {
-        Tc sy = cy[g.ny + j] * v + cy[j] * (Tc)x[idx - g.ldx] + cy[2 * g.ny + j] * (Tc)x[idx + g.ldx];
-        s = s + sy;
-    }
-    return s;
-}
-
-static int choose_kc(int64_t npts, int nsteps) {
-    // enough threads to fill the GPU a few times over; at most 32 steps per thread, and
-    // never more than 60000 blocks in a launch (the reduction partials hold 65536)
-    int64_t target = (int64_t)g_num_sms * 2048;
-    int64_t kc = (npts * nsteps) / (target > 0 ? target : 1);
-    if (kc < 1) kc = 1;
-    if (kc > 32) kc = 32;
-    int64_t blocks_per_chunk = (npts + 255) / 256 + 1;
-    while (blocks_per_chunk * ((nsteps + kc - 1) / kc) > 60000) ++kc;
-    return (int)kc;
-}
-
-struct Launch2 {
-    dim3 grid, block;
-};
-
-// thread -> spatial point (i, j); block/grid cover (nx, ny) x chunks
-static Launch2 point_launch(int dim, int nx, int ny, int nchunks) {
-    Launch2 L;
-    if (dim == 1) {
-        int bx = nx >= 256 ? 256 : ((nx + 31) / 32) * 32;
-        L.block = dim3(bx, 1, 1);
-        L.grid = dim3((nx + bx - 1) / bx, nchunks, 1);
-    } else {
-        L.block = dim3(32, 8, 1);
-        L.grid = dim3((nx + 31) / 32, (ny + 7) / 8, nchunks);
-    }
-    return L;
-}
-
-template <int DIM>
-__device__ __forceinline__ bool point_index(int &i, int &j, int &chunk) {
-    i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (DIM == 1) {
-        j = 0;
-        chunk = blockIdx.y;
-    } else {
-        j = blockIdx.y * blockDim.y + threadIdx.y;
-        chunk = blockIdx.z;
-    }
-    return true;
-}
 
 // ---------------------------------------------------------------------------------------
 // layout conversion
@@ -86,7 +28,7 @@ __global__ void k_pack(Geom g, const Tsrc *__restrict__ dense, Tdst *__restrict_
         int64_t k = e / npts;
         int64_t r = e - k * npts;
         int j = (int)(r / g.nx), i = (int)(r - (int64_t)j * g.nx);
-        padded[g.at((int)k, j, i)] = (Tdst)dense[e];
+        padded[g.at((int)k, j, i)] = cvt_to<Tdst>(dense[e]);
     }
 }
 
@@ -99,7 +41,7 @@ __global__ void k_unpack(Geom g, const Tsrc *__restrict__ padded, Tdst *__restri
         int64_t k = e / npts;
         int64_t r = e - k * npts;
         int j = (int)(r / g.nx), i = (int)(r - (int64_t)j * g.nx);
-        dense[e] = (Tdst)padded[g.at((int)k, j, i)];
+        dense[e] = cvt_to<Tdst>(padded[g.at((int)k, j, i)]);
     }
 }
 
@@ -110,13 +52,6 @@ __global__ void k_convert(int64_t n, const Tsrc *__restrict__ src, Tdst *__restr
         dst[e] = (Tdst)src[e];
 }
 
-static int grid_for(int64_t n, int block) {
-    int64_t g = (n + block - 1) / block;
-    int64_t cap = (int64_t)g_num_sms * 16;
-    if (g > cap) g = cap;
-    if (g < 1) g = 1;
-    return (int)g;
-}
 
 template <typename Tsrc, typename Tdst>
 void launch_pack(const Geom &g, const Tsrc *dense, Tdst *padded, cudaStream_t s) {
@@ -172,13 +107,13 @@ __global__ void __launch_bounds__(256) k_apply(Geom g, Tc a, Tc b, SpaceOp<Tc> L
     Tc prev = 0, Lprev = 0;
     if (k0 > 0) {
         int64_t idx = g.at(k0 - 1, j, i);
-        prev = (Tc)x[idx];
+        prev = ldv<Tc>(x, idx);
         Lprev = lap_at<DIM, Tc>(x, idx, i, j, g, L.x, L.y);
     }
 #pragma unroll 4
     for (int k = k0; k < k1; ++k) {
         int64_t idx = g.at(k, j, i);
-        Tc cur = (Tc)x[idx];
+        Tc cur = ldv<Tc>(x, idx);
         Tc Lc = lap_at<DIM, Tc>(x, idx, i, j, g, L.x, L.y);
         Tc r = (k == 0) ? cur : (cur - a * Lc) - (prev + b * Lprev);
         w[idx] = (Tout)r;
@@ -303,7 +238,7 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu, Tc a
                     Lprev[q][p] = 0;
                     if (p < npx && q < npy) {
                         int64_t idx = gf.at(kf, jj[q], ii[p]);
-                        prev[q][p] = (Tc)v[idx];
+                        prev[q][p] = ldv<Tc>(v, idx);
                         Lprev[q][p] = lap_at<DIM, Tc>(v, idx, ii[p], jj[q], gf, L.x, L.y);
                     }
                 }
@@ -317,7 +252,7 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu, Tc a
                     for (int p = 0; p < PX; ++p) {
                         if (p < npx && q < npy) {
                             int64_t idx = gf.at(0, jj[q], ii[p]);
-                            Tc cur = (Tc)v[idx];
+                            Tc cur = ldv<Tc>(v, idx);
                             sum += cur - mu * cur;
                             prev[q][p] = cur;
                             Lprev[q][p] = lap_at<DIM, Tc>(v, idx, ii[p], jj[q], gf, L.x, L.y);
@@ -332,7 +267,7 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu, Tc a
                         for (int p = 0; p < PX; ++p) {
                             if (p < npx && q < npy) {
                                 int64_t idx = gf.at(kf, jj[q], ii[p]);
-                                Tc cur = (Tc)v[idx];
+                                Tc cur = ldv<Tc>(v, idx);
                                 Tc Lc = lap_at<DIM, Tc>(v, idx, ii[p], jj[q], gf, L.x, L.y);
                                 Tc Av = (cur - a * Lc) - (prev[q][p] + b * Lprev[q][p]);
                                 sum += Av - mu * cur;
@@ -344,6 +279,94 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu, Tc a
             }
             Tc outv = scale * (sum * inv_count);
             vhat[gc.at(K, J, I)] = (Tout)outv;
+            acc2 += (double)outv * (double)outv;
+        }
+    }
+    if (ks.d) block_partial_and_finish(acc2, rs, slot, ks, EPI_BETA);
+}
+
+// 1D specialisation of K3: one thread per coarse column; each fine value is loaded once and
+// its spatial neighbours come from the adjacent lanes (warp shuffles; the two edge lanes of
+// a warp load their outer neighbour).  With agglomeration a thread owns the fine pair
+// (2I, 2I+1).  Every lane of a warp runs the loop (lanes past the grid carry zeros).
+template <bool SPACE, typename Tin, typename Tout, typename Tc>
+__global__ void __launch_bounds__(256) k_restrict_1d(Geom gf, Geom gc, int nu, Tc a, Tc b, Tc mu,
+                                                     SpaceOp<Tc> L, const Tin *__restrict__ v,
+                                                     const double *__restrict__ sigma,
+                                                     Tout *__restrict__ vhat, int kc,
+                                                     ReduceScratch rs, int slot, KState ks,
+                                                     const int *__restrict__ done) {
+    if (done && *done) return;
+    const unsigned FULL = 0xffffffffu;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int nf = gf.nx;
+    const bool active = I < gc.nx;
+    const int p0 = SPACE ? 2 * I : I;           // fine points of this column
+    const int p1 = SPACE ? 2 * I + 1 : I;
+    const bool has0 = p0 < nf, has1 = SPACE && p1 < nf;
+    const Tc *cx = L.x;
+    const Tc lo0 = has0 ? cx[p0] : (Tc)0, di0 = has0 ? cx[nf + p0] : (Tc)0, up0 = has0 ? cx[2 * nf + p0] : (Tc)0;
+    const Tc lo1 = has1 ? cx[p1] : (Tc)0, di1 = has1 ? cx[nf + p1] : (Tc)0, up1 = has1 ? cx[2 * nf + p1] : (Tc)0;
+    const Tc inv_count = SPACE ? ((Tc)1 / (Tc)(has1 ? 2 : 1)) : (Tc)1;
+    const Tc scale = sigma ? (Tc)(*sigma) : (Tc)1;
+    auto fine = [&](int k, int p) -> Tc { return (p >= 0 && p < nf) ? ldv<Tc>(v, gf.at(k, 0, p)) : (Tc)0; };
+    // values and Laplacians of the thread's fine points at fine step k
+    auto row = [&](int k, Tc &c0, Tc &c1, Tc &l0, Tc &l1) {
+        c0 = has0 ? ldv<Tc>(v, gf.at(k, 0, p0)) : (Tc)0;
+        c1 = has1 ? ldv<Tc>(v, gf.at(k, 0, p1)) : (Tc)0;
+        Tc left, right;
+        if (SPACE) {
+            left = __shfl_up_sync(FULL, c1, 1);
+            right = __shfl_down_sync(FULL, c0, 1);
+            if (lane == 0) left = fine(k, p0 - 1);
+            if (lane == 31) right = fine(k, p1 + 1);
+            l0 = di0 * c0 + lo0 * left + up0 * c1;
+            l1 = di1 * c1 + lo1 * c0 + up1 * right;
+        } else {
+            left = __shfl_up_sync(FULL, c0, 1);
+            right = __shfl_down_sync(FULL, c0, 1);
+            if (lane == 0) left = fine(k, p0 - 1);
+            if (lane == 31) right = fine(k, p0 + 1);
+            l0 = di0 * c0 + lo0 * left + up0 * right;
+            l1 = (Tc)0;
+        }
+    };
+    double acc2 = 0.0;
+    const int K0 = blockIdx.y * kc;
+    const int K1 = min(K0 + kc, gc.nt + 1);
+    Tc pr0 = 0, pr1 = 0, Lp0 = 0, Lp1 = 0;
+    if (K0 > 0) row(nu * (K0 - 1), pr0, pr1, Lp0, Lp1);
+    for (int K = K0; K < K1; ++K) {
+        Tc sum = 0;
+        if (K == 0) {
+            Tc c0, c1, l0, l1;
+            row(0, c0, c1, l0, l1);
+            sum = (c0 - mu * c0) + (c1 - mu * c1);
+            pr0 = c0;
+            pr1 = c1;
+            Lp0 = l0;
+            Lp1 = l1;
+        } else {
+            for (int st = 1; st <= nu; ++st) {
+                const int kf = nu * (K - 1) + st;
+                Tc c0, c1, l0, l1;
+                row(kf, c0, c1, l0, l1);
+                Tc Av0 = (c0 - a * l0) - (pr0 + b * Lp0);
+                sum += Av0 - mu * c0;
+                if (SPACE) {
+                    Tc Av1 = (c1 - a * l1) - (pr1 + b * Lp1);
+                    sum += Av1 - mu * c1;
+                }
+                pr0 = c0;
+                pr1 = c1;
+                Lp0 = l0;
+                Lp1 = l1;
+            }
+        }
+        if (active) {
+            Tc outv = scale * (sum * inv_count);
+            vhat[gc.at(K, 0, I)] = (Tout)outv;
             acc2 += (double)outv * (double)outv;
         }
     }
@@ -362,13 +385,17 @@ void launch_restrict(const Geom &gf, const Geom &gc, int nu, bool space, const W
 #define MK_RESTRICT(D, S) \
     k_restrict<D, S, Tin, Tout, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, nu, a, b, mu, L, v, sigma, \
                                                                 vhat, kc, rs, slot, ks_c, done)
+#define MK_RESTRICT1(S) \
+    k_restrict_1d<S, Tin, Tout, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, nu, a, b, mu, L, v, sigma, \
+                                                                vhat, kc, rs, slot, ks_c, done)
     prof_begin(s);
     if (gf.dim == 1) {
-        if (space) MK_RESTRICT(1, true); else MK_RESTRICT(1, false);
+        if (space) MK_RESTRICT1(true); else MK_RESTRICT1(false);
     } else {
         if (space) MK_RESTRICT(2, true); else MK_RESTRICT(2, false);
     }
 #undef MK_RESTRICT
+#undef MK_RESTRICT1
     prof_end(s, PROF_RESTRICT, (double)gf.interior() * sizeof(Tin) + (double)gc.interior() * sizeof(Tout));
     count_launch();
 }
@@ -402,7 +429,9 @@ struct XEval {
             zt = (Tx)Xc[cidx];
         } else {
             zt = (Tx)0;
-            for (int m = 0; m < mc; ++m) zt += y[m] * (Tx)Xc[cidx + m * xc_stride];
+#pragma unroll
+            for (int m = 0; m < MK_MAX_INNER; ++m)
+                if (m < mc) zt += y[m] * (Tx)Xc[cidx + m * xc_stride];
         }
         return sigma * (Tx)v[gf.at(k, j, i)] - zt;
     }
@@ -461,6 +490,89 @@ __global__ void __launch_bounds__(256) k_interp(Geom gf, Geom gc, int nu, Tc a, 
     }
 }
 
+// 1D specialisation of K4: x is formed once per point and its spatial neighbours come from
+// the adjacent lanes (warp shuffles).  Row base pointers and the coarse block index K(k)
+// are advanced once per time step (no division per point), and the combination
+// vt = sum_m y_m Xc_m is specialised on the number of coarse directions MC (0: a single
+// vector with coefficient 1; 1; 2; -1: any count up to MK_MAX_INNER).
+template <bool SPACE, int MC, typename Tv, typename Tz, typename Tx, typename Tw, typename Tc>
+__global__ void __launch_bounds__(256) k_interp_1d(Geom gf, Geom gc, int nu, Tc a, Tc b,
+                                                   SpaceOp<Tc> L, const Tv *__restrict__ v,
+                                                   const double *__restrict__ sigma,
+                                                   const Tz *__restrict__ Xc, int mc,
+                                                   int64_t xc_stride,
+                                                   const double *__restrict__ yc,
+                                                   Tx *__restrict__ xout, Tw *__restrict__ wout,
+                                                   int kc, const int *__restrict__ done) {
+    if (done && *done) return;
+    const unsigned FULL = 0xffffffffu;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int nx = gf.nx;
+    const bool act = i < nx;
+    const Tx sig = sigma ? (Tx)(*sigma) : (Tx)1;
+    constexpr int NY = MC > 0 ? MC : MK_MAX_INNER;
+    Tx y[NY];
+#pragma unroll
+    for (int m = 0; m < NY; ++m) y[m] = (yc && m < mc) ? (Tx)yc[m] : (Tx)0;
+    const Tc *cx = L.x;
+    const Tc clo = act ? cx[i] : (Tc)0, cdi = act ? cx[nx + i] : (Tc)0,
+             cup = act ? cx[2 * nx + i] : (Tc)0;
+    auto xval = [&](const Tv *vr, const Tz *zr, int ii) -> Tx {
+        if (ii < 0 || ii >= nx) return (Tx)0;
+        const Tz *zp = zr + (SPACE ? (ii >> 1) : ii);
+        Tx zt;
+        if (MC == 0) {
+            zt = (Tx)zp[0];
+        } else if (MC == 1) {
+            zt = y[0] * (Tx)zp[0];
+        } else if (MC == 2) {
+            zt = y[0] * (Tx)zp[0] + y[NY > 1 ? 1 : 0] * (Tx)zp[xc_stride];
+        } else {
+            zt = (Tx)0;
+#pragma unroll
+            for (int m = 0; m < NY; ++m)
+                if (m < mc) zt += y[m] * (Tx)zp[m * xc_stride];
+        }
+        return sig * ldv<Tx>(vr, ii) - zt;
+    };
+    const int k0 = blockIdx.y * kc;
+    const int k1 = min(k0 + kc, gf.nt + 1);
+    const int kstart = k0 > 0 ? k0 - 1 : 0;
+    // coarse block of fine step k: 0 for k = 0, (k-1)/nu + 1 otherwise (tracked incrementally)
+    int K = (kstart == 0) ? 0 : (kstart - 1) / nu + 1;
+    int ph = (kstart == 0) ? nu - 1 : (kstart - 1) % nu;
+    Tc prev = 0, Lprev = 0;
+    for (int k = kstart; k < k1; ++k) {
+        if (k > kstart) {
+            if (ph == nu - 1) {
+                ++K;
+                ph = 0;
+            } else {
+                ++ph;
+            }
+        }
+        const Tv *vr = v + gf.guard + (int64_t)k * gf.plane;
+        const Tz *zr = Xc + gc.guard + (int64_t)K * gc.plane;
+        Tx xc = xval(vr, zr, i);
+        Tx xl = __shfl_up_sync(FULL, xc, 1), xr = __shfl_down_sync(FULL, xc, 1);
+        if (lane == 0) xl = xval(vr, zr, i - 1);
+        if (lane == 31) xr = xval(vr, zr, i + 1);
+        Tc cur = (Tc)xc;
+        Tc Lc = cdi * cur + clo * (Tc)xl + cup * (Tc)xr;
+        if (k >= k0) {
+            Tc r = (k == 0) ? cur : (cur - a * Lc) - (prev + b * Lprev);
+            if (act) {
+                int64_t idx = gf.guard + (int64_t)k * gf.plane + i;
+                xout[idx] = xc;
+                wout[idx] = (Tw)r;
+            }
+        }
+        prev = cur;
+        Lprev = Lc;
+    }
+}
+
 template <typename Tv, typename Tz, typename Tx, typename Tw, typename Tc>
 void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Weights &w,
                    SpaceOp<Tc> L, const Tv *v, const double *sigma, const Tz *Xc, int mc,
@@ -474,13 +586,26 @@ void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Wei
     k_interp<D, S, Tv, Tz, Tx, Tw, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, nu, a, b, L, v, sigma, \
                                                                   Xc, mc, xc_stride, yc, x, wout, \
                                                                   kc, done)
+#define MK_INTERP1M(S, M)                                                                     \
+    k_interp_1d<S, M, Tv, Tz, Tx, Tw, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, nu, a, b, L, v,     \
+                                                                     sigma, Xc, mc, xc_stride, yc, \
+                                                                     x, wout, kc, done)
+#define MK_INTERP1(S)                                                                         \
+    do {                                                                                      \
+        if (!yc) MK_INTERP1M(S, 0);                                                           \
+        else if (mc == 1) MK_INTERP1M(S, 1);                                                  \
+        else if (mc == 2) MK_INTERP1M(S, 2);                                                  \
+        else MK_INTERP1M(S, -1);                                                              \
+    } while (0)
     prof_begin(s);
     if (gf.dim == 1) {
-        if (space) MK_INTERP(1, true); else MK_INTERP(1, false);
+        if (space) MK_INTERP1(true); else MK_INTERP1(false);
     } else {
         if (space) MK_INTERP(2, true); else MK_INTERP(2, false);
     }
 #undef MK_INTERP
+#undef MK_INTERP1
+#undef MK_INTERP1M
     prof_end(s, PROF_INTERP, (double)gf.interior() * (sizeof(Tv) + sizeof(Tx) + sizeof(Tw)) +
                                  (double)mc * gc.interior() * sizeof(Tz));
     count_launch();
@@ -581,6 +706,8 @@ template void launch_pack<double, double>(const Geom &, const double *, double *
 template void launch_pack<double, float>(const Geom &, const double *, float *, cudaStream_t);
 template void launch_unpack<double, double>(const Geom &, const double *, double *, cudaStream_t);
 template void launch_unpack<float, double>(const Geom &, const float *, double *, cudaStream_t);
+template void launch_pack<double, float2>(const Geom &, const double *, float2 *, cudaStream_t);
+template void launch_unpack<float2, double>(const Geom &, const float2 *, double *, cudaStream_t);
 template void launch_convert<double, float>(int64_t, const double *, float *, cudaStream_t);
 template void launch_convert<float, double>(int64_t, const float *, double *, cudaStream_t);
 
@@ -599,6 +726,12 @@ template void launch_restrict<double, double, double>(const Geom &, const Geom &
 template void launch_restrict<double, float, float>(const Geom &, const Geom &, int, bool,
                                                     const Weights &, SpaceOp<float>,
                                                     const double *, const double *, float *,
+                                                    const ReduceScratch &, int, KState,
+                                                    const int *, cudaStream_t);
+// mixed, level 1 with the basis in double-float pairs
+template void launch_restrict<float2, float, float>(const Geom &, const Geom &, int, bool,
+                                                    const Weights &, SpaceOp<float>,
+                                                    const float2 *, const double *, float *,
                                                     const ReduceScratch &, int, KState,
                                                     const int *, cudaStream_t);
 template void launch_restrict<float, float, float>(const Geom &, const Geom &, int, bool,

@@ -1,0 +1,102 @@
+// Helpers shared by the space-time stencil kernels (see stencil.cu).
+#pragma once
+
+#include "kernels.h"
+
+namespace mk {
+
+// ---------------------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------------------
+// load an element in the arithmetic type; a double-float pair (float2) is read as its
+// leading float (the value rounded to FP32)
+// conversions used by the layout kernels; a double becomes a double-float pair (hi, lo)
+template <typename Td, typename Ts>
+__device__ __forceinline__ Td cvt_to(Ts v) {
+    return (Td)v;
+}
+template <>
+__device__ __forceinline__ float2 cvt_to<float2, double>(double v) {
+    float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+template <>
+__device__ __forceinline__ double cvt_to<double, float2>(float2 v) {
+    return (double)v.x + (double)v.y;
+}
+
+template <typename Tc, typename T>
+__device__ __forceinline__ Tc ldv(const T *__restrict__ p, int64_t i) {
+    return (Tc)p[i];
+}
+template <>
+__device__ __forceinline__ float ldv<float, float2>(const float2 *__restrict__ p, int64_t i) {
+    return p[i].x;
+}
+
+template <int DIM, typename Tc, typename Tin>
+__device__ __forceinline__ Tc lap_at(const Tin *__restrict__ x, int64_t idx, int i, int j,
+                                     const Geom &g, const Tc *__restrict__ cx,
+                                     const Tc *__restrict__ cy) {
+    Tc v = ldv<Tc>(x, idx);
+    Tc s = cx[g.nx + i] * v + cx[i] * ldv<Tc>(x, idx - 1) + cx[2 * g.nx + i] * ldv<Tc>(x, idx + 1);
+    if (DIM == 2) {
+        Tc sy = cy[g.ny + j] * v + cy[j] * ldv<Tc>(x, idx - g.ldx) + cy[2 * g.ny + j] * ldv<Tc>(x, idx + g.ldx);
+        s = s + sy;
+    }
+    return s;
+}
+
+static inline int choose_kc(int64_t npts, int nsteps) {
+    // enough threads to fill the GPU a few times over; at most 32 steps per thread, and
+    // never more than 60000 blocks in a launch (the reduction partials hold 65536)
+    int64_t target = (int64_t)g_num_sms * 2048;
+    int64_t kc = (npts * nsteps) / (target > 0 ? target : 1);
+    if (kc < 1) kc = 1;
+    if (kc > 32) kc = 32;
+    int64_t blocks_per_chunk = (npts + 255) / 256 + 1;
+    while (blocks_per_chunk * ((nsteps + kc - 1) / kc) > 60000) ++kc;
+    return (int)kc;
+}
+
+struct Launch2 {
+    dim3 grid, block;
+};
+
+// thread -> spatial point (i, j); block/grid cover (nx, ny) x chunks
+static inline Launch2 point_launch(int dim, int nx, int ny, int nchunks) {
+    Launch2 L;
+    if (dim == 1) {
+        int bx = nx >= 256 ? 256 : ((nx + 31) / 32) * 32;
+        L.block = dim3(bx, 1, 1);
+        L.grid = dim3((nx + bx - 1) / bx, nchunks, 1);
+    } else {
+        L.block = dim3(32, 8, 1);
+        L.grid = dim3((nx + 31) / 32, (ny + 7) / 8, nchunks);
+    }
+    return L;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool point_index(int &i, int &j, int &chunk) {
+    i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (DIM == 1) {
+        j = 0;
+        chunk = blockIdx.y;
+    } else {
+        j = blockIdx.y * blockDim.y + threadIdx.y;
+        chunk = blockIdx.z;
+    }
+    return true;
+}
+
+
+static inline int grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    int64_t cap = (int64_t)g_num_sms * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace mk
