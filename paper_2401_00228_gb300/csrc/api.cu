@@ -672,7 +672,7 @@ static mk_status op_coarsest_t(Hierarchy &H, const double *dr, double *dx, cudaS
         if (slab_warp_supported<T>(C.g.nx)) {
             const int U = spike_block_size(C.g.nx);
             std::vector<double> tab;
-            spike_tables(C.Lx, C.w.a, U, tab);
+            spike_tables(C.Lx, C.w.a, U, spike_threads(C.g.nx), tab);
             DevMem sp;
             CK(up(sp, tab));
             launch_slab_1d_warp<T>(C.g, C.w.b, sp.as<T>(), U, H.key.n_cgs, rp.as<T>(), xp.as<T>(),

@@ -136,6 +136,7 @@ void launch_slab_1d(const Geom &g, double b, SpaceOp<T> L, const T *alpha, const
 // 1D, one warp per slab: partitioned solver with the tables of spike_tables() in T.
 // cls: PROF_SLAB or PROF_MARCH for the kernel-class timing.
 int spike_block_size(int n);
+int spike_threads(int n);
 template <typename T>
 bool slab_warp_supported(int n);
 template <typename T>

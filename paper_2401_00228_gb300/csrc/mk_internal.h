@@ -70,9 +70,10 @@ double tri_lambda_max_neg(const Tri &L);       // largest eigenvalue of -L
 int pcr_levels(int n);
 void pcr_tables(const Tri &L, double a, int npad, std::vector<double> &alpha,
                 std::vector<double> &gamma, std::vector<double> &binv);
-// Tables of the one-warp partitioned (spike) solver for I - aL with 32 blocks of U rows.
-int spike_items(int U);
-void spike_tables(const Tri &L, double a, int U, std::vector<double> &tab);
+// Tables of the partitioned (spike) slab solver for I - aL with P blocks of U rows.
+int spike_levels(int P);
+int spike_items(int U, int P);
+void spike_tables(const Tri &L, double a, int U, int P, std::vector<double> &tab);
 // Diagonalisation L = S diag(lam) S^{-1} (real: L is similar to a symmetric matrix).
 // S, Sinv row-major n x n.
 void tri_eigen(const Tri &L, std::vector<double> &lam, std::vector<double> &S,

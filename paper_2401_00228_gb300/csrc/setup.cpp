@@ -161,29 +161,37 @@ void pcr_tables(const Tri &L, double a, int npad, std::vector<double> &alpha,
     for (int i = 0; i < npad; ++i) binv[i] = 1.0 / B[i];
 }
 
-// Tables of the one-warp partitioned solver for M = I - aL (see slab.cu, k_slab_1d_warp).
-// The system is padded to 32*U rows (identity beyond n) and split into 32 blocks of U
-// rows, one per lane.  Per lane p (rows pU .. pU+U-1), stored item-major (item*32 + p):
+// Tables of the partitioned (spike) slab solver for M = I - aL (see slab.cu,
+// k_slab_1d_spike).  The system is padded to P*U rows (identity beyond n) and split into P
+// blocks of U rows, one per thread (P = 32 * warps).  Per thread p (rows pU .. pU+U-1),
+// stored item-major (item * P + p):
 //   m[U]     Thomas multipliers (m[0] unused)      uinv[U]  1 / pivots
 //   sup[U]   super-diagonal of the block            v[U], w[U]  spikes M_p^{-1} e_0, e_{U-1}
 //   lo, di, up [U each]  the rows of L (for the explicit part (I + bL) x_{k-1})
 //   A, C     couplings M[pU, pU-1], M[pU+U-1, pU+U]
-//   alpha[5][4], gamma[5][4]  2x2 block-PCR multipliers on the interface unknowns
-//                             (F_p, G_p) = (x[pU], x[pU+U-1]), strides 1, 2, 4, 8, 16
+//   alpha[nl][4], gamma[nl][4]  2x2 block-PCR multipliers on the interface unknowns
+//                               (F_p, G_p) = (x[pU], x[pU+U-1]), strides 1, 2, .., P/2
 //   dinv[4]  inverse of the final 2x2 diagonal block
-int spike_items(int U) { return 8 * U + 46; }
+// with nl = log2(P).
+int spike_levels(int P) {
+    int l = 0;
+    while ((1 << l) < P) ++l;
+    return l;
+}
 
-void spike_tables(const Tri &L, double a, int U, std::vector<double> &tab) {
+int spike_items(int U, int P) { return 8 * U + 2 + 8 * spike_levels(P) + 4; }
+
+void spike_tables(const Tri &L, double a, int U, int P, std::vector<double> &tab) {
     const int n = L.n();
-    const int P = 32;
     const int N = P * U;
+    const int nl = spike_levels(P);
     std::vector<double> sub(N, 0.0), dia(N, 1.0), sup(N, 0.0);
     for (int i = 0; i < n; ++i) {
         sub[i] = (i > 0) ? -a * L.lo[i] : 0.0;
         dia[i] = 1.0 - a * L.di[i];
         sup[i] = (i < n - 1) ? -a * L.up[i] : 0.0;
     }
-    const int items = spike_items(U);
+    const int items = spike_items(U, P);
     tab.assign((size_t)items * P, 0.0);
     auto T = [&](int item, int p) -> double & { return tab[(size_t)item * P + p]; };
     typedef std::array<double, 4> M2;   // row-major 2x2
@@ -241,7 +249,7 @@ void spike_tables(const Tri &L, double a, int U, std::vector<double> &tab) {
     };
     auto neg = [](const M2 &x) { return M2{-x[0], -x[1], -x[2], -x[3]}; };
     const M2 Z = {0.0, 0.0, 0.0, 0.0};
-    for (int l = 0; l < 5; ++l) {
+    for (int l = 0; l < nl; ++l) {
         const int s = 1 << l;
         std::vector<M2> D2(P), E2(P), H2(P);
         for (int p = 0; p < P; ++p) {
@@ -249,7 +257,7 @@ void spike_tables(const Tri &L, double a, int U, std::vector<double> &tab) {
             M2 ga = (p + s < P) ? neg(mul(Hm[p], inv(D[p + s]))) : Z;
             for (int e = 0; e < 4; ++e) {
                 T(8 * U + 2 + l * 4 + e, p) = al[e];
-                T(8 * U + 22 + l * 4 + e, p) = ga[e];
+                T(8 * U + 2 + 4 * nl + l * 4 + e, p) = ga[e];
             }
             D2[p] = D[p];
             if (p - s >= 0) D2[p] = add(D2[p], mul(al, Hm[p - s]));
@@ -263,7 +271,7 @@ void spike_tables(const Tri &L, double a, int U, std::vector<double> &tab) {
     }
     for (int p = 0; p < P; ++p) {
         M2 di = inv(D[p]);
-        for (int e = 0; e < 4; ++e) T(8 * U + 42 + e, p) = di[e];
+        for (int e = 0; e < 4; ++e) T(8 * U + 2 + 8 * nl + e, p) = di[e];
     }
 }
 

@@ -143,52 +143,58 @@ static void slab_1d_launch(const Geom &g, double b, SpaceOp<T> L, const T *alpha
 }
 
 // ---------------------------------------------------------------------------------------
-// 1D, one warp per slab: partitioned (spike) solver for the constant tridiagonal I - aL.
-// Lane p owns rows pU .. pU+U-1 (the system padded to 32U rows with identity rows):
-//   1. right-hand side r_k + (I + bL) x_{k-1} from the lane's own x_{k-1} values and one
-//      neighbour from each adjacent lane;
-//   2. Thomas on the lane's U x U block (precomputed multipliers and pivots): y = M_p^{-1} d;
+// 1D partitioned (spike) slab solver for the constant tridiagonal I - aL, one CTA of
+// P = 32*NW threads per slab.  Thread p owns rows pU .. pU+U-1 of the system padded to P*U
+// rows (identity rows beyond n).  Per time step:
+//   1. right-hand side r_k + (I + bL) x_{k-1} from the thread's own x_{k-1} values and one
+//      neighbour on each side;
+//   2. Thomas on the thread's U x U block (precomputed multipliers and pivots): y = M_p^{-1} d;
 //   3. the interface unknowns (F_p, G_p) = (x[pU], x[pU+U-1]) satisfy a block-tridiagonal
-//      system with 2x2 blocks, solved by block parallel cyclic reduction over the 32 lanes
-//      in five shuffle steps (strides 1..16, precomputed multipliers);
+//      system with 2x2 blocks, solved by block parallel cyclic reduction over the P threads
+//      (strides 1..16 by warp shuffles, larger strides through shared memory);
 //   4. x = y - A_p G_{p-1} v_p - C_p F_{p+1} w_p with the precomputed spikes v_p, w_p.
-// No block barrier is needed.  Rows are read and written coalesced through a padded shared
-// staging buffer, and the next right-hand side is prefetched during the current step.
-// Tables: spike_tables() in setup.cpp (item-major, 32 lanes per item).
+// The work per step is O(n) (Thomas) plus O(P log P) on the interfaces, against O(n log n)
+// for plain PCR, and only log2(P) - 5 block barriers are on the critical path.  Rows are
+// read and written coalesced through a padded shared staging buffer and the next
+// right-hand side is prefetched during the current step.  Tables: spike_tables().
 // ---------------------------------------------------------------------------------------
-template <typename T, int U>
-__global__ void __launch_bounds__(32) k_slab_1d_warp(Geom g, T b, const T *__restrict__ tab,
-                                                     int steps, int coupled,
-                                                     const T *__restrict__ r,
-                                                     T *__restrict__ x,
-                                                     const int *__restrict__ done) {
+template <int NW>
+struct SpikeLevels {
+    static constexpr int value = NW == 1 ? 5 : NW == 2 ? 6 : NW == 4 ? 7 : 8;
+};
+
+template <typename T, int U, int NW>
+__global__ void __launch_bounds__(32 * NW) k_slab_1d_spike(Geom g, T b, const T *__restrict__ tab,
+                                                           int steps, int coupled,
+                                                           const T *__restrict__ r,
+                                                           T *__restrict__ x,
+                                                           const int *__restrict__ done) {
     if (done && *done) return;
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int ITEMS = 8 * U + 46;
+    constexpr int P = 32 * NW;
+    constexpr int NL = SpikeLevels<NW>::value;
+    constexpr int ITEMS = 8 * U + 2 + 8 * NL + 4;
+    constexpr int NBUF = P * U + (P * U) / 32;
     extern __shared__ unsigned char smem_raw[];
-    T *tb = reinterpret_cast<T *>(smem_raw);   // ITEMS x 32
-    T *buf = tb + ITEMS * 32;                  // 32U values, one pad slot per 32
-    const int lane = threadIdx.x;
+    T *tb = reinterpret_cast<T *>(smem_raw);   // ITEMS x P
+    T *buf = tb + ITEMS * P;                   // staging, one pad slot per 32 values
+    T *ifc = buf + NBUF;                       // interface exchange [2 buffers][F|G][P]
+    const int t = threadIdx.x;
+    const int lane = t & 31;
     const int n = g.nx;
     const int slab = blockIdx.x;
     const int kbeg = 1 + slab * steps;
-    for (int e = lane; e < ITEMS * 32; e += 32) tb[e] = tab[e];
-    auto TB = [&](int item) -> T { return tb[item * 32 + lane]; };
+    for (int e = t; e < ITEMS * P; e += P) tb[e] = tab[e];
+    auto TB = [&](int item) -> T { return tb[item * P + t]; };
     auto sidx = [](int e) { return e + (e >> 5); };
     T pre[U];
     auto load_row = [&](int k) {
         const T *row = r + g.guard + (int64_t)k * g.plane;
 #pragma unroll
         for (int q = 0; q < U; ++q) {
-            const int e = q * 32 + lane;
+            const int e = q * P + t;
             pre[q] = (e < n) ? row[e] : (T)0;
         }
-    };
-    auto stage = [&]() {
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < U; ++q) buf[sidx(q * 32 + lane)] = pre[q];
-        __syncwarp();
     };
     T xp[U];
 #pragma unroll
@@ -199,30 +205,39 @@ __global__ void __launch_bounds__(32) k_slab_1d_warp(Geom g, T b, const T *__res
             T *row0 = x + g.guard;
 #pragma unroll
             for (int q = 0; q < U; ++q) {
-                const int e = q * 32 + lane;
+                const int e = q * P + t;
                 if (e < n) row0[e] = pre[q];
             }
         }
         if (coupled) {
-            stage();
 #pragma unroll
-            for (int q = 0; q < U; ++q) xp[q] = buf[sidx(lane * U + q)];
+            for (int q = 0; q < U; ++q) buf[sidx(q * P + t)] = pre[q];
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < U; ++q) xp[q] = buf[sidx(t * U + q)];
         }
     }
+    __syncthreads();   // tables loaded; buf holds x_0 when coupled
     load_row(kbeg);
+    int cur = 0;
     for (int s = 0; s < steps; ++s) {
         const int k = kbeg + s;
-        stage();
-        if (s + 1 < steps) load_row(k + 1);
         const bool first = (s == 0) && !coupled;
-        T xl = __shfl_up_sync(FULL, xp[U - 1], 1);
-        T xr = __shfl_down_sync(FULL, xp[0], 1);
-        if (lane == 0) xl = (T)0;
-        if (lane == 31) xr = (T)0;
+        // neighbours of x_{k-1} across the thread's block boundaries (buf holds x_{k-1})
+        T xl = (T)0, xr = (T)0;
+        if (!first) {
+            xl = (t > 0) ? buf[sidx(t * U - 1)] : (T)0;
+            xr = (t < P - 1) ? buf[sidx(t * U + U)] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < U; ++q) buf[sidx(q * P + t)] = pre[q];
+        __syncthreads();
+        if (s + 1 < steps) load_row(k + 1);
         T d[U];
 #pragma unroll
         for (int q = 0; q < U; ++q) {
-            T rv = buf[sidx(lane * U + q)];
+            T rv = buf[sidx(t * U + q)];
             if (!first) {
                 const T left = q ? xp[q - 1] : xl;
                 const T right = (q < U - 1) ? xp[q + 1] : xr;
@@ -231,100 +246,161 @@ __global__ void __launch_bounds__(32) k_slab_1d_warp(Geom g, T b, const T *__res
             }
             d[q] = rv;
         }
-        // Thomas on the lane's block
+        // Thomas on the thread's block
 #pragma unroll
         for (int q = 1; q < U; ++q) d[q] -= TB(q) * d[q - 1];
         d[U - 1] *= TB(U + U - 1);
 #pragma unroll
         for (int q = U - 2; q >= 0; --q) d[q] = (d[q] - TB(2 * U + q) * d[q + 1]) * TB(U + q);
-        // interface unknowns: block PCR across the lanes
+        // interface unknowns: block PCR across the threads
         T rF = d[0], rG = d[U - 1];
 #pragma unroll
-        for (int l = 0; l < 5; ++l) {
+        for (int l = 0; l < NL; ++l) {
             const int st = 1 << l;
-            T lF = __shfl_up_sync(FULL, rF, st), lG = __shfl_up_sync(FULL, rG, st);
-            T hF = __shfl_down_sync(FULL, rF, st), hG = __shfl_down_sync(FULL, rG, st);
-            if (lane < st) {
-                lF = (T)0;
-                lG = (T)0;
+            T lF, lG, hF, hG;
+            if (st < 32) {
+                lF = __shfl_up_sync(FULL, rF, st);
+                lG = __shfl_up_sync(FULL, rG, st);
+                hF = __shfl_down_sync(FULL, rF, st);
+                hG = __shfl_down_sync(FULL, rG, st);
+                // the shuffles stay inside a warp: partners in other warps come from
+                // shared memory for the lanes at the warp edge
+                if (NW > 1) {
+                    T *fF = ifc + cur * 2 * P, *fG = fF + P;
+                    fF[t] = rF;
+                    fG[t] = rG;
+                    __syncthreads();
+                    if (lane < st) {
+                        lF = (t - st >= 0) ? fF[t - st] : (T)0;
+                        lG = (t - st >= 0) ? fG[t - st] : (T)0;
+                    }
+                    if (lane + st >= 32) {
+                        hF = (t + st < P) ? fF[t + st] : (T)0;
+                        hG = (t + st < P) ? fG[t + st] : (T)0;
+                    }
+                    cur ^= 1;
+                } else {
+                    if (lane < st) {
+                        lF = (T)0;
+                        lG = (T)0;
+                    }
+                    if (lane + st >= 32) {
+                        hF = (T)0;
+                        hG = (T)0;
+                    }
+                }
+            } else {
+                T *fF = ifc + cur * 2 * P, *fG = fF + P;
+                fF[t] = rF;
+                fG[t] = rG;
+                __syncthreads();
+                lF = (t - st >= 0) ? fF[t - st] : (T)0;
+                lG = (t - st >= 0) ? fG[t - st] : (T)0;
+                hF = (t + st < P) ? fF[t + st] : (T)0;
+                hG = (t + st < P) ? fG[t + st] : (T)0;
+                cur ^= 1;
             }
-            if (lane + st >= 32) {
-                hF = (T)0;
-                hG = (T)0;
-            }
-            const int ia = 8 * U + 2 + 4 * l, ig = 8 * U + 22 + 4 * l;
+            const int ia = 8 * U + 2 + 4 * l, ig = 8 * U + 2 + 4 * NL + 4 * l;
             T nF = rF + TB(ia) * lF + TB(ia + 1) * lG + TB(ig) * hF + TB(ig + 1) * hG;
             T nG = rG + TB(ia + 2) * lF + TB(ia + 3) * lG + TB(ig + 2) * hF + TB(ig + 3) * hG;
             rF = nF;
             rG = nG;
         }
-        const int idv = 8 * U + 42;
+        const int idv = 8 * U + 2 + 8 * NL;
         const T F = TB(idv) * rF + TB(idv + 1) * rG;
         const T G = TB(idv + 2) * rF + TB(idv + 3) * rG;
-        T Gm = __shfl_up_sync(FULL, G, 1), Fp = __shfl_down_sync(FULL, F, 1);
-        if (lane == 0) Gm = (T)0;
-        if (lane == 31) Fp = (T)0;
+        // neighbours' interface values
+        T *fF = ifc + cur * 2 * P, *fG = fF + P;
+        fF[t] = F;
+        fG[t] = G;
+        cur ^= 1;
+        __syncthreads();
+        const T Gm = (t > 0) ? fG[t - 1] : (T)0;
+        const T Fp = (t < P - 1) ? fF[t + 1] : (T)0;
         const T cA = TB(8 * U) * Gm, cC = TB(8 * U + 1) * Fp;
 #pragma unroll
         for (int q = 0; q < U; ++q) xp[q] = d[q] - cA * TB(3 * U + q) - cC * TB(4 * U + q);
-        // write x_k coalesced
-        __syncwarp();
+        // write x_k coalesced (buf then keeps x_k for the next step's neighbours)
 #pragma unroll
-        for (int q = 0; q < U; ++q) buf[sidx(lane * U + q)] = xp[q];
-        __syncwarp();
+        for (int q = 0; q < U; ++q) buf[sidx(t * U + q)] = xp[q];
+        __syncthreads();
         T *xrow = x + g.guard + (int64_t)k * g.plane;
 #pragma unroll
         for (int q = 0; q < U; ++q) {
-            const int e = q * 32 + lane;
+            const int e = q * P + t;
             if (e < n) xrow[e] = buf[sidx(e)];
         }
     }
 }
 
+// (U, NW) for n unknowns: U rows per thread, NW warps per slab
+void spike_shape(int n, bool fp64, int &U, int &NW) {
+    if (n <= 256) {
+        NW = 1;
+        U = 1;
+        while (32 * U < n) U *= 2;
+    } else {
+        NW = 4;
+        U = 1;
+        while (128 * U < n) U *= 2;
+    }
+    if (U > (fp64 ? 16 : 32)) U = 0;   // not supported: caller falls back to PCR
+}
+
 int spike_block_size(int n) {
-    int U = 1;
-    while (32 * U < n) U *= 2;
+    int U, NW;
+    spike_shape(n, false, U, NW);
     return U;
 }
 
 template <typename T>
-size_t slab_warp_smem(int U) {
-    return sizeof(T) * ((size_t)(8 * U + 46) * 32 + 32 * U + U);
+size_t slab_spike_smem(int U, int NW) {
+    const int P = 32 * NW;
+    const int NL = NW == 1 ? 5 : NW == 2 ? 6 : NW == 4 ? 7 : 8;
+    const size_t items = 8 * U + 2 + 8 * NL + 4;
+    return sizeof(T) * (items * P + (size_t)P * U + (size_t)(P * U) / 32 + 4 * P);
 }
 
 template <typename T>
 bool slab_warp_supported(int n) {
-    const int U = spike_block_size(n);
-    return sizeof(T) == 4 ? U <= 64 : U <= 32;
+    int U, NW;
+    spike_shape(n, sizeof(T) == 8, U, NW);
+    return U > 0;
 }
 
 template <typename T>
 void launch_slab_1d_warp(const Geom &g, double b, const T *tab, int U, int n_cgs, const T *r, T *x,
                          const int *done, cudaStream_t s, int cls) {
+    int Uc, NW;
+    spike_shape(g.nx, sizeof(T) == 8, Uc, NW);
+    (void)U;
     const int nslabs = n_cgs <= 0 ? 1 : n_cgs;
     const int steps = n_cgs <= 0 ? g.nt : g.nt / n_cgs;
     const int coupled = n_cgs <= 0 ? 1 : 0;
-    const size_t shm = slab_warp_smem<T>(U);
+    const size_t shm = slab_spike_smem<T>(Uc, NW);
     prof_begin(s);
-#define MK_SW(UU)                                                                              \
-    case UU:                                                                                   \
-        k_slab_1d_warp<T, UU><<<nslabs, 32, shm, s>>>(g, (T)b, tab, steps, coupled, r, x, done); \
-        break
-    switch (U) {
-        MK_SW(1);
-        MK_SW(2);
-        MK_SW(4);
-        MK_SW(8);
-        MK_SW(16);
-        MK_SW(32);
-        default:
-            if constexpr (sizeof(T) == 4)
-                k_slab_1d_warp<T, 64><<<nslabs, 32, shm, s>>>(g, (T)b, tab, steps, coupled, r, x, done);
-            break;
+#define MK_SP(UU, WW)                                                                                  \
+    if (Uc == UU && NW == WW)                                                                          \
+        k_slab_1d_spike<T, UU, WW><<<nslabs, 32 * WW, shm, s>>>(g, (T)b, tab, steps, coupled, r, x, done)
+    MK_SP(1, 1);
+    MK_SP(2, 1);
+    MK_SP(4, 1);
+    MK_SP(8, 1);
+    MK_SP(4, 4);
+    MK_SP(8, 4);
+    MK_SP(16, 4);
+    if constexpr (sizeof(T) == 4) {
+        MK_SP(32, 4);
     }
-#undef MK_SW
+#undef MK_SP
     prof_end(s, cls, 2.0 * sizeof(T) * (double)g.interior());
     count_launch();
+}
+
+int spike_threads(int n) {
+    int U, NW;
+    spike_shape(n, false, U, NW);
+    return 32 * NW;
 }
 
 template <typename T>
@@ -511,19 +587,21 @@ cudaError_t slab_set_attributes() {
     set((const void *)k_slab_1d<double, 1>);
     set((const void *)k_slab_1d<double, 2>);
     set((const void *)k_slab_1d<double, 4>);
-    set((const void *)k_slab_1d_warp<float, 1>);
-    set((const void *)k_slab_1d_warp<float, 2>);
-    set((const void *)k_slab_1d_warp<float, 4>);
-    set((const void *)k_slab_1d_warp<float, 8>);
-    set((const void *)k_slab_1d_warp<float, 16>);
-    set((const void *)k_slab_1d_warp<float, 32>);
-    set((const void *)k_slab_1d_warp<float, 64>);
-    set((const void *)k_slab_1d_warp<double, 1>);
-    set((const void *)k_slab_1d_warp<double, 2>);
-    set((const void *)k_slab_1d_warp<double, 4>);
-    set((const void *)k_slab_1d_warp<double, 8>);
-    set((const void *)k_slab_1d_warp<double, 16>);
-    set((const void *)k_slab_1d_warp<double, 32>);
+    set((const void *)k_slab_1d_spike<float, 1, 1>);
+    set((const void *)k_slab_1d_spike<float, 2, 1>);
+    set((const void *)k_slab_1d_spike<float, 4, 1>);
+    set((const void *)k_slab_1d_spike<float, 8, 1>);
+    set((const void *)k_slab_1d_spike<float, 4, 4>);
+    set((const void *)k_slab_1d_spike<float, 8, 4>);
+    set((const void *)k_slab_1d_spike<float, 16, 4>);
+    set((const void *)k_slab_1d_spike<float, 32, 4>);
+    set((const void *)k_slab_1d_spike<double, 1, 1>);
+    set((const void *)k_slab_1d_spike<double, 2, 1>);
+    set((const void *)k_slab_1d_spike<double, 4, 1>);
+    set((const void *)k_slab_1d_spike<double, 8, 1>);
+    set((const void *)k_slab_1d_spike<double, 4, 4>);
+    set((const void *)k_slab_1d_spike<double, 8, 4>);
+    set((const void *)k_slab_1d_spike<double, 16, 4>);
     return e;
 }
 

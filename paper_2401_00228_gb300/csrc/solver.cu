@@ -151,7 +151,7 @@ static mk_status build_coarsest_tables(Level &C, int dim, bool fp64) {
         if (fp64 ? slab_warp_supported<double>(n) : slab_warp_supported<float>(n)) {
             C.spikeU = spike_block_size(n);
             std::vector<double> tab;
-            spike_tables(C.Lx, C.w.a, C.spikeU, tab);
+            spike_tables(C.Lx, C.w.a, C.spikeU, spike_threads(n), tab);
             if (fp64) MKCK(upload<double>(C.spike, tab));
             else MKCK(upload<float>(C.spike, tab));
         }
@@ -595,7 +595,7 @@ mk_status prepare_march(Problem &P) {
         if (slab_warp_supported<double>(P.nx)) {
             P.m_spikeU = spike_block_size(P.nx);
             std::vector<double> tab;
-            spike_tables(Lx, a, P.m_spikeU, tab);
+            spike_tables(Lx, a, P.m_spikeU, spike_threads(P.nx), tab);
             MKCK(upload<double>(P.m_spike, tab));
         }
     } else {
