@@ -51,7 +51,9 @@ typedef enum mk_status {
     MK_ERR_CUDA = 3,           /* a CUDA runtime call failed (see mk_last_cuda_error) */
     MK_ERR_NONFINITE = 4,      /* NaN/Inf in an input or in the iteration */
     MK_ERR_NOT_CONVERGED = 5,  /* max_iters reached: u_out holds the last iterate, info the residual */
-    MK_ERR_TIMEOUT = 6         /* a bounded device-side wait expired */
+    MK_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
+    MK_ERR_TOO_LARGE = 7       /* the input needs more than a fixed-size static buffer holds
+                                  (mk_op_residual_noalloc) */
 } mk_status;
 
 /* Spatial operator A_n (Sec. 3.3): tau * second-order FD Laplacian, zero Dirichlet,
@@ -251,6 +253,41 @@ mk_status mk_op_orthogonalize(mk_problem *p, int32_t j, const double *V, double 
 /* Least squares y = argmin || beta e_1 - H y ||, H (j+1) x j column-major (host),
    solved on the device by Givens rotations.  y: host, j doubles; res: |g_{j+1}|. */
 mk_status mk_op_lsq(int32_t j, const double *H, double beta, double *y, double *res, void *stream);
+
+/* ---- Allocation-free residual (a library extension: the paper has no counterpart) ----
+
+   r = f - A_h u on the fine level (Eq. (finesys)), its norm ||r||_2 and optionally the
+   per-step norms ||r_k||_2, k = 0..n_t -- the same quantities as mk_op_residual, computed
+   without allocating anything: no cudaMalloc/cudaFree, no staging buffer, no temporary
+   level.  It is for callers that must not allocate while they run: a loop that works in
+   a device-memory budget fixed at start-up, a caller that cannot afford the device-wide
+   synchronisation that cudaFree implies, or a caller whose own allocator owns the device.
+   mk_op_residual, by contrast, builds a temporary fine level and stages host arrays.
+
+   f, u:        device pointers, dense (n_t+1) x n FP64 (the layout of this ABI).
+   r:           device pointer to (n_t+1) x n doubles, or NULL to compute the norms only.
+   rnorm:       device pointer to one double: ||f - A_h u||_2.
+   rnorm_steps: device pointer to n_t+1 doubles (||r_k||_2), or NULL.
+   Host pointers, and NULL f/u/rnorm, return MK_ERR_INVALID.  The call does not
+   synchronise: the outputs are ready in the order of `stream`.
+
+   Scratch: the reduction's partial sums live in one array of MK_NOALLOC_MAX_PARTIALS
+   doubles in the library's static device memory (one copy per device, 512 KiB).  A call
+   needs (n_t+1) * ceil(nx*ny / MK_NOALLOC_CHUNK) of them; above that it returns
+   MK_ERR_TOO_LARGE and launches nothing.  The partial sums need no initial value; an
+   arrival counter beside them must be zero when a launch starts -- it is zero when the
+   library's device code is loaded, and every completed launch leaves it at zero.
+   Set-up: the first call on each device looks up the scratch's address
+   (cudaGetSymbolAddress, with that device current), which may load the library's device
+   code; make one call on each device before any stream capture.
+   Concurrency: every call on a device uses the same scratch, so calls whose executions
+   overlap on one device (other streams, other host threads, without event ordering)
+   race and return wrong results.  Order them on one stream.  Calls on different devices
+   are independent.  The results are deterministic (fixed reduction order). */
+#define MK_NOALLOC_MAX_PARTIALS 65536
+#define MK_NOALLOC_CHUNK 2048
+mk_status mk_op_residual_noalloc(const mk_problem *p, const double *f, const double *u,
+                                 double *r, double *rnorm, double *rnorm_steps, void *stream);
 
 #ifdef __cplusplus
 }

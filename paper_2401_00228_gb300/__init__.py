@@ -19,7 +19,7 @@ from ._lib import (MK_MAX_LEVELS, MKError, mk_level_desc, mk_solve_info, mk_solv
 
 __all__ = ["mk_default_opts", "mk_create_problem", "mk_set_source", "mk_destroy", "mk_solve",
            "mk_solve_rhs", "mk_march", "mk_adjoint", "mk_level_info", "mk_op_rhs", "mk_op_apply",
-           "mk_op_residual", "mk_op_restrict", "mk_op_interp_correct", "mk_op_coarsest",
+           "mk_op_residual", "mk_op_residual_noalloc", "mk_op_restrict", "mk_op_interp_correct", "mk_op_coarsest",
            "mk_op_precond", "mk_op_orthogonalize", "mk_op_lsq", "mk_kernel_launch_count",
            "make_opts", "Problem", "HeatSolve", "MKError", "lib"]
 
@@ -182,6 +182,16 @@ def mk_op_residual(p: int, f, u, r, stream=None) -> float:
     _lib.check(lib().mk_op_residual(p, _ptr(f), _ptr(u), _ptr(r), ctypes.byref(nrm), _stream(stream)),
                "mk_op_residual")
     return nrm.value
+
+
+def mk_op_residual_noalloc(p: int, f, u, r, rnorm, rnorm_steps=None, stream=None) -> None:
+    """r = f - A_h u, rnorm[0] = ||r||_2, rnorm_steps[k] = ||r_k||_2; every array on the device.
+
+    The library allocates nothing in this call (its reduction scratch is static device
+    memory); r and rnorm_steps may be None.  Results are ready in stream order."""
+    s = _stream(stream) or _current_stream_for(f, u)
+    _lib.check(lib().mk_op_residual_noalloc(p, _ptr(f), _ptr(u), _ptr(r), _ptr(rnorm),
+                                            _ptr(rnorm_steps), s), "mk_op_residual_noalloc")
 
 
 def mk_op_restrict(p: int, opts, level: int, precision: int, v, vhat, stream=None) -> None:

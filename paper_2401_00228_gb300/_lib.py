@@ -9,9 +9,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libmk.so")
 
 STATUS = {0: "MK_OK", 1: "MK_ERR_INVALID", 2: "MK_ERR_NOMEM", 3: "MK_ERR_CUDA",
-          4: "MK_ERR_NONFINITE", 5: "MK_ERR_NOT_CONVERGED", 6: "MK_ERR_TIMEOUT"}
+          4: "MK_ERR_NONFINITE", 5: "MK_ERR_NOT_CONVERGED", 6: "MK_ERR_TIMEOUT",
+          7: "MK_ERR_TOO_LARGE"}
 MK_OK, MK_ERR_INVALID, MK_ERR_NOMEM, MK_ERR_CUDA, MK_ERR_NONFINITE, MK_ERR_NOT_CONVERGED, \
-    MK_ERR_TIMEOUT = range(7)
+    MK_ERR_TIMEOUT, MK_ERR_TOO_LARGE = range(8)
+# static scratch of mk_op_residual_noalloc
+MK_NOALLOC_MAX_PARTIALS = 65536
+MK_NOALLOC_CHUNK = 2048
 
 
 class mk_stencil(ctypes.Structure):
@@ -71,6 +75,7 @@ SIGNATURES = {
     "mk_op_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
     "mk_op_apply": (ctypes.c_int, [_P, ctypes.POINTER(mk_solve_opts), _I, _I, _P, _P, _P]),
     "mk_op_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(_D), _P]),
+    "mk_op_residual_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "mk_op_restrict": (ctypes.c_int, [_P, ctypes.POINTER(mk_solve_opts), _I, _I, _P, _P, _P]),
     "mk_op_interp_correct": (ctypes.c_int, [_P, ctypes.POINTER(mk_solve_opts), _I, _I, _P, _P, _P, _P, _P]),
     "mk_op_coarsest": (ctypes.c_int, [_P, ctypes.POINTER(mk_solve_opts), _I, _P, _P, _P]),

@@ -153,6 +153,7 @@ const char *mk_status_string(mk_status s) {
         case MK_ERR_NONFINITE: return "MK_ERR_NONFINITE";
         case MK_ERR_NOT_CONVERGED: return "MK_ERR_NOT_CONVERGED";
         case MK_ERR_TIMEOUT: return "MK_ERR_TIMEOUT";
+        case MK_ERR_TOO_LARGE: return "MK_ERR_TOO_LARGE";
     }
     return "MK_ERR_UNKNOWN";
 }
@@ -847,6 +848,16 @@ mk_status mk_op_lsq(int32_t j, const double *H, double beta, double *y, double *
     else std::memcpy(y, hy.data(), sizeof(double) * j);
     if (res) *res = hr;
     return MK_OK;
+}
+
+// Allocation-free residual: pointer checks only, then one kernel launch (noalloc.cu).
+mk_status mk_op_residual_noalloc(const mk_problem *p, const double *f, const double *u, double *r,
+                                 double *rnorm, double *rnorm_steps, void *stream) {
+    if (!p || !f || !u || !rnorm) return MK_ERR_INVALID;
+    if (!is_device_ptr(f) || !is_device_ptr(u) || !is_device_ptr(rnorm)) return MK_ERR_INVALID;
+    if ((r && !is_device_ptr(r)) || (rnorm_steps && !is_device_ptr(rnorm_steps)))
+        return MK_ERR_INVALID;
+    return residual_noalloc(p->P, f, u, r, rnorm, rnorm_steps, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -113,4 +113,9 @@ void enqueue_coarsest(Hierarchy &H, const int *done, cudaStream_t s);
 
 mk_status prepare_march(Problem &P);
 
+// Allocation-free fine-level residual with a static-memory reduction scratch (noalloc.cu).
+int64_t noalloc_partials_needed(const Problem &P);
+mk_status residual_noalloc(const Problem &P, const double *f, const double *u, double *r,
+                           double *rnorm, double *rnorm_steps, cudaStream_t s);
+
 }  // namespace mk
