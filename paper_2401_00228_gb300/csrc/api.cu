@@ -2,6 +2,7 @@
 // the operator-level entry points used to check each step of the path on its own.
 #include <atomic>
 #include <cmath>
+#include <type_traits>
 #include <cstring>
 #include <memory>
 
@@ -58,6 +59,7 @@ static mk_status ensure_device() {
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CK(slab_set_attributes());
+    CK(dst_set_attributes());
     g_num_sms = sms > 0 ? sms : 1;
     return MK_OK;
 }
@@ -660,6 +662,24 @@ static mk_status op_coarsest_t(Hierarchy &H, const double *dr, double *dx, cudaS
         if (e == cudaSuccess) e = cudaMemcpy(m.p, t.data(), sizeof(T) * t.size(), cudaMemcpyHostToDevice);
         return e;
     };
+    if constexpr (std::is_same<T, float>::value) {
+        // the sine-transform slab solver where it applies (as in the solve)
+        Level D;
+        D.g = C.g;
+        D.w = C.w;
+        D.Lx = C.Lx;
+        mk_status st = build_dst_tables(D, H.key.n_cgs);
+        if (st != MK_OK) return st;
+        if (D.dstN2 > 0) {
+            launch_slab_1d_dst(D.g, D.dst.as<float>(), D.dsttw.as<float2>(), D.dstN2, H.key.n_cgs,
+                               D.dstbuf.as<float>(), D.dstld, rp.as<float>(), xp.as<float>(),
+                               nullptr, s);
+            launch_unpack<float, double>(C.g, xp.as<float>(), dx, s);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(s));
+            return MK_OK;
+        }
+    }
     if (C.g.dim == 1) {
         std::vector<double> a1, g1, b1;
         pcr_tables(C.Lx, C.w.a, C.npad, a1, g1, b1);

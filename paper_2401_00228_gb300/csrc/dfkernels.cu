@@ -308,7 +308,10 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
         else MK_IDF1M(S, -1);                                                                 \
     } while (0)
     prof_begin(s);
-    if (gf.dim == 1) {
+    if (launch_interp_df_1d_tiled(gf, gc, nu, space, ca, cb, has_b, v, sigma, Xc, mc, xc_stride,
+                                  yc, x, wout, done, s)) {
+        // 1D, nu = 2: time-tiled kernel (transfer1d.cu)
+    } else if (gf.dim == 1) {
         if (space) MK_IDF1(true); else MK_IDF1(false);
     } else {
         if (space) MK_IDF(2, true); else MK_IDF(2, false);
@@ -414,22 +417,25 @@ __global__ void __launch_bounds__(DF_THREADS) k_multidot_df(int64_t len, const f
         const int lane2 = threadIdx.x & 31, warp2 = threadIdx.x >> 5;
         double *res = smem_md;
         for (int t = warp2; t < nslots; t += DF_WARPS) {
-            const volatile double *p = rs.partials + (int64_t)t * rs.max_blocks;
+            const double *p = rs.partials + (int64_t)t * rs.max_blocks;
             double a = 0.0;
-            for (int b = lane2; b < (int)gridDim.x; b += 32) a += p[b];
+#pragma unroll 8
+            for (int b = lane2; b < (int)gridDim.x; b += 32) a += __ldcg(p + b);
             a = warp_sum(a);
             if (lane2 == 0) res[t] = a;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        {
             double *H = ks.H() + (int64_t)j * (ks.m + 1);
-            for (int i = 0; i < nv; ++i) {
-                double hc = ks.sigma()[i] * res[i];
+            for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+                const double hc = ks.sigma()[i] * res[i];
                 ks.tmp()[i] = hc;
                 H[i] = second ? H[i] + hc : hc;
             }
-            if (!second) ks.misc()[2] = res[nv];
-            rs.counter[0] = 0u;
+            if (threadIdx.x == 0) {
+                if (!second) ks.misc()[2] = res[nv];
+                rs.counter[0] = 0u;
+            }
         }
     }
 }
@@ -463,10 +469,8 @@ __global__ void __launch_bounds__(DF_THREADS) k_update_df(int64_t len, const flo
     if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
     if (last_block_ticket(rs.counter)) {
         double tot = sum_partials(rs.partials, gridDim.x);
-        if (threadIdx.x == 0) {
-            update_epilogue(tot, ks, j, mode, second);
-            rs.counter[0] = 0u;
-        }
+        update_epilogue_block(tot, ks, j, mode, second);
+        if (threadIdx.x == 0) rs.counter[0] = 0u;
     }
 }
 

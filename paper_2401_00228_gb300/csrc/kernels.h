@@ -114,6 +114,35 @@ void launch_lsq(int j, double *H, double beta, double *gg, double *y, double *re
 void launch_residual_df(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
                         const double *u, float2 *r, const ReduceScratch &rs, int slot, KState ks,
                         int epi, cudaStream_t s);
+// Coarsest decoupled slabs by sine-transform diagonalisation (slab_dst.cu), FP32, for a
+// uniform 1D operator.  dst_transform_size(n) = 2(n+1) when that is a power of two <= 4096,
+// else 0 (not supported).  tab = [alpha (n) | beta (n)], tw = FFT twiddle table,
+// rh = scratch (nt+1) x ldd.  Three launches.
+int dst_transform_size(int n);
+size_t dst_smem_bytes(int N2);
+cudaError_t dst_set_attributes();
+void launch_slab_1d_dst(const Geom &g, const float *tab, const float2 *tw, int N2, int n_cgs,
+                        float *rh, int ldd, const float *r, float *x, const int *done,
+                        cudaStream_t s);
+
+// Time-tiled 1D variants for nu = 2 (transfer1d.cu).  Each returns false, launching
+// nothing, when the case is not covered (2D, nu != 2); the caller then uses the general
+// kernel.  The caller brackets the launch (profiling, launch count).
+template <typename Tin, typename Tout, typename Tc>
+bool launch_restrict_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space,
+                              const Weights &w, SpaceOp<Tc> L, const Tin *v, const double *sigma,
+                              Tout *vhat, const ReduceScratch &rs, int slot, KState ks_c,
+                              const int *done, cudaStream_t s);
+template <typename Tv, typename Tz, typename Tx, typename Tw, typename Tc>
+bool launch_interp_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space, const Weights &w,
+                            SpaceOp<Tc> L, const Tv *v, const double *sigma, const Tz *Xc,
+                            int mc, int64_t xc_stride, const double *yc, Tx *x, Tw *wout,
+                            const int *done, cudaStream_t s);
+bool launch_interp_df_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space,
+                               const float2 *ca, const float2 *cb, bool has_b, const float2 *v,
+                               const double *sigma, const float *Xc, int mc, int64_t xc_stride,
+                               const double *yc, float *x, float2 *wout, const int *done,
+                               cudaStream_t s);
 // ca, cb: double-float a*L and b*L coefficient rows, [x: lo|di|up (3 nx) | y: (3 ny)]
 void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const float2 *ca,
                       const float2 *cb, bool has_b, const float2 *v, const double *sigma,

@@ -7,6 +7,8 @@
 // device, so no separate scaling pass is needed.  Every scalar of the process (H, Givens
 // rotations, y, flags) lives on the device and is updated by the last block of the
 // reduction that produces it, so a whole restart cycle runs without a host round trip.
+#include <type_traits>
+
 #include "kernels.h"
 #include "reduce.cuh"
 #include "krylov_epilogue.cuh"
@@ -23,13 +25,26 @@ __device__ __forceinline__ void finish_slots(const double *part, int max_blocks,
                                              int nb, double *out_smem) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = warp; t < nslots; t += KR_WARPS) {
-        const volatile double *p = part + (int64_t)t * max_blocks;
+        const double *p = part + (int64_t)t * max_blocks;
         double acc = 0.0;
-        for (int b = lane; b < nb; b += 32) acc += p[b];
+#pragma unroll 8
+        for (int b = lane; b < nb; b += 32) acc += __ldcg(p + b);
         acc = warp_sum(acc);
         if (lane == 0) out_smem[t] = acc;
     }
     __syncthreads();
+}
+
+// h_i = sigma_i d_i (i < nv) into H's column j and tmp; ||w||^2 into misc[2] (first pass).
+__device__ __forceinline__ void multidot_epilogue(const double *res, KState ks, int j, int nv,
+                                                  int second) {
+    double *H = ks.H() + (int64_t)j * (ks.m + 1);
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        const double hc = ks.sigma()[i] * res[i];
+        ks.tmp()[i] = hc;
+        H[i] = second ? H[i] + hc : hc;
+    }
+    if (!second && threadIdx.x == 0) ks.misc()[2] = res[nv];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -91,16 +106,8 @@ __global__ void __launch_bounds__(KR_THREADS) k_multidot(int64_t len, const TW *
     if (last_block_ticket(rs.counter)) {
         double *res = smem;  // reuse
         finish_slots(rs.partials, rs.max_blocks, nslots, gridDim.x, res);
-        if (threadIdx.x == 0) {
-            double *H = ks.H() + (int64_t)j * (ks.m + 1);
-            for (int i = 0; i < nv; ++i) {
-                double hc = ks.sigma()[i] * res[i];
-                ks.tmp()[i] = hc;
-                H[i] = second ? H[i] + hc : hc;
-            }
-            if (!second) ks.misc()[2] = res[nv];
-            rs.counter[0] = 0u;
-        }
+        multidot_epilogue(res, ks, j, nv, second);
+        if (threadIdx.x == 0) rs.counter[0] = 0u;
     }
 }
 
@@ -131,11 +138,146 @@ __global__ void __launch_bounds__(KR_THREADS) k_update(int64_t len, const TW *__
     if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
     if (last_block_ticket(rs.counter)) {
         double tot = sum_partials(rs.partials, gridDim.x);
-        if (threadIdx.x == 0) {
-            update_epilogue(tot, ks, j, mode, second);
-            rs.counter[0] = 0u;
-        }
+        update_epilogue_block(tot, ks, j, mode, second);
+        if (threadIdx.x == 0) rs.counter[0] = 0u;
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// Short-basis variants (j + 1 = NV <= MK_MAX_INNER vectors: every inner level, and the
+// first iterations of level 1 in FP64).  Each thread takes 8 consecutive elements per step
+// with 16-byte loads, and the vector count is a compile-time constant, so all NV + 1 loads
+// of a step are in flight together.  A vector's padded length is a multiple of 4096, so an
+// 8-element group never straddles its end.
+// ---------------------------------------------------------------------------------------
+constexpr int SB_EPT = 8;
+
+template <typename T>
+__device__ __forceinline__ void ld8(const T *p, T (&o)[SB_EPT]);
+template <>
+__device__ __forceinline__ void ld8<float>(const float *p, float (&o)[SB_EPT]) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void ld8<double>(const double *p, double (&o)[SB_EPT]) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const double2 a = __ldg(reinterpret_cast<const double2 *>(p) + h);
+        o[2 * h] = a.x;
+        o[2 * h + 1] = a.y;
+    }
+}
+// Plain (coherent) load: the source of a second Gram-Schmidt pass is written by this kernel.
+template <typename T>
+__device__ __forceinline__ void ld8_rw(const T *p, T (&o)[SB_EPT]) {
+#pragma unroll
+    for (int q = 0; q < SB_EPT; ++q) o[q] = p[q];
+}
+template <typename T>
+__device__ __forceinline__ void st8(T *p, const T (&o)[SB_EPT]) {
+#pragma unroll
+    for (int q = 0; q < SB_EPT; ++q) p[q] = o[q];
+}
+
+template <int NV, typename T>
+__global__ void __launch_bounds__(KR_THREADS) k_multidot_sb(int64_t len, const T *__restrict__ W,
+                                                            const T *__restrict__ V,
+                                                            int64_t vstride, ReduceScratch rs,
+                                                            KState ks, int second,
+                                                            const int *__restrict__ done) {
+    if (done && *done) return;
+    if (second && !ks.flags[2]) return;
+    constexpr int j = NV - 1;
+    __shared__ double acc[(NV + 1) * KR_WARPS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T *src = second ? (const T *)(V + (int64_t)(j + 1) * vstride) : W;
+    T d[NV + 1];
+#pragma unroll
+    for (int i = 0; i <= NV; ++i) d[i] = (T)0;
+    for (int64_t base = ((int64_t)blockIdx.x * KR_THREADS + threadIdx.x) * SB_EPT; base < len;
+         base += (int64_t)gridDim.x * KR_THREADS * SB_EPT) {
+        T w[SB_EPT], v[NV][SB_EPT];
+        if (second) ld8_rw(src + base, w); else ld8(src + base, w);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) ld8(V + (int64_t)i * vstride + base, v[i]);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            T s = (T)0;
+#pragma unroll
+            for (int q = 0; q < SB_EPT; ++q) s += w[q] * v[i][q];
+            d[i] += s;
+        }
+        T s = (T)0;
+#pragma unroll
+        for (int q = 0; q < SB_EPT; ++q) s += w[q] * w[q];
+        d[NV] += s;
+    }
+    const int nslots = second ? NV : NV + 1;
+#pragma unroll
+    for (int i = 0; i <= NV; ++i) {
+        const double t = warp_sum((double)d[i]);
+        if (lane == 0) acc[i * KR_WARPS + warp] = t;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nslots; t += KR_THREADS) {
+        double sum = 0.0;
+        for (int w2 = 0; w2 < KR_WARPS; ++w2) sum += acc[t * KR_WARPS + w2];
+        rs.partials[(int64_t)t * rs.max_blocks + blockIdx.x] = sum;
+    }
+    if (last_block_ticket(rs.counter)) {
+        double *res = acc;  // reuse
+        finish_slots(rs.partials, rs.max_blocks, nslots, gridDim.x, res);
+        multidot_epilogue(res, ks, j, NV, second);
+        if (threadIdx.x == 0) rs.counter[0] = 0u;
+    }
+}
+
+template <int NV, typename T>
+__global__ void __launch_bounds__(KR_THREADS) k_update_sb(int64_t len, const T *__restrict__ W,
+                                                          T *__restrict__ V, int64_t vstride,
+                                                          int write_next, ReduceScratch rs,
+                                                          KState ks, int mode, int second,
+                                                          const int *__restrict__ done) {
+    if (done && *done) return;
+    if (second && !ks.flags[2]) return;
+    constexpr int j = NV - 1;
+    T c[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) c[i] = (T)(ks.tmp()[i] * ks.sigma()[i]);
+    T *out = V + (int64_t)(j + 1) * vstride;
+    T acc = (T)0;
+    for (int64_t base = ((int64_t)blockIdx.x * KR_THREADS + threadIdx.x) * SB_EPT; base < len;
+         base += (int64_t)gridDim.x * KR_THREADS * SB_EPT) {
+        T val[SB_EPT], v[NV][SB_EPT];
+        if (second) ld8_rw(out + base, val); else ld8(W + base, val);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) ld8(V + (int64_t)i * vstride + base, v[i]);
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+#pragma unroll
+            for (int q = 0; q < SB_EPT; ++q) val[q] -= c[i] * v[i][q];
+        if (write_next) st8(out + base, val);
+#pragma unroll
+        for (int q = 0; q < SB_EPT; ++q) acc += val[q] * val[q];
+    }
+    double bs = block_sum((double)acc);
+    if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
+    if (last_block_ticket(rs.counter)) {
+        double tot = sum_partials(rs.partials, gridDim.x);
+        update_epilogue_block(tot, ks, j, mode, second);
+        if (threadIdx.x == 0) rs.counter[0] = 0u;
+    }
+}
+
+// one resident wave: these kernels hold up to 4 blocks of 256 threads per SM
+static int sb_grid(int64_t len) {
+    int64_t g = (len + KR_THREADS * SB_EPT - 1) / (KR_THREADS * SB_EPT);
+    const int64_t cap = (int64_t)g_num_sms * 4;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -182,6 +324,21 @@ void launch_multidot(int64_t len, const TW *W, const TV *V, int64_t vstride, int
     size_t shm = sizeof(double) * (size_t)(j + 2) * KR_WARPS;
     if (shm < sizeof(double) * (size_t)(j + 2)) shm = sizeof(double) * (size_t)(j + 2);
     prof_begin(s);
+    if constexpr (std::is_same<TW, TV>::value) {
+        if (j + 1 <= MK_MAX_INNER && len % (KR_THREADS * SB_EPT) == 0) {
+            const int g = sb_grid(len);
+            const int sec = second_pass ? 1 : 0;
+            switch (j + 1) {
+#define MK_MD(N) \
+    case N: k_multidot_sb<N, TV><<<g, KR_THREADS, 0, s>>>(len, W, V, vstride, rs, ks, sec, done); break;
+                MK_MD(1) MK_MD(2) MK_MD(3) MK_MD(4) MK_MD(5) MK_MD(6) MK_MD(7) MK_MD(8)
+#undef MK_MD
+            }
+            prof_end(s, PROF_MULTIDOT, (double)(j + 2) * alg_n * sizeof(TV));
+            count_launch();
+            return;
+        }
+    }
     k_multidot<TW, TV><<<grid, KR_THREADS, shm, s>>>(len, W, V, vstride, j, rs, ks,
                                                       second_pass ? 1 : 0, done);
     prof_end(s, PROF_MULTIDOT, (double)(j + 2) * alg_n * sizeof(TV));
@@ -195,6 +352,24 @@ void launch_update(int64_t len, const TW *W, TV *V, int64_t vstride, int j, bool
     const double alg_n = prof_alg_n() > 0 ? prof_alg_n() : (double)len;
     int grid = krylov_grid(len, (int64_t)KR_THREADS * 8);
     prof_begin(s);
+    if constexpr (std::is_same<TW, TV>::value) {
+        if (j + 1 <= MK_MAX_INNER && len % (KR_THREADS * SB_EPT) == 0) {
+            const int g = sb_grid(len);
+            const int wn = write_next ? 1 : 0, sec = second_pass ? 1 : 0;
+            switch (j + 1) {
+#define MK_UP(N)                                                                              \
+    case N:                                                                                   \
+        k_update_sb<N, TV><<<g, KR_THREADS, 0, s>>>(len, W, V, vstride, wn, rs, ks, mode, sec, \
+                                                    done);                                    \
+        break;
+                MK_UP(1) MK_UP(2) MK_UP(3) MK_UP(4) MK_UP(5) MK_UP(6) MK_UP(7) MK_UP(8)
+#undef MK_UP
+            }
+            prof_end(s, PROF_UPDATE, (double)(j + 2 + (write_next ? 1 : 0)) * alg_n * sizeof(TV));
+            count_launch();
+            return;
+        }
+    }
     k_update<TW, TV><<<grid, KR_THREADS, 0, s>>>(len, W, V, vstride, j, write_next ? 1 : 0, rs,
                                                   ks, mode, second_pass ? 1 : 0, done);
     prof_end(s, PROF_UPDATE, (double)(j + 2 + (write_next ? 1 : 0)) * alg_n * sizeof(TV));

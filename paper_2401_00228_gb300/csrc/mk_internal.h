@@ -74,6 +74,11 @@ void pcr_tables(const Tri &L, double a, int npad, std::vector<double> &alpha,
 int spike_levels(int P);
 int spike_items(int U, int P);
 void spike_tables(const Tri &L, double a, int U, int P, std::vector<double> &tab);
+// Uniform operator test and tables of the sine-transform slab solver (slab_dst.cu).
+bool tri_uniform(const Tri &L, double &c);
+// tab = [alpha (n) | beta (n)], tw = FFT twiddles pass after pass (interleaved re, im)
+void dst_tables(int n, double c, double a, double b, std::vector<double> &tab,
+                std::vector<double> &tw);
 // Diagonalisation L = S diag(lam) S^{-1} (real: L is similar to a symmetric matrix).
 // S, Sinv row-major n x n.
 void tri_eigen(const Tri &L, std::vector<double> &lam, std::vector<double> &S,

@@ -70,7 +70,10 @@ __device__ __forceinline__ double sum_partials(const double *p, int nb) {
     int per = (nb + nthreads - 1) / nthreads;
     int s0 = tid * per, s1 = min(s0 + per, nb);
     double acc = 0.0;
-    for (int s = s0; s < s1; ++s) acc += ((volatile const double *)p)[s];
+    // L2 loads (the partials were written by other blocks before their fence), unrolled so
+    // that they are in flight together
+#pragma unroll 8
+    for (int s = s0; s < s1; ++s) acc += __ldcg(p + s);
     return block_sum(acc);
 }
 

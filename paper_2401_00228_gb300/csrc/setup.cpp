@@ -348,4 +348,56 @@ void tri_eigen(const Tri &L, std::vector<double> &lam, std::vector<double> &S,
         }
 }
 
+// L = c tridiag(1, -2, 1) with zero ends (to a relative 1e-13): the operator the sine
+// transform diagonalises.
+bool tri_uniform(const Tri &L, double &c) {
+    const int n = L.n();
+    if (n < 1) return false;
+    c = -0.5 * L.di[0];
+    if (!(c > 0.0)) return false;
+    const double tol = 1e-13 * c;
+    for (int i = 0; i < n; ++i) {
+        if (std::fabs(L.di[i] + 2.0 * c) > tol) return false;
+        if (std::fabs(L.lo[i] - (i > 0 ? c : 0.0)) > tol) return false;
+        if (std::fabs(L.up[i] - (i + 1 < n ? c : 0.0)) > tol) return false;
+    }
+    return true;
+}
+
+// Sine-transform slab tables for I - aL, I + bL with L = c tridiag(1, -2, 1):
+//   tab = [alpha_j (n) | beta_j (n)], lam_j = -4c sin^2(pi (j+1) / (2(n+1))),
+//   beta_j = 1 / (1 - a lam_j), alpha_j = (1 + b lam_j) beta_j.
+void dst_tables(int n, double c, double a, double b, std::vector<double> &tab,
+                std::vector<double> &tw) {
+    const double pi = 3.14159265358979323846;
+    const int N = n + 1;
+    tab.assign(2 * (size_t)n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        const double sj = std::sin(pi * (j + 1) / (2.0 * N));
+        const double lam = -4.0 * c * sj * sj;
+        const double beta = 1.0 / (1.0 - a * lam);
+        tab[j] = (1.0 + b * lam) * beta;
+        tab[n + j] = beta;
+    }
+    // twiddles exp(-2 pi i k r / (Ns R)) of the FFT passes over N2 = 2(n+1) points (radix 8,
+    // then one radix-4 or radix-2 pass), interleaved (re, im), pass after pass
+    tw.clear();
+    const int N2 = 2 * N;
+    int p = 0;
+    while ((1 << p) < N2) ++p;
+    int Ns = 1;
+    while (p > 0) {
+        const int R = p >= 3 ? 8 : (p == 2 ? 4 : 2);
+        for (int k = 0; k < Ns; ++k)   // Ns (R - 1) entries per pass, also for Ns = 1
+            for (int r = 1; r < R; ++r) {
+                const double ang = -2.0 * pi * (double)k * r / ((double)Ns * R);
+                tw.push_back(std::cos(ang));
+                tw.push_back(std::sin(ang));
+            }
+        Ns *= R;
+        p -= (R == 8 ? 3 : (R == 4 ? 2 : 1));
+    }
+    if (tw.empty()) tw.assign(2, 0.0);
+}
+
 }  // namespace mk

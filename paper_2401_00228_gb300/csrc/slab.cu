@@ -22,6 +22,8 @@
 
 namespace mk {
 
+constexpr int SLAB_SMEM_LIMIT = 200 * 1024;   // dynamic shared memory of the slab kernels
+
 // ---------------------------------------------------------------------------------------
 // 1D PCR slab kernel.  NT threads; each owns unknowns i = tid + u*NT (u < U).
 // shared: buf0[npad], buf1[npad], xprev[npad + 2]
@@ -345,6 +347,15 @@ void spike_shape(int n, bool fp64, int &U, int &NW) {
         while (128 * U < n) U *= 2;
     }
     if (U > (fp64 ? 16 : 32)) U = 0;   // not supported: caller falls back to PCR
+    // the tables and staging buffers must fit the dynamic shared memory the kernels are
+    // configured for (slab_set_attributes); n = 2047 in FP64 does not
+    if (U > 0) {
+        const int P = 32 * NW;
+        const int NL = NW == 1 ? 5 : NW == 2 ? 6 : NW == 4 ? 7 : 8;
+        const size_t items = 8 * (size_t)U + 2 + 8 * (size_t)NL + 4;
+        const size_t bytes = (fp64 ? 8 : 4) * (items * P + (size_t)P * U + (size_t)(P * U) / 32 + 4 * P);
+        if (bytes > (size_t)SLAB_SMEM_LIMIT) U = 0;
+    }
 }
 
 int spike_block_size(int n) {
@@ -573,7 +584,7 @@ void launch_march_2d(const Geom &g, double a, double b, SpaceOp<double> L, const
 
 // Opt in to large dynamic shared memory once, before any launch or graph capture.
 cudaError_t slab_set_attributes() {
-    const int big = 200 * 1024;
+    const int big = SLAB_SMEM_LIMIT;
     cudaError_t e = cudaSuccess;
     auto set = [&](const void *f) {
         cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

@@ -10,6 +10,8 @@
 #include <cstring>
 
 #include "df64.cuh"
+#include <type_traits>
+
 #include "solver.h"
 
 namespace mk {
@@ -124,8 +126,25 @@ static mk_status alloc_kstate(Level &L, int m) {
     return MK_OK;
 }
 
+mk_status build_dst_tables(Level &C, int n_cgs) {
+    C.dstN2 = 0;
+    if (C.g.dim != 1 || n_cgs < 1 || C.g.nt % n_cgs != 0 || C.g.nt / n_cgs > 64) return MK_OK;
+    const int n = C.g.nx;
+    const int N2 = dst_transform_size(n);
+    double c = 0.0;
+    if (N2 == 0 || !tri_uniform(C.Lx, c)) return MK_OK;
+    std::vector<double> tab, tw;
+    dst_tables(n, c, C.w.a, C.w.b, tab, tw);
+    MKCK(upload<float>(C.dst, tab));
+    MKCK(upload<float>(C.dsttw, tw));
+    C.dstld = ((n + 31) / 32) * 32;
+    MKCK(C.dstbuf.alloc(sizeof(float) * (size_t)(C.g.nt + 1) * C.dstld));
+    C.dstN2 = N2;
+    return MK_OK;
+}
+
 // Coarsest-level direct solver tables.
-static mk_status build_coarsest_tables(Level &C, int dim, bool fp64) {
+static mk_status build_coarsest_tables(Level &C, int dim, bool fp64, int n_cgs) {
     if (dim == 1) {
         int n = C.Lx.n();
         int np = 32;
@@ -154,6 +173,10 @@ static mk_status build_coarsest_tables(Level &C, int dim, bool fp64) {
             spike_tables(C.Lx, C.w.a, C.spikeU, spike_threads(n), tab);
             if (fp64) MKCK(upload<double>(C.spike, tab));
             else MKCK(upload<float>(C.spike, tab));
+        }
+        if (!fp64) {
+            mk_status st = build_dst_tables(C, n_cgs);
+            if (st != MK_OK) return st;
         }
     } else {
         std::vector<double> lx, Sx, Sxi, ly, Sy, Syi;
@@ -253,7 +276,7 @@ mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out) {
             lv->m = 1;
             MKCK(lv->R.alloc(cs * len));
             MKCK(lv->X.alloc(cs * len));
-            st = build_coarsest_tables(*lv, P.dim, fp64);
+            st = build_coarsest_tables(*lv, P.dim, fp64, o.n_cgs);
             if (st != MK_OK) return st;
         }
         H->lv.push_back(std::move(lv));
@@ -278,6 +301,14 @@ mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out) {
 template <typename Tc>
 void enqueue_coarsest_t(Hierarchy &H, const int *done, cudaStream_t s) {
     Level &C = *H.lv.back();
+    if constexpr (std::is_same<Tc, float>::value) {
+        if (C.dstN2 > 0) {
+            launch_slab_1d_dst(C.g, C.dst.as<float>(), C.dsttw.as<float2>(), C.dstN2, H.key.n_cgs,
+                               C.dstbuf.as<float>(), C.dstld, C.R.as<float>(), C.X.as<float>(),
+                               done, s);
+            return;
+        }
+    }
     if (C.g.dim == 1 && C.spikeU > 0)
         launch_slab_1d_warp<Tc>(C.g, C.w.b, C.spike.as<Tc>(), C.spikeU, H.key.n_cgs, C.R.as<Tc>(),
                                 C.X.as<Tc>(), done, s, PROF_SLAB);

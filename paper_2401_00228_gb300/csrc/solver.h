@@ -61,6 +61,8 @@ struct Level {
     int npad = 0, nlev = 0;
     DevMem spike;      // one-warp partitioned solver tables (1D), spikeU = rows per lane
     int spikeU = 0;
+    DevMem dst, dsttw, dstbuf;   // sine-transform slab solver (1D uniform L, FP32 cycle)
+    int dstN2 = 0, dstld = 0;
     DevMem Sx, Sxi, lamx, Sy, Syi, lamy;
 };
 
@@ -101,6 +103,9 @@ template <>
 inline SpaceOp<float> op_of<float>(const Level &L) { return L.op32; }
 
 mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out);
+// Sine-transform slab tables for coarsest level C when they apply (1D, L uniform, n + 1 a
+// power of two, 1 <= n_cgs with at most 64 steps per slab); C.dstN2 stays 0 otherwise.
+mk_status build_dst_tables(Level &C, int n_cgs);
 mk_status validate_opts(const Problem &P, const mk_solve_opts &o);
 
 // FGMRES + MK on f (padded FP64, level 1) -> H.u.  f is copied into H.f.

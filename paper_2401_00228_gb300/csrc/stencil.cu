@@ -389,7 +389,10 @@ void launch_restrict(const Geom &gf, const Geom &gc, int nu, bool space, const W
     k_restrict_1d<S, Tin, Tout, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, nu, a, b, mu, L, v, sigma, \
                                                                 vhat, kc, rs, slot, ks_c, done)
     prof_begin(s);
-    if (gf.dim == 1) {
+    if (launch_restrict_1d_tiled<Tin, Tout, Tc>(gf, gc, nu, space, w, L, v, sigma, vhat, rs, slot,
+                                                ks_c, done, s)) {
+        // 1D, nu = 2: time-tiled kernel (transfer1d.cu)
+    } else if (gf.dim == 1) {
         if (space) MK_RESTRICT1(true); else MK_RESTRICT1(false);
     } else {
         if (space) MK_RESTRICT(2, true); else MK_RESTRICT(2, false);
@@ -598,7 +601,10 @@ void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Wei
         else MK_INTERP1M(S, -1);                                                              \
     } while (0)
     prof_begin(s);
-    if (gf.dim == 1) {
+    if (launch_interp_1d_tiled<Tv, Tz, Tx, Tw, Tc>(gf, gc, nu, space, w, L, v, sigma, Xc, mc,
+                                                   xc_stride, yc, x, wout, done, s)) {
+        // 1D, nu = 2: time-tiled kernel (transfer1d.cu)
+    } else if (gf.dim == 1) {
         if (space) MK_INTERP1(true); else MK_INTERP1(false);
     } else {
         if (space) MK_INTERP(2, true); else MK_INTERP(2, false);

@@ -146,6 +146,24 @@ def test_coarsest_slabs(case, precision, tol):
     assert _rel(x, O.coarsest_solve(lv, r, H.n_cgs)) <= tol
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-4)])
+@pytest.mark.parametrize("nx,nt", [(1023, 8192), (2047, 64)])
+def test_coarsest_uniform_1d(nx, nt, precision, tol):
+    """Coarsest decoupled slabs of a uniform 1D operator: 513 x 1023 in 16 slabs of 32 steps
+    (the n = 1023, n_t = 8192 heat workload) and the largest transform, n = 2047.  In mixed
+    precision these take the sine-transform slab solver, in FP64 the partitioned one."""
+    levels = 5 if nt == 8192 else 3
+    sched = W.Schedule((2,) * (levels - 1), (False,) * (levels - 1), (2,) * (levels - 3) + (1,), 16)
+    P = W.custom(1, nx, nt, 1.0, 1.0, 1.0, sched, seed=31)
+    H = _hier(P)
+    lv = H.levels[-1]
+    r = np.random.default_rng(27).standard_normal(lv.shape())
+    x = np.empty_like(r)
+    with _prob(P) as p:
+        mk.mk_op_coarsest(p.handle, _opts(sched), precision, r, x)
+    assert _rel(x, O.coarsest_solve(lv, r, H.n_cgs)) <= tol
+
+
 def test_coarsest_exact_coupled(case):
     P, H, p = case
     o = _opts(P.schedule, n_cgs=0)
