@@ -132,6 +132,50 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def bench_batch(mk, torch, dev, count_1d=12, count_2d=4, max_iters=600):
+    """16 members of the uneven batched workload (1D n 63..2047 x n_t 256..8192, 2D side
+    63..255 x n_t 128..1024, tau log-uniform [0.1, 10], theta in {1/2, 1}; mixed, tol 1e-10):
+    one autotuned batch against the same members solved one after another."""
+    ms = W.batched_problems(seed=4, count_1d=count_1d, count_2d=count_2d)
+
+    def opts(P):
+        s = P.schedule
+        return mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner,
+                            n_cgs=s.n_cgs, tol=P.tol, precision=P.precision, max_iters=max_iters)
+
+    probs = [mk.Problem(P.dim, P.nx, P.tau, P.theta, P.dt, P.nt,
+                        None if P.g is None else torch.from_numpy(P.g).to(dev), ny=P.ny) for P in ms]
+    u0 = [torch.from_numpy(P.u0).to(dev) for P in ms]
+    outs = [torch.empty((P.nt + 1,) + P.space_shape(), dtype=torch.float64, device=dev) for P in ms]
+    ol = [opts(P) for P in ms]
+    points = int(sum(P.nx * P.ny * (P.nt + 1) for P in ms))
+    t0 = time.perf_counter()
+    b = mk.Batch(probs, ol, autotune=True)
+    t_setup = time.perf_counter() - t0
+    b.solve(u0, outs, allow_not_converged=True)          # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    infos = b.solve(u0, outs, allow_not_converged=True)
+    t_batch = time.perf_counter() - t0
+    b.close()
+    for p, o, x, y in zip(probs, ol, u0, outs):          # warm-up of the single solves
+        mk.mk_solve(p.handle, x, y, o, allow_not_converged=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for p, o, x, y in zip(probs, ol, u0, outs):
+        mk.mk_solve(p.handle, x, y, o, allow_not_converged=True)
+    torch.cuda.synchronize(dev)
+    t_seq = time.perf_counter() - t0
+    for p in probs:
+        p.close()
+    conv = [i.rel_residual <= 1.0001 * P.tol for i, P in zip(infos, ms)]
+    return {"problems": len(ms), "points": points, "s": t_batch, "sequential_s": t_seq,
+            "speedup_vs_sequential": t_seq / t_batch, "setup_s": t_setup,
+            "Gpoints_per_s": points / t_batch / 1e9, "converged": int(sum(conv)),
+            "max_iters": max_iters, "iterations": [int(i.iterations) for i in infos],
+            "workload": "batched_problems(seed=4) members 0-11 (1D) and 48-51 (2D), mixed, tol 1e-10"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -258,6 +302,13 @@ def main():
                 tm.append(e0.elapsed_time(e1))
         u_march = u_dev.cpu().numpy().copy()
 
+        # ---------------- batched uneven problems ----------------
+        line["paths"] = {}
+        try:
+            line["paths"]["mk_batch"] = bench_batch(mk, torch, dev)
+        except Exception as e:   # reported, not fatal: the headline does not depend on it
+            line["paths"]["mk_batch"] = {"error": str(e)[:200]}
+
         # ---------------- roofline: kernel-class timing of one profiled solve ----------------
         lib = mk.lib()
         lib.mk_set_profiling(1)
@@ -315,7 +366,7 @@ def main():
         line["cpu_baseline"] = {"value": statistics.median(tc), "unit": "s", "cores": 1, "kind": "oracle",
                                 "sample": "full workload solved 3 times (sequential FP64 theta-march, "
                                           "Thomas algorithm, plain C)"}
-        line["paths"] = {
+        line["paths"].update({
             "mk_mixed": {"s": ms_mixed / 1e3, "iterations": int(inf_mixed[-1].iterations),
                          "rel_residual": inf_mixed[-1].rel_residual,
                          "max_rel_err": O.max_rel_error(u_mixed, ref)},
@@ -324,7 +375,7 @@ def main():
                         "max_rel_err": O.max_rel_error(u_fp64, ref)},
             "march_gpu_fp64": {"s": statistics.mean(tm) / 1e3, "max_rel_err": O.max_rel_error(u_march, ref)},
             "oracle_cpu": {"s": statistics.median(tc)},
-        }
+        })
     prob.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -254,6 +254,37 @@ mk_status mk_op_orthogonalize(mk_problem *p, int32_t j, const double *V, double 
    solved on the device by Givens rotations.  y: host, j doubles; res: |g_{j+1}|. */
 mk_status mk_op_lsq(int32_t j, const double *H, double beta, double *y, double *res, void *stream);
 
+/* ---- Batches of independent problems (Sec. 4's method applied to many problems at once) ----
+
+   A batch solves `count` independent problems of any sizes, dimensions, theta and tau
+   together.  Every problem gets its own level hierarchy (built from opts[i], or the defaults
+   when opts is NULL), and one CUDA graph holds one restart cycle of every problem, each on
+   its own branch, so a replay of the graph advances all unconverged problems at once and
+   the GPU overlaps their kernels.  A problem that has converged, failed or used max_iters
+   is stopped through its own done flag; its branch then exits at once in later replays.
+   With autotune != 0 the tile depth of each level's 1D transfer kernels and the coarsest
+   slab solver variant (sine transform, partitioned, cyclic reduction) are chosen by timing
+   them on the problem's own buffers at creation (a few milliseconds per problem).
+
+   mk_create_batch: problems = count distinct handles (not owned; they must outlive the
+     batch and keep their source); opts = NULL or count option structs.  The batch holds
+     its hierarchies, graph and streams on the current device until mk_destroy_batch.
+     Errors: MK_ERR_INVALID (count < 1, a NULL or repeated handle, bad options),
+     MK_ERR_NOMEM, MK_ERR_CUDA.
+   mk_solve_batch: u0[i] = initial state of problem i (nx or ny x nx), u_out[i] = its
+     (nt+1) x n solution; each pointer host or device as elsewhere in this ABI.  infos =
+     NULL or count structs (solve_ms and kernel_launches are those of the whole batch).
+     Returns MK_OK when every problem converged, else the first non-OK status of a member
+     (MK_ERR_NOT_CONVERGED, MK_ERR_NONFINITE); every u_out[i] holds that member's last
+     iterate.  Synchronises `stream` before returning.  One batch must not be solved from
+     two host threads at once. */
+typedef struct mk_batch mk_batch;
+mk_status mk_create_batch(mk_problem *const *problems, int32_t count, const mk_solve_opts *opts,
+                          int32_t autotune, mk_batch **out);
+mk_status mk_solve_batch(mk_batch *batch, const double *const *u0, double *const *u_out,
+                         mk_solve_info *infos, void *stream);
+void mk_destroy_batch(mk_batch *batch);
+
 /* ---- Allocation-free residual (a library extension: the paper has no counterpart) ----
 
    r = f - A_h u on the fine level (Eq. (finesys)), its norm ||r||_2 and optionally the

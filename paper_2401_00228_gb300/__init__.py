@@ -9,7 +9,7 @@ Functions carry the ABI's names; ``Problem`` and ``HeatSolve`` are conveniences 
 from __future__ import annotations
 
 import ctypes
-from typing import Optional, Sequence
+from typing import List, Optional, Sequence
 
 import numpy as np
 
@@ -21,6 +21,7 @@ __all__ = ["mk_default_opts", "mk_create_problem", "mk_set_source", "mk_destroy"
            "mk_solve_rhs", "mk_march", "mk_adjoint", "mk_level_info", "mk_op_rhs", "mk_op_apply",
            "mk_op_residual", "mk_op_residual_noalloc", "mk_op_restrict", "mk_op_interp_correct", "mk_op_coarsest",
            "mk_op_precond", "mk_op_orthogonalize", "mk_op_lsq", "mk_kernel_launch_count",
+           "mk_create_batch", "mk_solve_batch", "mk_destroy_batch", "Batch",
            "make_opts", "Problem", "HeatSolve", "MKError", "lib"]
 
 
@@ -128,6 +129,67 @@ def mk_solve(p: int, u0, u_out, opts: Optional[mk_solve_opts] = None, stream=Non
                           ctypes.byref(info), s)
     _lib.check(code, "mk_solve", allow=(_lib.MK_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return info
+
+
+def mk_create_batch(problems: Sequence[int], opts: Optional[Sequence[mk_solve_opts]] = None,
+                    autotune: bool = True) -> int:
+    """Batch handle for the given problem handles (one options struct per problem, or None)."""
+    n = len(problems)
+    arr = (ctypes.c_void_p * n)(*problems)
+    oarr = (mk_solve_opts * n)(*opts) if opts is not None else None
+    out = ctypes.c_void_p()
+    _lib.check(lib().mk_create_batch(arr, n, oarr, 1 if autotune else 0, ctypes.byref(out)),
+               "mk_create_batch")
+    return out.value
+
+
+def mk_solve_batch(b: int, u0s: Sequence, u_outs: Sequence, stream=None,
+                   allow_not_converged: bool = False) -> List[mk_solve_info]:
+    """Solve every member: u0s[i] -> u_outs[i]; returns the per-member infos."""
+    n = len(u0s)
+    if len(u_outs) != n:
+        raise ValueError("u0s and u_outs differ in length")
+    a0 = (ctypes.c_void_p * n)(*[_ptr(x) for x in u0s])
+    a1 = (ctypes.c_void_p * n)(*[_ptr(x) for x in u_outs])
+    infos = (mk_solve_info * n)()
+    s = _stream(stream) or _current_stream_for(*u0s, *u_outs)
+    code = lib().mk_solve_batch(b, a0, a1, infos, s)
+    _lib.check(code, "mk_solve_batch",
+               allow=(_lib.MK_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return list(infos)
+
+
+def mk_destroy_batch(b: int) -> None:
+    lib().mk_destroy_batch(b)
+
+
+class Batch:
+    """Owning handle of an mk_batch over Problem objects (which must outlive it)."""
+
+    def __init__(self, problems: Sequence["Problem"], opts: Optional[Sequence[mk_solve_opts]] = None,
+                 autotune: bool = True):
+        self.problems = list(problems)
+        self.handle = mk_create_batch([p.handle for p in self.problems], opts, autotune)
+
+    def solve(self, u0s, u_outs, stream=None, allow_not_converged=False) -> List[mk_solve_info]:
+        return mk_solve_batch(self.handle, u0s, u_outs, stream, allow_not_converged)
+
+    def close(self):
+        if self.handle:
+            mk_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def mk_solve_rhs(p: int, f, u_out, opts: Optional[mk_solve_opts] = None, stream=None) -> mk_solve_info:

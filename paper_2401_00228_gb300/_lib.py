@@ -63,6 +63,9 @@ SIGNATURES = {
     "mk_set_source": (ctypes.c_int, [_P, _P, _P]),
     "mk_destroy": (None, [_P]),
     "mk_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(mk_solve_opts), _P, ctypes.POINTER(mk_solve_info), _P]),
+    "mk_create_batch": (ctypes.c_int, [_P, _I, ctypes.POINTER(mk_solve_opts), _I, ctypes.POINTER(_P)]),
+    "mk_solve_batch": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mk_solve_info), _P]),
+    "mk_destroy_batch": (None, [_P]),
     "mk_solve_rhs": (ctypes.c_int, [_P, _P, ctypes.POINTER(mk_solve_opts), _P, ctypes.POINTER(mk_solve_info), _P]),
     "mk_march": (ctypes.c_int, [_P, _P, _P, _P]),
     "mk_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mk_solve_opts), _P, _P, _P, _P,

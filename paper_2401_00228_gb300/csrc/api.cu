@@ -37,6 +37,38 @@ struct mk_problem {
     Problem P;
 };
 
+// A batch: its own hierarchy per problem and one CUDA graph whose replay runs one restart
+// cycle of every problem, each on its own branch.
+struct mk_batch {
+    std::vector<mk_problem *> probs;
+    std::vector<mk_solve_opts> opts;
+    std::vector<std::unique_ptr<Hierarchy>> H;
+    std::vector<cudaStream_t> streams;   // one per problem + the capture origin
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_kernels = 0;
+    DevMem flagptrs, miscptrs, gflags, gmisc;   // status gather
+    std::vector<int> one;                       // source of the "stop" flag copies
+    ~mk_batch() {
+        cudaDeviceSynchronize();
+        if (graph) cudaGraphExecDestroy(graph);
+        for (cudaStream_t s : streams)
+            if (s) cudaStreamDestroy(s);
+    }
+};
+
+namespace mk {
+// flags[0..7] and misc[0..7] of every problem's level-1 FGMRES state into two arrays
+__global__ void k_gather_status(const int *const *flags, const double *const *misc, int n,
+                                int *of, double *om) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int q = 0; q < 8; ++q) {
+        of[8 * i + q] = flags[i][q];
+        om[8 * i + q] = misc[i][q];
+    }
+}
+}  // namespace mk
+
 #define CK(call)                                                                 \
     do {                                                                         \
         cudaError_t e_ = (call);                                                 \
@@ -869,6 +901,159 @@ mk_status mk_op_lsq(int32_t j, const double *H, double beta, double *y, double *
     if (res) *res = hr;
     return MK_OK;
 }
+
+mk_status mk_create_batch(mk_problem *const *problems, int32_t count, const mk_solve_opts *opts,
+                          int32_t autotune, mk_batch **out) {
+    if (!problems || !out || count < 1) return MK_ERR_INVALID;
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        if (!problems[i]) return MK_ERR_INVALID;
+        for (int k = 0; k < i; ++k)
+            if (problems[k] == problems[i]) return MK_ERR_INVALID;   // one hierarchy each
+    }
+    CKS(ensure_device());
+    std::unique_ptr<mk_batch> b(new mk_batch());
+    b->probs.assign(problems, problems + count);
+    cudaStream_t s0 = nullptr;
+    for (int i = 0; i < count; ++i) {
+        mk_solve_opts o = resolve_opts(opts ? &opts[i] : nullptr);
+        Problem &P = problems[i]->P;
+        CKS(validate_opts(P, o));
+        std::unique_ptr<Hierarchy> H;
+        CKS(build_hierarchy_new(P, o, H));
+        if (autotune) CKS(autotune_hierarchy(*H, s0));
+        b->opts.push_back(o);
+        b->H.push_back(std::move(H));
+    }
+    CK(cudaStreamSynchronize(s0));
+    b->streams.assign(count + 1, nullptr);
+    for (auto &st : b->streams) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    std::vector<Problem *> P;
+    std::vector<Hierarchy *> H;
+    std::vector<const int *> fp;
+    std::vector<const double *> mp;
+    for (int i = 0; i < count; ++i) {
+        P.push_back(&problems[i]->P);
+        H.push_back(b->H[i].get());
+        fp.push_back(b->H[i]->lv[0]->ks.flags);
+        mp.push_back(b->H[i]->lv[0]->ks.misc());
+    }
+    CKS(capture_batch(P, H, b->streams, b->graph, b->graph_kernels));
+    CK(b->flagptrs.alloc(sizeof(void *) * count));
+    CK(b->miscptrs.alloc(sizeof(void *) * count));
+    CK(cudaMemcpy(b->flagptrs.p, fp.data(), sizeof(void *) * count, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->miscptrs.p, mp.data(), sizeof(void *) * count, cudaMemcpyHostToDevice));
+    CK(b->gflags.alloc(sizeof(int) * 8 * count));
+    CK(b->gmisc.alloc(sizeof(double) * 8 * count));
+    b->one.assign(count, 1);
+    *out = b.release();
+    return MK_OK;
+}
+
+mk_status mk_solve_batch(mk_batch *b, const double *const *u0, double *const *u_out,
+                         mk_solve_info *infos, void *stream) {
+    if (!b || !u0 || !u_out) return MK_ERR_INVALID;
+    const int n = (int)b->probs.size();
+    for (int i = 0; i < n; ++i)
+        if (!u0[i] || !u_out[i]) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t launches_start = mk_kernel_launch_count();
+    // right-hand sides (f = source blocks, f_0 = u0) and r_0 = f for every problem
+    std::vector<OutStage> os(n);
+    {
+        std::vector<DevMem> tin(n);
+        for (int i = 0; i < n; ++i) {
+            Problem &P = b->probs[i]->P;
+            Hierarchy &H = *b->H[i];
+            const double *du0 = nullptr;
+            CKS(stage_in(u0[i], space_n(P), tin[i], du0, s));
+            CKS(stage_out(u_out[i], st_n(P), os[i]));
+            CK(cudaMemcpyAsync(H.f.p, P.fsrc.p, sizeof(double) * P.g.len, cudaMemcpyDeviceToDevice, s));
+            Geom g0 = P.g;
+            g0.nt = 0;
+            launch_pack<double, double>(g0, du0, H.f.as<double>(), s);
+            CKS(solve_prepare(H, b->opts[i], s));
+        }
+        CK(cudaStreamSynchronize(s));   // before the staging buffers are released
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    std::vector<int> hf(8 * (size_t)n);
+    std::vector<double> hm(8 * (size_t)n);
+    std::vector<mk_status> st(n, MK_OK);
+    std::vector<int> finished(n, 0), cycles(n, 0);
+    int max_cycles = 0;
+    for (int i = 0; i < n; ++i)
+        max_cycles = std::max(max_cycles, b->opts[i].max_iters / std::max(1, b->opts[i].restart) + 2);
+    for (int c = 0; c < max_cycles; ++c) {
+        CK(cudaGraphLaunch(b->graph, s));
+        add_launches(b->graph_kernels);
+        k_gather_status<<<(n + 127) / 128, 128, 0, s>>>(b->flagptrs.as<const int *>(),
+                                                        b->miscptrs.as<const double *>(), n,
+                                                        b->gflags.as<int>(), b->gmisc.as<double>());
+        count_launch();
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(hf.data(), b->gflags.p, sizeof(int) * 8 * n, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hm.data(), b->gmisc.p, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        int left = 0;
+        for (int i = 0; i < n; ++i) {
+            if (finished[i]) continue;
+            ++cycles[i];
+            const int *f = &hf[8 * (size_t)i];
+            bool stop = false;
+            if (f[3]) {
+                st[i] = MK_ERR_NONFINITE;
+                stop = true;
+            } else if (f[0]) {
+                finished[i] = 1;   // converged: its kernels exit early from now on
+            } else if (f[4] >= b->opts[i].max_iters) {
+                st[i] = MK_ERR_NOT_CONVERGED;
+                stop = true;
+            }
+            if (stop) {
+                // freeze this problem: its done flag stops its branch in later replays
+                finished[i] = 1;
+                CK(cudaMemcpyAsync(b->H[i]->lv[0]->ks.flags, &b->one[i], sizeof(int),
+                                   cudaMemcpyHostToDevice, s));
+            }
+            if (!finished[i]) ++left;
+        }
+        if (left == 0) break;
+    }
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    mk_status result = MK_OK;
+    for (int i = 0; i < n; ++i) {
+        if (!finished[i] && st[i] == MK_OK) st[i] = MK_ERR_NOT_CONVERGED;
+        Problem &P = b->probs[i]->P;
+        launch_unpack<double, double>(P.g, b->H[i]->u.as<double>(), os[i].dev, s);
+        CK(cudaGetLastError());
+        CKS(finish_out(os[i], s));
+        if (infos) {
+            const int *f = &hf[8 * (size_t)i];
+            const double *m = &hm[8 * (size_t)i];
+            infos[i].iterations = f[4];
+            infos[i].restarts = cycles[i];
+            infos[i].f_norm = m[3];
+            infos[i].rel_residual = m[3] > 0.0 ? m[4] / m[3] : 0.0;
+            infos[i].solve_ms = ms;
+            infos[i].kernel_launches = (int32_t)(mk_kernel_launch_count() - launches_start);
+            infos[i].levels = (int32_t)b->H[i]->lv.size();
+        }
+        if (result == MK_OK && st[i] != MK_OK) result = st[i];
+    }
+    CK(cudaStreamSynchronize(s));
+    return result;
+}
+
+void mk_destroy_batch(mk_batch *b) { delete b; }
 
 // Allocation-free residual: pointer checks only, then one kernel launch (noalloc.cu).
 mk_status mk_op_residual_noalloc(const mk_problem *p, const double *f, const double *u, double *r,

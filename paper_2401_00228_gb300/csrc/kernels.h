@@ -125,6 +125,10 @@ void launch_slab_1d_dst(const Geom &g, const float *tab, const float2 *tw, int N
                         float *rh, int ldd, const float *r, float *x, const int *done,
                         cudaStream_t s);
 
+// Tile depth (time steps per thread) for the tiled 1D transfer launches that follow on this
+// host thread: restriction in {1, 2, 4}, interpolation in {2, 4}; 0 = built-in heuristic.
+void set_tile_hint(int kc_restrict, int kc_interp);
+
 // Time-tiled 1D variants for nu = 2 (transfer1d.cu).  Each returns false, launching
 // nothing, when the case is not covered (2D, nu != 2); the caller then uses the general
 // kernel.  The caller brackets the launch (profiling, launch count).

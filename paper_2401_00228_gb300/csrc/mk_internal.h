@@ -95,6 +95,7 @@ void tri_eigen(const Tri &L, std::vector<double> &lam, std::vector<double> &S,
 // ---------------------------------------------------------------------------------------
 extern int g_num_sms;
 void count_launch(int n = 1);
+void add_launches(int64_t n);   // n kernels of a replayed graph
 void set_cuda_error(cudaError_t e);
 
 enum ProfClass {

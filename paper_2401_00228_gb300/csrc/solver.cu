@@ -208,6 +208,16 @@ mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out) {
         return MK_OK;
     }
     P.H.reset();
+    std::unique_ptr<Hierarchy> H;
+    mk_status st = build_hierarchy_new(P, o, H);
+    if (st != MK_OK) return st;
+    P.H = std::move(H);
+    out = P.H.get();
+    return MK_OK;
+}
+
+mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_ptr<Hierarchy> &out) {
+    OptsKey key = make_key(o);
     std::unique_ptr<Hierarchy> H(new Hierarchy());
     H->key = key;
     H->precision = o.precision;
@@ -290,8 +300,7 @@ mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out) {
     MKCK(H->counters.alloc(sizeof(unsigned) * 16));
     H->rs.partials = H->partials.as<double>();
     H->rs.counter = H->counters.as<unsigned>();
-    P.H = std::move(H);
-    out = P.H.get();
+    out = std::move(H);
     return MK_OK;
 }
 
@@ -301,15 +310,16 @@ mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out) {
 template <typename Tc>
 void enqueue_coarsest_t(Hierarchy &H, const int *done, cudaStream_t s) {
     Level &C = *H.lv.back();
+    const int kind = C.coarse_kind;   // 0: sine transform, else partitioned, else PCR
     if constexpr (std::is_same<Tc, float>::value) {
-        if (C.dstN2 > 0) {
+        if (C.dstN2 > 0 && (kind == 0 || kind == 1)) {
             launch_slab_1d_dst(C.g, C.dst.as<float>(), C.dsttw.as<float2>(), C.dstN2, H.key.n_cgs,
                                C.dstbuf.as<float>(), C.dstld, C.R.as<float>(), C.X.as<float>(),
                                done, s);
             return;
         }
     }
-    if (C.g.dim == 1 && C.spikeU > 0)
+    if (C.g.dim == 1 && C.spikeU > 0 && kind != 3)
         launch_slab_1d_warp<Tc>(C.g, C.w.b, C.spike.as<Tc>(), C.spikeU, H.key.n_cgs, C.R.as<Tc>(),
                                 C.X.as<Tc>(), done, s, PROF_SLAB);
     else if (C.g.dim == 1)
@@ -338,6 +348,7 @@ static thread_local int t_outer_j = -1;
 
 static void set_ctx(const Level &L, int level) {
     prof_set_context(level + 1, t_outer_j, (double)L.g.interior());
+    set_tile_hint(L.kc_r, L.kc_i);
 }
 
 // x_j = sigma_j V_j - Z vt and w = A x_j (K4).  Level 1 of the mixed solve keeps V and w as
@@ -468,7 +479,6 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s) {
 }
 
 void release_pairs(std::vector<ProfPair> &pairs);
-void add_launches(int64_t n);
 
 Hierarchy::~Hierarchy() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -509,6 +519,27 @@ static mk_status capture_cycle(Problem &P, Hierarchy &H) {
     return MK_OK;
 }
 
+mk_status solve_prepare(Hierarchy &H, const mk_solve_opts &o, cudaStream_t s) {
+    Level &L = *H.lv[0];
+    const int64_t len = L.g.len;
+    MKCK(cudaMemsetAsync(H.u.p, 0, sizeof(double) * len, s));
+    MKCK(cudaMemsetAsync(L.ks.flags, 0, sizeof(int) * 8, s));
+    // the tolerance goes through a device-side copy of H's own (the source buffer of an
+    // asynchronous copy must outlive it)
+    H.tol_host = o.tol;
+    MKCK(cudaMemcpyAsync(L.ks.misc() + 7, &H.tol_host, sizeof(double), cudaMemcpyHostToDevice, s));
+    // r_0 = f (u^0 = 0): ||f||, tol * ||f||, v_1
+    t_outer_j = -1;
+    set_ctx(L, 0);
+    if (H.precision == 0)
+        launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<double>(),
+                        H.rs, 0, L.ks, EPI_OUTER_INIT, s);
+    else
+        launch_residual_df(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<float2>(),
+                           H.rs, 0, L.ks, EPI_OUTER_INIT, s);
+    return MK_OK;
+}
+
 mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const double *f_padded,
                     mk_solve_info *info, cudaStream_t s) {
     Level &L = *H.lv[0];
@@ -520,20 +551,10 @@ mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const doub
     MKCK(cudaEventRecord(e0, s));
     if (f_padded && f_padded != H.f.as<double>())
         MKCK(cudaMemcpyAsync(H.f.p, f_padded, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
-    MKCK(cudaMemsetAsync(H.u.p, 0, sizeof(double) * len, s));
-    MKCK(cudaMemsetAsync(L.ks.flags, 0, sizeof(int) * 8, s));
-    static thread_local double tolbuf;
-    tolbuf = o.tol;
-    MKCK(cudaMemcpyAsync(L.ks.misc() + 7, &tolbuf, sizeof(double), cudaMemcpyHostToDevice, s));
-    // r_0 = f (u^0 = 0): ||f||, tol * ||f||, v_1
-    t_outer_j = -1;
-    set_ctx(L, 0);
-    if (H.precision == 0)
-        launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<double>(),
-                        H.rs, 0, L.ks, EPI_OUTER_INIT, s);
-    else
-        launch_residual_df(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<float2>(),
-                           H.rs, 0, L.ks, EPI_OUTER_INIT, s);
+    {
+        mk_status st = solve_prepare(H, o, s);
+        if (st != MK_OK) return st;
+    }
     // one restart cycle as a CUDA graph (captured once per hierarchy and profiling mode)
     if (o.use_graph && (!H.graph || H.graph_profiled != prof_enabled())) {
         mk_status st = capture_cycle(P, H);
@@ -595,6 +616,154 @@ mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const doub
         info->kernel_launches = (int32_t)(launches_total() - launches_start);
     }
     return status;
+}
+
+mk_status capture_batch(std::vector<Problem *> &P, std::vector<Hierarchy *> &H,
+                        std::vector<cudaStream_t> &streams, cudaGraphExec_t &graph,
+                        int64_t &kernels) {
+    const size_t n = P.size();
+    if (n == 0 || H.size() != n || streams.size() < n + 1) return MK_ERR_INVALID;
+    kernels = 0;
+    cudaStream_t cs = streams[n];   // the capture origin
+    std::vector<cudaEvent_t> ev(n + 1, nullptr);
+    for (auto &e : ev) MKCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    set_capture_counter(&kernels);
+    prof_set_sink(nullptr);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev[n], cs);
+    // fork: every problem's restart cycle on its own branch, then join on the origin
+    for (size_t i = 0; i < n && ce == cudaSuccess; ++i) {
+        ce = cudaStreamWaitEvent(streams[i], ev[n], 0);
+        if (ce != cudaSuccess) break;
+        enqueue_outer_cycle(*P[i], *H[i], streams[i]);
+        ce = cudaEventRecord(ev[i], streams[i]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, ev[i], 0);
+    }
+    set_capture_counter(nullptr);
+    cudaError_t ce2 = cudaStreamEndCapture(cs, &g);
+    if (ce == cudaSuccess) ce = ce2;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (ce != cudaSuccess) {
+        set_cuda_error(ce);
+        graph = nullptr;
+        return MK_ERR_CUDA;
+    }
+    return MK_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Autotuner: tile depths of the 1D transfers per level, coarsest solver variant.
+// ---------------------------------------------------------------------------------------
+template <typename F>
+static float time_launch(F launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    launch();   // warm-up
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+        cudaEventRecord(e0, s);
+        launch();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    return best;
+}
+
+template <typename Tc, typename Tv>
+static void tune_level(Hierarchy &H, int l, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    Level &L = *H.lv[l];
+    Level &C = *H.lv[l + 1];
+    if (L.g.dim != 1 || L.nu != 2) return;
+    const Tv *v = L.V.as<Tv>();
+    // restriction into the next level's first basis slot (or the coarsest right-hand side)
+    Tc *dst = C.coarsest ? C.R.as<Tc>() : C.V.as<Tc>();
+    const KState ksc = C.coarsest ? KState{nullptr, nullptr, 0} : C.ks;
+    float best = 1e30f;
+    for (int kc : {1, 2, 4}) {
+        set_tile_hint(kc, 0);
+        const float t = time_launch([&] {
+            launch_restrict<Tv, Tc, Tc>(L.g, C.g, L.nu, L.space, L.w, op_of<Tc>(L), v, nullptr, dst,
+                                        H.rs, 0, ksc, nullptr, s);
+        }, s, e0, e1);
+        if (t < best) {
+            best = t;
+            L.kc_r = kc;
+        }
+    }
+    set_tile_hint(0, 0);
+}
+
+template <typename Tc>
+static void tune_interp(Hierarchy &H, int l, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    Level &L = *H.lv[l];
+    Level &C = *H.lv[l + 1];
+    if (L.g.dim != 1 || L.nu != 2) return;
+    const int mc = C.coarsest ? 1 : C.m;
+    const double *yc = C.coarsest ? nullptr : C.ks.y();
+    float best = 1e30f;
+    for (int kc : {2, 4}) {
+        set_tile_hint(0, kc);
+        const float t = time_launch([&] {
+            if (l == 0 && H.precision == 1)
+                InterpStep<float2, float, float, float2, double>::run(L, C, L.V.as<float2>(), nullptr,
+                                                                      C.X.as<float>(), mc, yc, 0,
+                                                                      nullptr, s);
+            else
+                InterpStep<Tc, Tc, Tc, Tc, Tc>::run(L, C, L.V.as<Tc>(), nullptr, C.X.as<Tc>(), mc,
+                                                    yc, 0, nullptr, s);
+        }, s, e0, e1);
+        if (t < best) {
+            best = t;
+            L.kc_i = kc;
+        }
+    }
+    set_tile_hint(0, 0);
+}
+
+mk_status autotune_hierarchy(Hierarchy &H, cudaStream_t s) {
+    cudaEvent_t e0, e1;
+    MKCK(cudaEventCreate(&e0));
+    MKCK(cudaEventCreate(&e1));
+    const int L = (int)H.lv.size();
+    const bool fp64 = H.precision == 0;
+    for (int l = 0; l + 1 < L; ++l) {
+        if (fp64) {
+            tune_level<double, double>(H, l, s, e0, e1);
+            tune_interp<double>(H, l, s, e0, e1);
+        } else {
+            if (l == 0) tune_level<float, float2>(H, l, s, e0, e1);
+            else tune_level<float, float>(H, l, s, e0, e1);
+            tune_interp<float>(H, l, s, e0, e1);
+        }
+    }
+    // coarsest: every applicable variant of the decoupled slab solve
+    Level &C = *H.lv.back();
+    if (C.g.dim == 1) {
+        float best = 1e30f;
+        for (int kind : {1, 2, 3}) {
+            if (kind == 1 && (fp64 || C.dstN2 == 0)) continue;
+            if (kind == 2 && C.spikeU == 0) continue;
+            C.coarse_kind = kind;
+            const float t = time_launch([&] { enqueue_coarsest(H, nullptr, s); }, s, e0, e1);
+            if (t < best) {
+                best = t;
+                C.coarse_kind_best = kind;
+            }
+        }
+        C.coarse_kind = C.coarse_kind_best;
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return MK_ERR_CUDA;
+    }
+    return MK_OK;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -63,6 +63,9 @@ struct Level {
     int spikeU = 0;
     DevMem dst, dsttw, dstbuf;   // sine-transform slab solver (1D uniform L, FP32 cycle)
     int dstN2 = 0, dstld = 0;
+    // autotuned choices (0 = heuristic): tile depth of the restriction from / interpolation
+    // on this level, and the coarsest solver (1 sine transform, 2 partitioned, 3 PCR)
+    int kc_r = 0, kc_i = 0, coarse_kind = 0, coarse_kind_best = 0;
     DevMem Sx, Sxi, lamx, Sy, Syi, lamy;
 };
 
@@ -77,6 +80,7 @@ struct Hierarchy {
     bool graph_profiled = false;        // captured with kernel-class timing events
     int64_t graph_kernels = 0;          // kernels in one replay of the graph
     std::vector<ProfPair> graph_pairs;  // timing events inside the graph
+    double tol_host = 0.0;              // source of the tolerance's host-to-device copy
     ~Hierarchy();
 };
 
@@ -103,6 +107,11 @@ template <>
 inline SpaceOp<float> op_of<float>(const Level &L) { return L.op32; }
 
 mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out);
+// A hierarchy owned by the caller (not cached in P).
+mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_ptr<Hierarchy> &out);
+// Time the tile depths of the 1D transfers on every level and the coarsest solver variants
+// on this hierarchy's own buffers, and keep the fastest (a few ms; state is reset by a solve).
+mk_status autotune_hierarchy(Hierarchy &H, cudaStream_t s);
 // Sine-transform slab tables for coarsest level C when they apply (1D, L uniform, n + 1 a
 // power of two, 1 <= n_cgs with at most 64 steps per slab); C.dstN2 stays 0 otherwise.
 mk_status build_dst_tables(Level &C, int n_cgs);
@@ -111,6 +120,13 @@ mk_status validate_opts(const Problem &P, const mk_solve_opts &o);
 // FGMRES + MK on f (padded FP64, level 1) -> H.u.  f is copied into H.f.
 mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const double *f_padded,
                     mk_solve_info *info, cudaStream_t s);
+// The part of run_solve before its restart loop: u = 0, flags, tolerance, r_0 = f.
+mk_status solve_prepare(Hierarchy &H, const mk_solve_opts &o, cudaStream_t s);
+// One CUDA graph whose replay runs one restart cycle of every hierarchy, each on its own
+// branch (captured on streams[i]); kernels counts the graph's kernels.
+mk_status capture_batch(std::vector<Problem *> &P, std::vector<Hierarchy *> &H,
+                        std::vector<cudaStream_t> &streams, cudaGraphExec_t &graph,
+                        int64_t &kernels);
 
 // x_j = Q_l v_j, w = A_l x_j for basis slot j of level l (enqueue only).
 void enqueue_cycle_step(Hierarchy &H, int l, int j, const int *done, cudaStream_t s);

@@ -442,7 +442,16 @@ inline int tiled_kc(int xb, int rows, bool allow1) {
     return kc;
 }
 
+// tile depths chosen by the autotuner for the level being enqueued (0: heuristic)
+thread_local int t_kc_restrict = 0;
+thread_local int t_kc_interp = 0;
+
 }  // namespace
+
+void set_tile_hint(int kc_restrict, int kc_interp) {
+    t_kc_restrict = kc_restrict;
+    t_kc_interp = kc_interp;
+}
 
 template <typename Tin, typename Tout, typename Tc>
 bool launch_restrict_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space,
@@ -452,7 +461,8 @@ bool launch_restrict_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space
     if (gf.dim != 1 || nu != 2) return false;
     const int xb = (gf.nx + TT * PT - 1) / (TT * PT);
     const int rows = gc.nt + 1;
-    const int kc = tiled_kc(xb, rows, true);
+    const int h = t_kc_restrict;
+    const int kc = (h == 1 || h == 2 || h == 4) ? h : tiled_kc(xb, rows, true);
     const int yb = (rows + kc - 1) / kc;
     if (ks_c.d && (int64_t)xb * yb > rs.max_blocks) return false;
     const dim3 grid(xb, yb);
@@ -477,7 +487,8 @@ bool launch_interp_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space, 
     if (gf.dim != 1 || nu != 2) return false;
     const int xb = (gf.nx + TT * PT - 1) / (TT * PT);
     const int rows = gf.nt + 1;
-    const int kc = tiled_kc(xb, rows, false);
+    const int h = t_kc_interp;
+    const int kc = (h == 2 || h == 4) ? h : tiled_kc(xb, rows, false);
     const dim3 grid(xb, (rows + kc - 1) / kc);
     const Tc a = (Tc)w.a, b = (Tc)w.b;
 #define MK_IT(S, M, K)                                                                        \
@@ -508,7 +519,8 @@ bool launch_interp_df_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool spac
     if (gf.dim != 1 || nu != 2) return false;
     const int xb = (gf.nx + TT * PT - 1) / (TT * PT);
     const int rows = gf.nt + 1;
-    const int kc = tiled_kc(xb, rows, false);
+    const int h = t_kc_interp;
+    const int kc = (h == 2 || h == 4) ? h : tiled_kc(xb, rows, false);
     const dim3 grid(xb, (rows + kc - 1) / kc);
     const int hb = has_b ? 1 : 0;
 #define MK_ID(S, M, K)                                                                        \
