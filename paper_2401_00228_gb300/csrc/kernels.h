@@ -80,10 +80,13 @@ void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Wei
 // ---- Krylov family (krylov.cu) --------------------------------------------------------
 // Arnoldi step j on a process with state ks, vectors of length len (padded):
 //   h_i = sigma_i <W, V_i>, i = 0..j   (multidot, partials + last block)
+// close_mode != 0 (inner levels, last iteration j = m - 1, first pass): the new basis vector
+// is not needed, so its norm comes from Pythagoras, ||w - sum h_i v_i||^2 = ||w||^2 - sum h_i^2,
+// and the update epilogue of mode close_mode (the least squares) runs in this kernel.
 template <typename TW, typename TV>
 void launch_multidot(int64_t len, const TW *W, const TV *V, int64_t vstride, int j,
                      const ReduceScratch &rs, KState ks, bool second_pass, const int *done,
-                     cudaStream_t s);
+                     cudaStream_t s, int close_mode = 0);
 //   V_{j+1} = W - sum_i h_i sigma_i V_i, ||.||^2 -> h_{j+1,j}, sigma_{j+1};
 //   last block also runs the least-squares bookkeeping (Givens for the outer level,
 //   final solve on the last inner iteration).

@@ -47,6 +47,23 @@ __device__ __forceinline__ void multidot_epilogue(const double *res, KState ks, 
     if (!second && threadIdx.x == 0) ks.misc()[2] = res[nv];
 }
 
+// Last inner iteration: h_{j+1,j}^2 = ||w||^2 - sum_i h_ij^2 (orthonormal basis), then the
+// update epilogue of the given mode (least squares) without forming V_{j+1}.
+__device__ __forceinline__ void close_iteration(const double *res, KState ks, int j, int nv,
+                                                int mode) {
+    __syncthreads();   // H's column j, written by several threads, is read by the epilogue
+    double nrm2 = 0.0;
+    if (threadIdx.x == 0) {
+        double s2 = 0.0;
+        for (int i = 0; i < nv; ++i) {
+            const double h = ks.sigma()[i] * res[i];
+            s2 += h * h;
+        }
+        nrm2 = fmax(res[nv] - s2, 0.0);
+    }
+    update_epilogue_block(nrm2, ks, j, mode, 0);
+}
+
 // ---------------------------------------------------------------------------------------
 // multidot: d_i = <W, V_i>, i = 0..j ; first pass also ||W||^2.
 // ---------------------------------------------------------------------------------------
@@ -55,7 +72,8 @@ __global__ void __launch_bounds__(KR_THREADS) k_multidot(int64_t len, const TW *
                                                          const TV *__restrict__ V,
                                                          int64_t vstride, int j,
                                                          ReduceScratch rs, KState ks, int second,
-                                                         const int *__restrict__ done) {
+                                                         const int *__restrict__ done,
+                                                         int close_mode) {
     if (done && *done) return;
     if (second && !ks.flags[2]) return;
     extern __shared__ double smem[];
@@ -107,6 +125,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_multidot(int64_t len, const TW *
         double *res = smem;  // reuse
         finish_slots(rs.partials, rs.max_blocks, nslots, gridDim.x, res);
         multidot_epilogue(res, ks, j, nv, second);
+        if (close_mode && !second) close_iteration(res, ks, j, nv, close_mode);
         if (threadIdx.x == 0) rs.counter[0] = 0u;
     }
 }
@@ -186,7 +205,8 @@ __global__ void __launch_bounds__(KR_THREADS) k_multidot_sb(int64_t len, const T
                                                             const T *__restrict__ V,
                                                             int64_t vstride, ReduceScratch rs,
                                                             KState ks, int second,
-                                                            const int *__restrict__ done) {
+                                                            const int *__restrict__ done,
+                                                            int close_mode) {
     if (done && *done) return;
     if (second && !ks.flags[2]) return;
     constexpr int j = NV - 1;
@@ -230,6 +250,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_multidot_sb(int64_t len, const T
         double *res = acc;  // reuse
         finish_slots(rs.partials, rs.max_blocks, nslots, gridDim.x, res);
         multidot_epilogue(res, ks, j, NV, second);
+        if (close_mode && !second) close_iteration(res, ks, j, NV, close_mode);
         if (threadIdx.x == 0) rs.counter[0] = 0u;
     }
 }
@@ -318,7 +339,7 @@ static int krylov_grid(int64_t len, int64_t per_block) {
 template <typename TW, typename TV>
 void launch_multidot(int64_t len, const TW *W, const TV *V, int64_t vstride, int j,
                      const ReduceScratch &rs, KState ks, bool second_pass, const int *done,
-                     cudaStream_t s) {
+                     cudaStream_t s, int close_mode) {
     int grid = krylov_grid(len, MD_TILE);
     const double alg_n = prof_alg_n() > 0 ? prof_alg_n() : (double)len;
     size_t shm = sizeof(double) * (size_t)(j + 2) * KR_WARPS;
@@ -330,7 +351,10 @@ void launch_multidot(int64_t len, const TW *W, const TV *V, int64_t vstride, int
             const int sec = second_pass ? 1 : 0;
             switch (j + 1) {
 #define MK_MD(N) \
-    case N: k_multidot_sb<N, TV><<<g, KR_THREADS, 0, s>>>(len, W, V, vstride, rs, ks, sec, done); break;
+    case N:                                                                                   \
+        k_multidot_sb<N, TV><<<g, KR_THREADS, 0, s>>>(len, W, V, vstride, rs, ks, sec, done,  \
+                                                      close_mode);                            \
+        break;
                 MK_MD(1) MK_MD(2) MK_MD(3) MK_MD(4) MK_MD(5) MK_MD(6) MK_MD(7) MK_MD(8)
 #undef MK_MD
             }
@@ -340,7 +364,7 @@ void launch_multidot(int64_t len, const TW *W, const TV *V, int64_t vstride, int
         }
     }
     k_multidot<TW, TV><<<grid, KR_THREADS, shm, s>>>(len, W, V, vstride, j, rs, ks,
-                                                      second_pass ? 1 : 0, done);
+                                                      second_pass ? 1 : 0, done, close_mode);
     prof_end(s, PROF_MULTIDOT, (double)(j + 2) * alg_n * sizeof(TV));
     count_launch();
 }
@@ -395,10 +419,10 @@ void launch_lsq(int j, double *H, double beta, double *gg, double *y, double *re
 
 template void launch_multidot<double, double>(int64_t, const double *, const double *, int64_t,
                                               int, const ReduceScratch &, KState, bool,
-                                              const int *, cudaStream_t);
+                                              const int *, cudaStream_t, int);
 template void launch_multidot<float, float>(int64_t, const float *, const float *, int64_t, int,
                                             const ReduceScratch &, KState, bool, const int *,
-                                            cudaStream_t);
+                                            cudaStream_t, int);
 template void launch_update<double, double>(int64_t, const double *, double *, int64_t, int, bool,
                                             const ReduceScratch &, KState, int, bool,
                                             const int *, cudaStream_t);

@@ -412,10 +412,17 @@ static void enqueue_inner_solve(Hierarchy &H, int l, const int *done, cudaStream
     for (int j = 0; j < L.m; ++j) {
         cycle_step_t<Tc, Tc, Tc, Tc, Tc>(H, l, j, done, s);
         set_ctx(L, l);
-        launch_multidot<Tc, Tc>(len, L.W.as<Tc>(), L.V.as<Tc>(), L.stride, j, H.rs, L.ks, false,
-                                done, s);
-        launch_update<Tc, Tc>(len, L.W.as<Tc>(), L.V.as<Tc>(), L.stride, j, j < L.m - 1, H.rs, L.ks,
-                              UPD_INNER, false, done, s);
+        if (j < L.m - 1) {
+            launch_multidot<Tc, Tc>(len, L.W.as<Tc>(), L.V.as<Tc>(), L.stride, j, H.rs, L.ks, false,
+                                    done, s);
+            launch_update<Tc, Tc>(len, L.W.as<Tc>(), L.V.as<Tc>(), L.stride, j, true, H.rs, L.ks,
+                                  UPD_INNER, false, done, s);
+        } else {
+            // last iteration: V_m is not needed; its norm by Pythagoras, least squares in the
+            // same kernel
+            launch_multidot<Tc, Tc>(len, L.W.as<Tc>(), L.V.as<Tc>(), L.stride, j, H.rs, L.ks, false,
+                                    done, s, UPD_INNER);
+        }
     }
 }
 
