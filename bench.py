@@ -196,6 +196,8 @@ def main():
     ap.add_argument("--restart", type=int, default=40)
     ap.add_argument("--orth", type=int, default=0, help="Gram-Schmidt passes: 0 one, 1 conditional, 2 two")
     ap.add_argument("--no-aux", action="store_true", help="skip the secondary paths")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="built-in tile heuristics instead of the per-hierarchy autotuner")
     ap.add_argument("--profile-run", action="store_true",
                     help="run one warm-up solve and one solve of the workload, no timing (the "
                          "command that ncu captures)")
@@ -224,7 +226,7 @@ def main():
     def opts(precision):
         return mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner,
                             n_cgs=s.n_cgs, tol=args.tol, restart=args.restart, precision=precision,
-                            orth=args.orth)
+                            orth=args.orth, autotune=not args.no_autotune)
 
     o_mixed, o_fp64 = opts("mixed"), opts("fp64")
     g_dev = torch.from_numpy(P.g).to(dev)
@@ -286,6 +288,7 @@ def main():
             "config": {"workload": WORKLOAD, "nx": P.nx, "nt": P.nt, "theta": P.theta,
                        "levels": s.levels, "nu": list(s.nu), "m_inner": list(s.m_inner),
                        "n_cgs": s.n_cgs, "restart": args.restart, "tol": args.tol, "orth": args.orth,
+                       "autotune": not args.no_autotune,
                        "precision": "mixed", "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MB write)"},
             "gpu_launches": int(launches),

@@ -88,6 +88,11 @@ typedef struct mk_solve_opts {
     int32_t orth;        /* level-1 Arnoldi: 0 = one classical Gram-Schmidt pass; 1 = a second
                             pass when the norm drops below 1/sqrt(2) of its value (default);
                             2 = always two passes */
+    int32_t autotune;    /* 1: when the hierarchy for these options is built, time the tile depth
+                            of each level's 1D transfer kernels and the coarsest slab solver
+                            variants on its own buffers and keep the fastest (a few ms, once per
+                            hierarchy); 0: built-in heuristics (default; bitwise reproducible
+                            across processes) */
 } mk_solve_opts;
 
 typedef struct mk_solve_info {

@@ -73,7 +73,7 @@ def mk_default_opts() -> mk_solve_opts:
 def make_opts(levels: int = 3, nu: Sequence[int] = (), space: Sequence[bool] = (),
               m_inner: Sequence[int] = (), n_cgs: int = 16, tol: float = 1e-12, restart: int = 40,
               max_iters: int = 2000, precision: str = "fp64", mu: str | float = "lambda_max",
-              use_graph: bool = True, orth: int = 1) -> mk_solve_opts:
+              use_graph: bool = True, orth: int = 1, autotune: bool = False) -> mk_solve_opts:
     """Options struct from Python values (unset per-level entries keep the defaults)."""
     o = mk_default_opts()
     o.levels = levels
@@ -96,6 +96,7 @@ def make_opts(levels: int = 3, nu: Sequence[int] = (), space: Sequence[bool] = (
         o.mu_mode, o.mu_value = 2, float(mu)
     o.use_graph = 1 if use_graph else 0
     o.orth = int(orth)
+    o.autotune = 1 if autotune else 0
     return o
 
 

@@ -28,7 +28,8 @@ class mk_solve_opts(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("nu", ctypes.c_int32 * MK_MAX_LEVELS),
                 ("space", ctypes.c_int32 * MK_MAX_LEVELS), ("m_inner", ctypes.c_int32 * MK_MAX_LEVELS),
                 ("n_cgs", ctypes.c_int32), ("mu_mode", ctypes.c_int32), ("mu_value", ctypes.c_double),
-                ("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("orth", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("orth", ctypes.c_int32),
+                ("autotune", ctypes.c_int32)]
 
 
 class mk_solve_info(ctypes.Structure):

@@ -482,6 +482,35 @@ static int df_grid(int64_t len, int64_t per_block) {
     return (int)g;
 }
 
+// u += sum_{i < jf} y_i X_i with FP32 X: y_i split into double-float once per block, each
+// term y_i X_i formed and summed in double-float on the FP32 pipe, one FP64 add per element.
+__global__ void __launch_bounds__(DF_THREADS) k_combine_df(int64_t len, double *__restrict__ u,
+                                                           const float *__restrict__ X,
+                                                           int64_t xstride, KState ks) {
+    __shared__ float2 y[MK_MAX_RESTART];
+    const int jf = ks.flags[1];
+    if (jf <= 0 || ks.flags[3]) return;
+    for (int i = threadIdx.x; i < jf; i += DF_THREADS) y[i] = df_pack(df_from_double(ks.y()[i]));
+    __syncthreads();
+    for (int64_t e = (int64_t)blockIdx.x * DF_THREADS + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * DF_THREADS) {
+        df acc = {0.f, 0.f};
+#pragma unroll 4
+        for (int i = 0; i < jf; ++i) acc = df_add(acc, df_mul_f(df_unpack(y[i]), X[(int64_t)i * xstride + e]));
+        u[e] += df_to_double(acc);
+    }
+}
+
+void launch_combine_df(int64_t len, double *u, const float *X, int64_t xstride, KState ks,
+                       cudaStream_t s) {
+    const double alg_n = prof_alg_n() > 0 ? prof_alg_n() : (double)len;
+    const int grid = df_grid(len, (int64_t)DF_THREADS * 8);
+    prof_begin(s);
+    k_combine_df<<<grid, DF_THREADS, 0, s>>>(len, u, X, xstride, ks);
+    prof_end(s, PROF_COMBINE, (double)alg_n * (16.0 + (double)ks.m * sizeof(float)));
+    count_launch();
+}
+
 void launch_multidot_df(int64_t len, const float2 *W, const float2 *V, int64_t vstride, int j,
                         const ReduceScratch &rs, KState ks, bool second_pass, const int *done,
                         cudaStream_t s) {

@@ -155,6 +155,9 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
                       const float2 *cb, bool has_b, const float2 *v, const double *sigma,
                       const float *Xc, int mc, int64_t xc_stride, const double *yc, float *x,
                       float2 *wout, const int *done, cudaStream_t s);
+// u += sum_{i < jf} y_i X_i for FP32 X in double-float arithmetic (mixed level 1)
+void launch_combine_df(int64_t len, double *u, const float *X, int64_t xstride, KState ks,
+                       cudaStream_t s);
 void launch_multidot_df(int64_t len, const float2 *W, const float2 *V, int64_t vstride, int j,
                         const ReduceScratch &rs, KState ks, bool second_pass, const int *done,
                         cudaStream_t s);

@@ -20,7 +20,8 @@ int64_t launches_total();
 
 bool OptsKey::operator==(const OptsKey &o) const {
     if (levels != o.levels || n_cgs != o.n_cgs || mu_mode != o.mu_mode ||
-        precision != o.precision || restart != o.restart || mu_value != o.mu_value || orth != o.orth)
+        precision != o.precision || restart != o.restart || mu_value != o.mu_value || orth != o.orth ||
+        autotune != o.autotune)
         return false;
     for (int i = 0; i < MK_MAX_LEVELS; ++i)
         if (nu[i] != o.nu[i] || space[i] != o.space[i] || m_inner[i] != o.m_inner[i]) return false;
@@ -36,6 +37,7 @@ static OptsKey make_key(const mk_solve_opts &o) {
     k.precision = o.precision;
     k.restart = o.restart;
     k.orth = o.orth;
+    k.autotune = o.autotune ? 1 : 0;
     k.mu_value = o.mu_mode == 2 ? o.mu_value : 0.0;
     for (int i = 0; i < o.levels - 1 && i < MK_MAX_LEVELS; ++i) {
         k.nu[i] = o.nu[i];
@@ -211,6 +213,11 @@ mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out) {
     std::unique_ptr<Hierarchy> H;
     mk_status st = build_hierarchy_new(P, o, H);
     if (st != MK_OK) return st;
+    if (o.autotune) {
+        st = autotune_hierarchy(*H, nullptr);
+        if (st != MK_OK) return st;
+        MKCK(cudaStreamSynchronize(nullptr));
+    }
     P.H = std::move(H);
     out = P.H.get();
     return MK_OK;
@@ -479,7 +486,7 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s) {
         launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), V, H.rs, 0, L.ks,
                         EPI_OUTER_START, s);
     } else {
-        launch_combine<float>(len, H.u.as<double>(), L.X.as<float>(), L.stride, L.ks, s);
+        launch_combine_df(len, H.u.as<double>(), L.X.as<float>(), L.stride, L.ks, s);
         launch_residual_df(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), Vd, H.rs, 0, L.ks,
                            EPI_OUTER_START, s);
     }

@@ -31,7 +31,7 @@ struct DevMem {
 };
 
 struct OptsKey {
-    int levels, n_cgs, mu_mode, precision, restart, orth;
+    int levels, n_cgs, mu_mode, precision, restart, orth, autotune;
     int nu[MK_MAX_LEVELS], space[MK_MAX_LEVELS], m_inner[MK_MAX_LEVELS];
     double mu_value;
     bool operator==(const OptsKey &o) const;
