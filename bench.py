@@ -140,6 +140,35 @@ def run_reference(args, world, rank):
 DRAM_TRAFFIC_RATIO = {"multidot@level1": 1.0026, "update@level1": 0.9979}
 
 
+def bench_2d(mk, torch, dev, args, steps=2):
+    """The 2D workload: 255 x 255 interior points, theta = 1/2, n_t = 1024, T = 0.05, mixed
+    precision, 4 levels nu = 2 with 2 x 2 agglomeration per coarsening (66.7 M space-time
+    points).  Its error against the oracle is checked on sampled steps by the parity tests
+    (a full CPU march of this size takes tens of seconds)."""
+    P = W.heat2d_large()
+    s = P.schedule
+    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=s.n_cgs,
+                     tol=args.tol, restart=args.restart, precision="mixed", orth=args.orth,
+                     autotune=not args.no_autotune)
+    u0 = torch.from_numpy(P.u0).to(dev)
+    u = torch.empty((P.nt + 1,) + P.space_shape(), dtype=torch.float64, device=dev)
+    with mk.Problem(P.dim, P.nx, P.tau, P.theta, P.dt, P.nt, None, ny=P.ny) as p:
+        mk.mk_solve(p.handle, u0, u, o)
+        ts, info = [], None
+        for _ in range(steps):
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = mk.mk_solve(p.handle, u0, u, o)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+    return {"s": statistics.mean(ts), "iterations": int(info.iterations),
+            "rel_residual": info.rel_residual, "points": int(P.nx * P.ny * (P.nt + 1)),
+            "workload": "heat2d_255x255_nt1024_theta0.5_T0.05_L4_nu2_2x2space", "tol": args.tol}
+
+
 def bench_batch(mk, torch, dev, count_1d=12, count_2d=4, max_iters=600):
     """16 members of the uneven batched workload (1D n 63..2047 x n_t 256..8192, 2D side
     63..255 x n_t 128..1024, tau log-uniform [0.1, 10], theta in {1/2, 1}; mixed, tol 1e-10):
@@ -313,8 +342,14 @@ def main():
                 tm.append(e0.elapsed_time(e1))
         u_march = u_dev.cpu().numpy().copy()
 
-        # ---------------- batched uneven problems ----------------
+        # ---------------- 2D workload (255 x 255, n_t = 1024, 4 levels with 2 x 2 agglomeration) ----
         line["paths"] = {}
+        try:
+            line["paths"]["mk_mixed_2d"] = bench_2d(mk, torch, dev, args)
+        except Exception as e:
+            line["paths"]["mk_mixed_2d"] = {"error": str(e)[:200]}
+
+        # ---------------- batched uneven problems ----------------
         try:
             line["paths"]["mk_batch"] = bench_batch(mk, torch, dev)
         except Exception as e:   # reported, not fatal: the headline does not depend on it

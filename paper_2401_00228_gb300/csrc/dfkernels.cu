@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(256) k_interp_df_1d(Geom gf, Geom gc, int nu,
 void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const float2 *ca,
                       const float2 *cb, bool has_b, const float2 *v, const double *sigma,
                       const float *Xc, int mc, int64_t xc_stride, const double *yc, float *x,
-                      float2 *wout, const int *done, cudaStream_t s) {
+                      float2 *wout, const int *done, cudaStream_t s, const float2 *uniform_ab) {
     int kc = choose_kc(gf.npts(), gf.nt + 1);
     int nch = (gf.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(gf.dim, gf.nx, gf.ny, nch);
@@ -309,7 +309,7 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
     } while (0)
     prof_begin(s);
     if (launch_interp_df_1d_tiled(gf, gc, nu, space, ca, cb, has_b, v, sigma, Xc, mc, xc_stride,
-                                  yc, x, wout, done, s)) {
+                                  yc, x, wout, done, s, uniform_ab)) {
         // 1D, nu = 2: time-tiled kernel (transfer1d.cu)
     } else if (gf.dim == 1) {
         if (space) MK_IDF1(true); else MK_IDF1(false);

@@ -145,16 +145,19 @@ bool launch_interp_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space, 
                             SpaceOp<Tc> L, const Tv *v, const double *sigma, const Tz *Xc,
                             int mc, int64_t xc_stride, const double *yc, Tx *x, Tw *wout,
                             const int *done, cudaStream_t s);
+// uniform_ab: nullptr, or the device pair (a c, b c) as double-floats when the level's
+// operator is c tridiag(1, -2, 1) (then ca/cb are not read)
 bool launch_interp_df_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space,
                                const float2 *ca, const float2 *cb, bool has_b, const float2 *v,
                                const double *sigma, const float *Xc, int mc, int64_t xc_stride,
                                const double *yc, float *x, float2 *wout, const int *done,
-                               cudaStream_t s);
+                               cudaStream_t s, const float2 *uniform_ab = nullptr);
 // ca, cb: double-float a*L and b*L coefficient rows, [x: lo|di|up (3 nx) | y: (3 ny)]
 void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const float2 *ca,
                       const float2 *cb, bool has_b, const float2 *v, const double *sigma,
                       const float *Xc, int mc, int64_t xc_stride, const double *yc, float *x,
-                      float2 *wout, const int *done, cudaStream_t s);
+                      float2 *wout, const int *done, cudaStream_t s,
+                      const float2 *uniform_ab = nullptr);
 // u += sum_{i < jf} y_i X_i for FP32 X in double-float arithmetic (mixed level 1)
 void launch_combine_df(int64_t len, double *u, const float *X, int64_t xstride, KState ks,
                        cudaStream_t s);

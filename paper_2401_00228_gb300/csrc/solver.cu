@@ -271,6 +271,12 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
             for (double v : c) t.push_back(df_pack_host(lv->w.b * v));
             MKCK(lv->cdf.alloc(sizeof(float2) * t.size()));
             MKCK(cudaMemcpy(lv->cdf.p, t.data(), sizeof(float2) * t.size(), cudaMemcpyHostToDevice));
+            double cu = 0.0;
+            if (P.dim == 1 && tri_uniform(lv->Lx, cu)) {
+                const float2 u[2] = {df_pack_host(lv->w.a * cu), df_pack_host(lv->w.b * cu)};
+                MKCK(lv->cuni.alloc(sizeof(u)));
+                MKCK(cudaMemcpy(lv->cuni.p, u, sizeof(u), cudaMemcpyHostToDevice));
+            }
         }
         if (st != MK_OK) return st;
         lv->stride = lv->g.len;
@@ -377,7 +383,7 @@ struct InterpStep<float2, float, float, float2, double> {
         const float2 *ca = L.cdf.as<float2>();
         launch_interp_df(L.g, C.g, L.nu, L.space, ca, ca + nc, L.w.b != 0.0, vj, sig, Xc, mc,
                          C.stride, yc, L.X.as<float>() + (int64_t)j * L.stride, L.W.as<float2>(),
-                         done, s);
+                         done, s, L.cuni.p ? L.cuni.as<float2>() : nullptr);
     }
 };
 template <typename Tv, typename Tc, typename Tx, typename Tw, typename Tcw>

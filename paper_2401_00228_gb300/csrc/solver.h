@@ -47,6 +47,7 @@ struct Level {
     bool coarsest = false;
     DevMem c64, c32;   // [3nx | 3ny] coefficients
     DevMem cdf;        // mixed level 1: double-float a*L then b*L, each [3nx | 3ny]
+    DevMem cuni;       // mixed level 1 in 1D with L = c tridiag(1,-2,1): double-float (a c, b c)
     SpaceOp<double> op64{nullptr, nullptr};
     SpaceOp<float> op32{nullptr, nullptr};
     // vectors (level 1: V, W in FP64, X in the cycle precision; others in cycle precision)

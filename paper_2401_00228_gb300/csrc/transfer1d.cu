@@ -327,10 +327,21 @@ __global__ void __launch_bounds__(TT) k_interp_1d_t(Geom gf, Geom gc, Tc a, Tc b
     }
 }
 
+// (x_{i-1} - 2 x_i + x_{i+1}) of FP32 values, exactly, as a double-float (two TwoSums; -2 x_i
+// is exact)
+__device__ __forceinline__ df lap3_exact(float l, float c, float r) {
+    const df s1 = two_sum(l, r);
+    const df s2 = two_sum(s1.hi, -2.f * c);
+    return fast_two_sum(s2.hi, s2.lo + s1.lo);
+}
+
 // Mixed level 1: v is a double-float basis vector (read as its FP32 rounding), x is FP32
 // and w = A x is formed in double-float from double-float coefficient rows a*L and b*L, so
 // the FP32 x enters the FP64-accurate Arnoldi with only the rounding of the product terms.
-template <bool SPACE, int MC, int KC>
+// UNIFORM: L = c tridiag(1, -2, 1) (the fine level), a L x = (a c) (x_{i-1} - 2 x_i + x_{i+1})
+// with the bracket exact and one double-float product (ca[0], cb[0] hold a c and b c);
+// HAS_B = false drops the (I + b L) x_{k-1} stencil (theta = 1).
+template <bool SPACE, int MC, int KC, bool UNIFORM, bool HAS_B>
 __global__ void __launch_bounds__(TT) k_interp_df_1d_t(Geom gf, Geom gc,
                                                        const float2 *__restrict__ ca,
                                                        const float2 *__restrict__ cb, int has_b,
@@ -372,17 +383,27 @@ __global__ void __launch_bounds__(TT) k_interp_df_1d_t(Geom gf, Geom gc,
     CR cr;
     cr.load(gc, Xc, mc, xc_stride, y, k0 / 2, i0, nf, act, lane);
     const df z = {0.f, 0.f};
-    df alo[PT], adi[PT], aup[PT], blo[PT], bdi[PT], bup[PT];
+    (void)has_b;
+    df alo[UNIFORM ? 1 : PT], adi[UNIFORM ? 1 : PT], aup[UNIFORM ? 1 : PT];
+    df blo[UNIFORM || !HAS_B ? 1 : PT], bdi[UNIFORM || !HAS_B ? 1 : PT], bup[UNIFORM || !HAS_B ? 1 : PT];
+    df ac = z, bc = z;
+    if constexpr (UNIFORM) {
+        ac = df_unpack(ca[0]);
+        if constexpr (HAS_B) bc = df_unpack(cb[0]);
+    } else {
 #pragma unroll
-    for (int p = 0; p < PT; ++p) {
-        const int i = i0 + p;
-        const bool in = i < nf;
-        alo[p] = in ? df_unpack(ca[i]) : z;
-        adi[p] = in ? df_unpack(ca[nf + i]) : z;
-        aup[p] = in ? df_unpack(ca[2 * nf + i]) : z;
-        blo[p] = (in && has_b) ? df_unpack(cb[i]) : z;
-        bdi[p] = (in && has_b) ? df_unpack(cb[nf + i]) : z;
-        bup[p] = (in && has_b) ? df_unpack(cb[2 * nf + i]) : z;
+        for (int p = 0; p < PT; ++p) {
+            const int i = i0 + p;
+            const bool in = i < nf;
+            alo[p] = in ? df_unpack(ca[i]) : z;
+            adi[p] = in ? df_unpack(ca[nf + i]) : z;
+            aup[p] = in ? df_unpack(ca[2 * nf + i]) : z;
+            if constexpr (HAS_B) {
+                blo[p] = in ? df_unpack(cb[i]) : z;
+                bdi[p] = in ? df_unpack(cb[nf + i]) : z;
+                bup[p] = in ? df_unpack(cb[2 * nf + i]) : z;
+            }
+        }
     }
     float xp[PT];
     df bLp[PT];
@@ -402,11 +423,21 @@ __global__ void __launch_bounds__(TT) k_interp_df_1d_t(Geom gf, Geom gc,
         for (int p = 0; p < PT; ++p) {
             const float left = p == 0 ? xl : x[p - 1];
             const float right = p == PT - 1 ? xr : x[p + 1];
-            aL[p] = df_add(df_add(df_mul_f(adi[p], x[p]), df_mul_f(alo[p], left)),
-                           df_mul_f(aup[p], right));
-            bL[p] = has_b ? df_add(df_add(df_mul_f(bdi[p], x[p]), df_mul_f(blo[p], left)),
-                                   df_mul_f(bup[p], right))
-                          : z;
+            if constexpr (UNIFORM) {
+                // points beyond n_x have x = 0 and neighbours 0 or x_{n-1}: mask them
+                const df t = lap3_exact(left, x[p], right);
+                const bool in = i0 + p < nf;
+                aL[p] = in ? df_mul(ac, t) : z;
+                bL[p] = (HAS_B && in) ? df_mul(bc, t) : z;
+            } else {
+                aL[p] = df_add(df_add(df_mul_f(adi[p], x[p]), df_mul_f(alo[p], left)),
+                               df_mul_f(aup[p], right));
+                if constexpr (HAS_B)
+                    bL[p] = df_add(df_add(df_mul_f(bdi[p], x[p]), df_mul_f(blo[p], left)),
+                                   df_mul_f(bup[p], right));
+                else
+                    bL[p] = z;
+            }
         }
         if (r > 0 && ok && act) {
             float2 w[PT];
@@ -515,7 +546,7 @@ bool launch_interp_df_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool spac
                                const float2 *ca, const float2 *cb, bool has_b, const float2 *v,
                                const double *sigma, const float *Xc, int mc, int64_t xc_stride,
                                const double *yc, float *x, float2 *wout, const int *done,
-                               cudaStream_t s) {
+                               cudaStream_t s, const float2 *uniform_ab) {
     if (gf.dim != 1 || nu != 2) return false;
     const int xb = (gf.nx + TT * PT - 1) / (TT * PT);
     const int rows = gf.nt + 1;
@@ -523,9 +554,24 @@ bool launch_interp_df_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool spac
     const int kc = (h == 2 || h == 4) ? h : tiled_kc(xb, rows, false);
     const dim3 grid(xb, (rows + kc - 1) / kc);
     const int hb = has_b ? 1 : 0;
+    // uniform fine-level operator: ca[0], cb[0] of the kernel are a c and b c
+    const bool uni = uniform_ab != nullptr;
+    const float2 *ka = uni ? uniform_ab : ca, *kb = uni ? uniform_ab + 1 : cb;
 #define MK_ID(S, M, K)                                                                        \
-    k_interp_df_1d_t<S, M, K><<<grid, TT, 0, s>>>(gf, gc, ca, cb, hb, v, sigma, Xc, mc,        \
-                                                  xc_stride, yc, x, wout, done)
+    do {                                                                                      \
+        if (uni && hb)                                                                        \
+            k_interp_df_1d_t<S, M, K, true, true><<<grid, TT, 0, s>>>(                        \
+                gf, gc, ka, kb, hb, v, sigma, Xc, mc, xc_stride, yc, x, wout, done);          \
+        else if (uni)                                                                         \
+            k_interp_df_1d_t<S, M, K, true, false><<<grid, TT, 0, s>>>(                       \
+                gf, gc, ka, kb, hb, v, sigma, Xc, mc, xc_stride, yc, x, wout, done);          \
+        else if (hb)                                                                          \
+            k_interp_df_1d_t<S, M, K, false, true><<<grid, TT, 0, s>>>(                       \
+                gf, gc, ka, kb, hb, v, sigma, Xc, mc, xc_stride, yc, x, wout, done);          \
+        else                                                                                  \
+            k_interp_df_1d_t<S, M, K, false, false><<<grid, TT, 0, s>>>(                      \
+                gf, gc, ka, kb, hb, v, sigma, Xc, mc, xc_stride, yc, x, wout, done);          \
+    } while (0)
 #define MK_ID_K(S, M) \
     do { if (kc == 4) MK_ID(S, M, 4); else MK_ID(S, M, 2); } while (0)
 #define MK_ID_M(S)                                       \
