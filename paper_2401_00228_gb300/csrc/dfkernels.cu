@@ -131,6 +131,39 @@ __device__ __forceinline__ df lap_df(const float2 *__restrict__ cx, const float2
     return s;
 }
 
+// w = A x in double-float, element-wise in 2D, for FP32 x (32 x 8 x 1 blocks over (i, j, k)):
+// w_0 = x_0, w_k = (x_k - x_{k-1}) - a L x_k - b L x_{k-1} with double-float a L, b L rows.
+__global__ void __launch_bounds__(256) k_apply_df_2d(Geom g, const float2 *__restrict__ ca,
+                                                     const float2 *__restrict__ cb, int has_b,
+                                                     const float *__restrict__ x,
+                                                     float2 *__restrict__ w,
+                                                     const int *__restrict__ done) {
+    if (done && *done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const int64_t idx = g.at(k, j, i);
+    const float c = x[idx];
+    df r;
+    if (k == 0) {
+        r = df_from_float(c);
+    } else {
+        const float2 *cax = ca, *cay = ca + 3 * g.nx;
+        const df aL = lap_df<2>(cax, cay, g.nx, g.ny, i, j, c, x[idx - 1], x[idx + 1],
+                                x[idx - g.ldx], x[idx + g.ldx]);
+        const int64_t ip = idx - g.plane;
+        const float p = x[ip];
+        r = df_sub(df_from_sum(c, -p), aL);
+        if (has_b) {
+            const float2 *cbx = cb, *cby = cb + 3 * g.nx;
+            r = df_sub(r, lap_df<2>(cbx, cby, g.nx, g.ny, i, j, p, x[ip - 1], x[ip + 1],
+                                    x[ip - g.ldx], x[ip + g.ldx]));
+        }
+    }
+    w[idx] = df_pack(r);
+}
+
 template <int DIM, bool SPACE>
 __global__ void __launch_bounds__(256) k_interp_df(Geom gf, Geom gc, int nu,
                                                    const float2 *__restrict__ ca,
@@ -314,7 +347,16 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
     } else if (gf.dim == 1) {
         if (space) MK_IDF1(true); else MK_IDF1(false);
     } else {
-        if (space) MK_IDF(2, true); else MK_IDF(2, false);
+        // 2D: x once per point, then w = A x in double-float from the stored x
+        const dim3 g2 = grid_2d_points(gf), b2(32, 8, 1);
+        if (space)
+            k_interp_x2d<true, float2, float, float><<<g2, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc,
+                                                                      xc_stride, yc, x, done);
+        else
+            k_interp_x2d<false, float2, float, float><<<g2, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc,
+                                                                       xc_stride, yc, x, done);
+        k_apply_df_2d<<<g2, b2, 0, s>>>(gf, ca, cb, hb, x, wout, done);
+        count_launch();
     }
 #undef MK_IDF
 #undef MK_IDF1

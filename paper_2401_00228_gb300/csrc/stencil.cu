@@ -122,6 +122,32 @@ __global__ void __launch_bounds__(256) k_apply(Geom g, Tc a, Tc b, SpaceOp<Tc> L
     }
 }
 
+// w = A x element-wise in 2D (32 x 8 x 1 blocks over (i, j, k)); rows k and k-1 of x are read
+// directly (neighbours from cache).
+template <typename Tin, typename Tout, typename Tc>
+__global__ void __launch_bounds__(256) k_apply_2d(Geom g, Tc a, Tc b, SpaceOp<Tc> L,
+                                                  const Tin *__restrict__ x,
+                                                  Tout *__restrict__ w,
+                                                  const int *__restrict__ done) {
+    if (done && *done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const int64_t idx = g.at(k, j, i);
+    const Tc cur = ldv<Tc>(x, idx);
+    Tc r;
+    if (k == 0) {
+        r = cur;
+    } else {
+        const int64_t ip = idx - g.plane;
+        const Tc Lc = lap_at<2, Tc>(x, idx, i, j, g, L.x, L.y);
+        const Tc Lp = lap_at<2, Tc>(x, ip, i, j, g, L.x, L.y);
+        r = (cur - a * Lc) - (ldv<Tc>(x, ip) + b * Lp);
+    }
+    w[idx] = (Tout)r;
+}
+
 template <typename Tin, typename Tout, typename Tc>
 void launch_apply(const Geom &g, const Weights &w, SpaceOp<Tc> L, const Tin *x, Tout *out,
                   cudaStream_t s) {
@@ -607,7 +633,17 @@ void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Wei
     } else if (gf.dim == 1) {
         if (space) MK_INTERP1(true); else MK_INTERP1(false);
     } else {
-        if (space) MK_INTERP(2, true); else MK_INTERP(2, false);
+        // 2D: x once per point, then w = A x from the stored x (the fused form evaluated x
+        // again at each of the four stencil neighbours of every point)
+        const dim3 g2 = grid_2d_points(gf), b2(32, 8, 1);
+        if (space)
+            k_interp_x2d<true, Tv, Tz, Tx><<<g2, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc, xc_stride,
+                                                            yc, x, done);
+        else
+            k_interp_x2d<false, Tv, Tz, Tx><<<g2, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc,
+                                                             xc_stride, yc, x, done);
+        k_apply_2d<Tx, Tw, Tc><<<g2, b2, 0, s>>>(gf, a, b, L, x, wout, done);
+        count_launch();
     }
 #undef MK_INTERP
 #undef MK_INTERP1

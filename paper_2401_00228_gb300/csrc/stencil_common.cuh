@@ -91,6 +91,42 @@ __device__ __forceinline__ bool point_index(int &i, int &j, int &chunk) {
 }
 
 
+// 2D interpolation + correction, element-wise (one thread per space-time point, 32 x 8 x 1
+// blocks over (i, j, k)):  x_k = sigma v_k - (Z vt)_{K(k)},  K(0) = 0, K(k) = (k-1)/nu + 1,
+// vt = sum_m y_m Xc_m (Xc itself when yc is null); aggregates of Z are 2 x 2 with SPACE.
+// Each x is formed once; w = A x follows in a separate stencil kernel that reads x back.
+template <bool SPACE, typename Tv, typename Tz, typename Tx>
+__global__ void __launch_bounds__(256) k_interp_x2d(Geom gf, Geom gc, int nu,
+                                                    const Tv *__restrict__ v,
+                                                    const double *__restrict__ sigma,
+                                                    const Tz *__restrict__ Xc, int mc,
+                                                    int64_t xc_stride,
+                                                    const double *__restrict__ yc,
+                                                    Tx *__restrict__ x,
+                                                    const int *__restrict__ done) {
+    if (done && *done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= gf.nx || j >= gf.ny) return;
+    const int K = (k == 0) ? 0 : (k - 1) / nu + 1;
+    const int64_t ci = gc.at(K, SPACE ? (j >> 1) : j, SPACE ? (i >> 1) : i);
+    Tx zt;
+    if (!yc) {
+        zt = (Tx)Xc[ci];
+    } else {
+        zt = (Tx)0;
+        for (int m = 0; m < mc; ++m) zt += (Tx)yc[m] * (Tx)Xc[ci + m * xc_stride];
+    }
+    const Tx sig = sigma ? (Tx)(*sigma) : (Tx)1;
+    const int64_t idx = gf.at(k, j, i);
+    x[idx] = sig * ldv<Tx>(v, idx) - zt;
+}
+
+inline dim3 grid_2d_points(const Geom &g) {
+    return dim3((g.nx + 31) / 32, (g.ny + 7) / 8, g.nt + 1);
+}
+
 static inline int grid_for(int64_t n, int block) {
     int64_t g = (n + block - 1) / block;
     int64_t cap = (int64_t)g_num_sms * 16;
