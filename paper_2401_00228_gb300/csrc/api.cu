@@ -747,8 +747,12 @@ static mk_status op_coarsest_t(Hierarchy &H, const double *dr, double *dx, cudaS
         CK(up(sy, Sy1));
         CK(up(syi, Syi1));
         CK(up(ly, ly1));
-        launch_slab_2d<T>(C.g, C.w.a, C.w.b, op, sx.as<T>(), sxi.as<T>(), lx.as<T>(), sy.as<T>(),
-                          syi.as<T>(), ly.as<T>(), H.key.n_cgs, rp.as<T>(), xp.as<T>(), nullptr, s);
+        DevMem rh;
+        CK(rh.alloc(sizeof(T) * (size_t)(C.g.nt + 1) * C.g.nx * C.g.ny));
+        launch_slab_2d_fdm<T>(C.g, C.w.a, C.w.b, sx.as<T>(), sxi.as<T>(), lx.as<T>(), sy.as<T>(),
+                              syi.as<T>(), ly.as<T>(), H.key.n_cgs, rh.as<T>(), rp.as<T>(),
+                              xp.as<T>(), nullptr, s);
+        CK(cudaStreamSynchronize(s));   // rh is released at the end of this scope
     }
     launch_unpack<T, double>(C.g, xp.as<T>(), dx, s);
     CK(cudaGetLastError());

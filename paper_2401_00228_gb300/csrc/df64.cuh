@@ -69,6 +69,13 @@ __device__ __forceinline__ df df_from_sum(float a, float b) { return two_sum(a, 
 
 __device__ __forceinline__ df df_from_float(float a) { return {a, 0.f}; }
 
+// (l - 2 c + r) of three floats, exactly, as a double-float (two TwoSums; -2 c is exact)
+__device__ __forceinline__ df lap3_exact(float l, float c, float r) {
+    const df s1 = two_sum(l, r);
+    const df s2 = two_sum(s1.hi, -2.f * c);
+    return fast_two_sum(s2.hi, s2.lo + s1.lo);
+}
+
 __host__ __device__ __forceinline__ float2 df_pack(df x) { return make_float2(x.hi, x.lo); }
 __host__ __device__ __forceinline__ df df_unpack(float2 v) { return {v.x, v.y}; }
 

@@ -164,6 +164,39 @@ __global__ void __launch_bounds__(256) k_apply_df_2d(Geom g, const float2 *__res
     w[idx] = df_pack(r);
 }
 
+// The same for L = cx tridiag_x(1,-2,1) (+) cy tridiag_y(1,-2,1) (the fine level): each bracket
+// exact, one double-float product per direction.  u = [a cx, b cx, a cy, b cy].
+template <bool HAS_B>
+__global__ void __launch_bounds__(256) k_apply_df_2d_uni(Geom g, const float2 *__restrict__ u,
+                                                         const float *__restrict__ x,
+                                                         float2 *__restrict__ w,
+                                                         const int *__restrict__ done) {
+    if (done && *done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const int64_t idx = g.at(k, j, i);
+    const float c = x[idx];
+    df r;
+    if (k == 0) {
+        r = df_from_float(c);
+    } else {
+        const df acx = df_unpack(u[0]), acy = df_unpack(u[2]);
+        const df aL = df_add(df_mul(acx, lap3_exact(x[idx - 1], c, x[idx + 1])),
+                             df_mul(acy, lap3_exact(x[idx - g.ldx], c, x[idx + g.ldx])));
+        const int64_t ip = idx - g.plane;
+        const float p = x[ip];
+        r = df_sub(df_from_sum(c, -p), aL);
+        if (HAS_B) {
+            const df bcx = df_unpack(u[1]), bcy = df_unpack(u[3]);
+            r = df_sub(r, df_add(df_mul(bcx, lap3_exact(x[ip - 1], p, x[ip + 1])),
+                                 df_mul(bcy, lap3_exact(x[ip - g.ldx], p, x[ip + g.ldx]))));
+        }
+    }
+    w[idx] = df_pack(r);
+}
+
 template <int DIM, bool SPACE>
 __global__ void __launch_bounds__(256) k_interp_df(Geom gf, Geom gc, int nu,
                                                    const float2 *__restrict__ ca,
@@ -355,7 +388,9 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
         else
             k_interp_x2d<false, float2, float, float><<<g2, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc,
                                                                        xc_stride, yc, x, done);
-        k_apply_df_2d<<<g2, b2, 0, s>>>(gf, ca, cb, hb, x, wout, done);
+        if (uniform_ab && hb) k_apply_df_2d_uni<true><<<g2, b2, 0, s>>>(gf, uniform_ab, x, wout, done);
+        else if (uniform_ab) k_apply_df_2d_uni<false><<<g2, b2, 0, s>>>(gf, uniform_ab, x, wout, done);
+        else k_apply_df_2d<<<g2, b2, 0, s>>>(gf, ca, cb, hb, x, wout, done);
         count_launch();
     }
 #undef MK_IDF

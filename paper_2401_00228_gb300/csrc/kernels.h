@@ -117,6 +117,14 @@ void launch_lsq(int j, double *H, double beta, double *gg, double *y, double *re
 void launch_residual_df(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
                         const double *u, float2 *r, const ReduceScratch &rs, int slot, KState ks,
                         int epi, cudaStream_t s);
+// 2D coarsest slabs in the eigenbasis of Lx (+) Ly, all time rows at once (slab.cu): forward
+// transform of every row, per-mode recurrence over each slab, inverse transform.  rh: scratch of
+// (nt+1) nx ny values.  Three launches.
+template <typename T>
+void launch_slab_2d_fdm(const Geom &g, double a, double b, const T *Sx, const T *Sxi,
+                        const T *lamx, const T *Sy, const T *Syi, const T *lamy, int n_cgs,
+                        T *rh, const T *r, T *x, const int *done, cudaStream_t s);
+
 // Coarsest decoupled slabs by sine-transform diagonalisation (slab_dst.cu), FP32, for a
 // uniform 1D operator.  dst_transform_size(n) = 2(n+1) when that is a power of two <= 4096,
 // else 0 (not supported).  tab = [alpha (n) | beta (n)], tw = FFT twiddle table,
@@ -145,8 +153,8 @@ bool launch_interp_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space, 
                             SpaceOp<Tc> L, const Tv *v, const double *sigma, const Tz *Xc,
                             int mc, int64_t xc_stride, const double *yc, Tx *x, Tw *wout,
                             const int *done, cudaStream_t s);
-// uniform_ab: nullptr, or the device pair (a c, b c) as double-floats when the level's
-// operator is c tridiag(1, -2, 1) (then ca/cb are not read)
+// uniform_ab: nullptr, or the device values (a cx, b cx, a cy, b cy) as double-floats when the
+// level's operator is cx tridiag(1, -2, 1) (+) cy tridiag(1, -2, 1) (then ca/cb are not read)
 bool launch_interp_df_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space,
                                const float2 *ca, const float2 *cb, bool has_b, const float2 *v,
                                const double *sigma, const float *Xc, int mc, int64_t xc_stride,

@@ -379,6 +379,157 @@ bool slab_warp_supported(int n) {
     return U > 0;
 }
 
+// ---------------------------------------------------------------------------------------
+// 2D slabs in the eigenbasis, all time rows at once.  With L = Lx (+) Ly and
+// Lx = Sx diag(lamx) Sx^{-1}, Ly = Sy diag(lamy) Sy^{-1}, every mode m = (j, i) of a slab follows
+//     xh_k = alpha_m xh_{k-1} + beta_m rh_k,  beta_m = 1/(1 - a lam_m), alpha_m = (1 + b lam_m) beta_m,
+// lam_m = lamy_j + lamx_i, xh = 0 before the slab's first step (x_0 = r_0 before step 1 when the
+// coupling is kept), where rh_k = Sy^{-1} R_k Sx^{-T} and X_k = Sy Xh_k Sx^T.  Three launches:
+// forward transform of every row, recurrence per (mode, slab) in place, inverse transform.
+// ---------------------------------------------------------------------------------------
+constexpr int FDM_THREADS = 256;
+
+template <typename T>
+__device__ __forceinline__ void fdm_product(const T *__restrict__ Mleft, const T *__restrict__ Mright_t,
+                                            T *__restrict__ A, T *__restrict__ B, int nx, int ny) {
+    // B = Mleft A (ny x ny times ny x nx), then A = B Mright_t^T (Mright_t is nx x nx, row-major)
+    const int nxy = nx * ny;
+    for (int e = threadIdx.x; e < nxy; e += FDM_THREADS) {
+        const int j = e / nx, i = e - j * nx;
+        T acc = 0;
+        for (int q = 0; q < ny; ++q) acc += Mleft[j * ny + q] * A[q * nx + i];
+        B[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nxy; e += FDM_THREADS) {
+        const int j = e / nx, i = e - j * nx;
+        T acc = 0;
+        for (int q = 0; q < nx; ++q) acc += B[j * nx + q] * Mright_t[i * nx + q];
+        A[e] = acc;
+    }
+    __syncthreads();
+}
+
+// rh[k] = Sy^{-1} R_k Sx^{-T} for k = k0 .. nt (one block per row)
+template <typename T>
+__global__ void __launch_bounds__(FDM_THREADS) k_fdm_forward(Geom g, const T *__restrict__ Sxi_g,
+                                                             const T *__restrict__ Syi_g,
+                                                             const T *__restrict__ r, T *__restrict__ rh,
+                                                             int k0, const int *__restrict__ done) {
+    if (done && *done) return;
+    extern __shared__ unsigned char smem_raw[];
+    const int nx = g.nx, ny = g.ny, nxy = nx * ny;
+    T *Sxi = reinterpret_cast<T *>(smem_raw);
+    T *Syi = Sxi + nx * nx;
+    T *A = Syi + ny * ny;
+    T *B = A + nxy;
+    const int k = k0 + blockIdx.x;
+    for (int e = threadIdx.x; e < nx * nx; e += FDM_THREADS) Sxi[e] = Sxi_g[e];
+    for (int e = threadIdx.x; e < ny * ny; e += FDM_THREADS) Syi[e] = Syi_g[e];
+    for (int e = threadIdx.x; e < nxy; e += FDM_THREADS) {
+        const int j = e / nx, i = e - j * nx;
+        A[e] = r[g.at(k, j, i)];
+    }
+    __syncthreads();
+    fdm_product(Syi, Sxi, A, B, nx, ny);
+    T *out = rh + (int64_t)k * nxy;
+    for (int e = threadIdx.x; e < nxy; e += FDM_THREADS) out[e] = A[e];
+}
+
+// in place on rh: the scalar recurrence of every mode over every slab (thread = (mode, slab))
+template <typename T>
+__global__ void __launch_bounds__(FDM_THREADS) k_fdm_recurrence(int nx, int ny, T a, T b,
+                                                                const T *__restrict__ lamx,
+                                                                const T *__restrict__ lamy,
+                                                                T *__restrict__ rh, int steps,
+                                                                int coupled,
+                                                                const int *__restrict__ done) {
+    if (done && *done) return;
+    const int nxy = nx * ny;
+    const int m = blockIdx.x * FDM_THREADS + threadIdx.x;
+    if (m >= nxy) return;
+    const int j = m / nx, i = m - j * nx;
+    const T lam = lamy[j] + lamx[i];
+    const T beta = (T)1 / ((T)1 - a * lam);
+    const T alpha = ((T)1 + b * lam) * beta;
+    const int s0 = 1 + blockIdx.y * steps;
+    T acc = coupled ? rh[m] : (T)0;   // coupled: x_0 = r_0, so xh_0 = rh_0
+    T *p = rh + (int64_t)s0 * nxy + m;
+    for (int q = 0; q < steps; ++q) {
+        acc = alpha * acc + beta * p[(int64_t)q * nxy];
+        p[(int64_t)q * nxy] = acc;
+    }
+}
+
+// X_k = Sy Xh_k Sx^T into the padded layout (k >= 1); block 0 copies x_0 = r_0
+template <typename T>
+__global__ void __launch_bounds__(FDM_THREADS) k_fdm_inverse(Geom g, const T *__restrict__ Sx_g,
+                                                             const T *__restrict__ Sy_g,
+                                                             const T *__restrict__ r,
+                                                             const T *__restrict__ xh,
+                                                             T *__restrict__ x,
+                                                             const int *__restrict__ done) {
+    if (done && *done) return;
+    extern __shared__ unsigned char smem_raw[];
+    const int nx = g.nx, ny = g.ny, nxy = nx * ny;
+    const int k = blockIdx.x;
+    if (k == 0) {
+        for (int e = threadIdx.x; e < nxy; e += FDM_THREADS) {
+            const int j = e / nx, i = e - j * nx;
+            x[g.at(0, j, i)] = r[g.at(0, j, i)];
+        }
+        return;
+    }
+    T *Sx = reinterpret_cast<T *>(smem_raw);
+    T *Sy = Sx + nx * nx;
+    T *A = Sy + ny * ny;
+    T *B = A + nxy;
+    for (int e = threadIdx.x; e < nx * nx; e += FDM_THREADS) Sx[e] = Sx_g[e];
+    for (int e = threadIdx.x; e < ny * ny; e += FDM_THREADS) Sy[e] = Sy_g[e];
+    const T *in = xh + (int64_t)k * nxy;
+    for (int e = threadIdx.x; e < nxy; e += FDM_THREADS) A[e] = in[e];
+    __syncthreads();
+    fdm_product(Sy, Sx, A, B, nx, ny);
+    for (int e = threadIdx.x; e < nxy; e += FDM_THREADS) {
+        const int j = e / nx, i = e - j * nx;
+        x[g.at(k, j, i)] = A[e];
+    }
+}
+
+template <typename T>
+size_t fdm_smem_bytes(int nx, int ny) {
+    return sizeof(T) * ((size_t)nx * nx + (size_t)ny * ny + 2 * (size_t)nx * ny);
+}
+
+template <typename T>
+void launch_slab_2d_fdm(const Geom &g, double a, double b, const T *Sx, const T *Sxi,
+                        const T *lamx, const T *Sy, const T *Syi, const T *lamy, int n_cgs,
+                        T *rh, const T *r, T *x, const int *done, cudaStream_t s) {
+    const int coupled = n_cgs <= 0 ? 1 : 0;
+    const int nslabs = coupled ? 1 : n_cgs;
+    const int steps = coupled ? g.nt : g.nt / n_cgs;
+    const int nxy = g.nx * g.ny;
+    const size_t shm = fdm_smem_bytes<T>(g.nx, g.ny);
+    prof_begin(s);
+    // row 0 is transformed only when the coupling to x_0 is kept
+    const int k0 = coupled ? 0 : 1;
+    k_fdm_forward<T><<<g.nt + 1 - k0, FDM_THREADS, shm, s>>>(g, Sxi, Syi, r, rh, k0, done);
+    k_fdm_recurrence<T><<<dim3((nxy + FDM_THREADS - 1) / FDM_THREADS, nslabs), FDM_THREADS, 0, s>>>(
+        g.nx, g.ny, (T)a, (T)b, lamx, lamy, rh, steps, coupled, done);
+    k_fdm_inverse<T><<<g.nt + 1, FDM_THREADS, shm, s>>>(g, Sx, Sy, r, rh, x, done);
+    prof_end(s, PROF_SLAB, 2.0 * sizeof(T) * (double)g.interior());
+    count_launch(3);
+}
+
+template void launch_slab_2d_fdm<float>(const Geom &, double, double, const float *, const float *,
+                                        const float *, const float *, const float *, const float *,
+                                        int, float *, const float *, float *, const int *,
+                                        cudaStream_t);
+template void launch_slab_2d_fdm<double>(const Geom &, double, double, const double *,
+                                         const double *, const double *, const double *,
+                                         const double *, const double *, int, double *,
+                                         const double *, double *, const int *, cudaStream_t);
+
 template <typename T>
 void launch_slab_1d_warp(const Geom &g, double b, const T *tab, int U, int n_cgs, const T *r, T *x,
                          const int *done, cudaStream_t s, int cls) {
@@ -592,6 +743,10 @@ cudaError_t slab_set_attributes() {
     };
     set((const void *)k_slab_2d<float>);
     set((const void *)k_slab_2d<double>);
+    set((const void *)k_fdm_forward<float>);
+    set((const void *)k_fdm_forward<double>);
+    set((const void *)k_fdm_inverse<float>);
+    set((const void *)k_fdm_inverse<double>);
     set((const void *)k_slab_1d<float, 1>);
     set((const void *)k_slab_1d<float, 2>);
     set((const void *)k_slab_1d<float, 4>);

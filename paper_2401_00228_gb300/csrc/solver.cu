@@ -184,6 +184,8 @@ static mk_status build_coarsest_tables(Level &C, int dim, bool fp64, int n_cgs) 
         std::vector<double> lx, Sx, Sxi, ly, Sy, Syi;
         tri_eigen(C.Lx, lx, Sx, Sxi);
         tri_eigen(C.Ly, ly, Sy, Syi);
+        MKCK(C.fdmbuf.alloc((fp64 ? sizeof(double) : sizeof(float)) * (size_t)(C.g.nt + 1) *
+                            C.g.nx * C.g.ny));
         if (fp64) {
             MKCK(upload<double>(C.Sx, Sx));
             MKCK(upload<double>(C.Sxi, Sxi));
@@ -271,9 +273,11 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
             for (double v : c) t.push_back(df_pack_host(lv->w.b * v));
             MKCK(lv->cdf.alloc(sizeof(float2) * t.size()));
             MKCK(cudaMemcpy(lv->cdf.p, t.data(), sizeof(float2) * t.size(), cudaMemcpyHostToDevice));
-            double cu = 0.0;
-            if (P.dim == 1 && tri_uniform(lv->Lx, cu)) {
-                const float2 u[2] = {df_pack_host(lv->w.a * cu), df_pack_host(lv->w.b * cu)};
+            // uniform operator: (a cx, b cx, a cy, b cy) for the exact-stencil kernels
+            double cx = 0.0, cy = 0.0;
+            if (tri_uniform(lv->Lx, cx) && (P.dim == 1 || tri_uniform(lv->Ly, cy))) {
+                const float2 u[4] = {df_pack_host(lv->w.a * cx), df_pack_host(lv->w.b * cx),
+                                     df_pack_host(lv->w.a * cy), df_pack_host(lv->w.b * cy)};
                 MKCK(lv->cuni.alloc(sizeof(u)));
                 MKCK(cudaMemcpy(lv->cuni.p, u, sizeof(u), cudaMemcpyHostToDevice));
             }
@@ -340,9 +344,9 @@ void enqueue_coarsest_t(Hierarchy &H, const int *done, cudaStream_t s) {
                            C.binv.as<Tc>(), C.npad, C.nlev, H.key.n_cgs, C.R.as<Tc>(), C.X.as<Tc>(),
                            done, s);
     else
-        launch_slab_2d<Tc>(C.g, C.w.a, C.w.b, op_of<Tc>(C), C.Sx.as<Tc>(), C.Sxi.as<Tc>(),
-                           C.lamx.as<Tc>(), C.Sy.as<Tc>(), C.Syi.as<Tc>(), C.lamy.as<Tc>(),
-                           H.key.n_cgs, C.R.as<Tc>(), C.X.as<Tc>(), done, s);
+        launch_slab_2d_fdm<Tc>(C.g, C.w.a, C.w.b, C.Sx.as<Tc>(), C.Sxi.as<Tc>(), C.lamx.as<Tc>(),
+                               C.Sy.as<Tc>(), C.Syi.as<Tc>(), C.lamy.as<Tc>(), H.key.n_cgs,
+                               C.fdmbuf.as<Tc>(), C.R.as<Tc>(), C.X.as<Tc>(), done, s);
 }
 
 void enqueue_coarsest(Hierarchy &H, const int *done, cudaStream_t s) {

@@ -47,7 +47,7 @@ struct Level {
     bool coarsest = false;
     DevMem c64, c32;   // [3nx | 3ny] coefficients
     DevMem cdf;        // mixed level 1: double-float a*L then b*L, each [3nx | 3ny]
-    DevMem cuni;       // mixed level 1 in 1D with L = c tridiag(1,-2,1): double-float (a c, b c)
+    DevMem cuni;       // mixed level 1 with uniform L: double-float (a cx, b cx, a cy, b cy)
     SpaceOp<double> op64{nullptr, nullptr};
     SpaceOp<float> op32{nullptr, nullptr};
     // vectors (level 1: V, W in FP64, X in the cycle precision; others in cycle precision)
@@ -68,6 +68,7 @@ struct Level {
     // on this level, and the coarsest solver (1 sine transform, 2 partitioned, 3 PCR)
     int kc_r = 0, kc_i = 0, coarse_kind = 0, coarse_kind_best = 0;
     DevMem Sx, Sxi, lamx, Sy, Syi, lamy;
+    DevMem fdmbuf;     // 2D coarsest: transformed rows, (nt+1) nx ny in the cycle precision
 };
 
 struct Hierarchy {

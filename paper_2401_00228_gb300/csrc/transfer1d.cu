@@ -327,14 +327,6 @@ __global__ void __launch_bounds__(TT) k_interp_1d_t(Geom gf, Geom gc, Tc a, Tc b
     }
 }
 
-// (x_{i-1} - 2 x_i + x_{i+1}) of FP32 values, exactly, as a double-float (two TwoSums; -2 x_i
-// is exact)
-__device__ __forceinline__ df lap3_exact(float l, float c, float r) {
-    const df s1 = two_sum(l, r);
-    const df s2 = two_sum(s1.hi, -2.f * c);
-    return fast_two_sum(s2.hi, s2.lo + s1.lo);
-}
-
 // Mixed level 1: v is a double-float basis vector (read as its FP32 rounding), x is FP32
 // and w = A x is formed in double-float from double-float coefficient rows a*L and b*L, so
 // the FP32 x enters the FP64-accurate Arnoldi with only the rounding of the product terms.
