@@ -381,12 +381,12 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
         if (space) MK_IDF1(true); else MK_IDF1(false);
     } else {
         // 2D: x once per point, then w = A x in double-float from the stored x
-        const dim3 g2 = grid_2d_points(gf), b2(32, 8, 1);
+        const dim3 g2 = grid_2d_points(gf), g4 = grid_2d_points4(gf), b2(32, 8, 1);
         if (space)
-            k_interp_x2d<true, float2, float, float><<<g2, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc,
+            k_interp_x2d<true, float2, float, float><<<g4, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc,
                                                                       xc_stride, yc, x, done);
         else
-            k_interp_x2d<false, float2, float, float><<<g2, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc,
+            k_interp_x2d<false, float2, float, float><<<g4, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc,
                                                                        xc_stride, yc, x, done);
         if (uniform_ab && hb) k_apply_df_2d_uni<true><<<g2, b2, 0, s>>>(gf, uniform_ab, x, wout, done);
         else if (uniform_ab) k_apply_df_2d_uni<false><<<g2, b2, 0, s>>>(gf, uniform_ab, x, wout, done);
@@ -581,9 +581,11 @@ __global__ void __launch_bounds__(DF_THREADS) k_combine_df(int64_t len, double *
 void launch_combine_df(int64_t len, double *u, const float *X, int64_t xstride, KState ks,
                        cudaStream_t s) {
     const double alg_n = prof_alg_n() > 0 ? prof_alg_n() : (double)len;
-    const int grid = df_grid(len, (int64_t)DF_THREADS * 8);
+    // one element per thread: each element is a dependent chain of jf double-float terms, so
+    // independent chains (threads), not a grid-stride loop, hide its latency
+    const int64_t grid = (len + DF_THREADS - 1) / DF_THREADS;
     prof_begin(s);
-    k_combine_df<<<grid, DF_THREADS, 0, s>>>(len, u, X, xstride, ks);
+    k_combine_df<<<(unsigned)grid, DF_THREADS, 0, s>>>(len, u, X, xstride, ks);
     prof_end(s, PROF_COMBINE, (double)alg_n * (16.0 + (double)ks.m * sizeof(float)));
     count_launch();
 }

@@ -635,12 +635,12 @@ void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Wei
     } else {
         // 2D: x once per point, then w = A x from the stored x (the fused form evaluated x
         // again at each of the four stencil neighbours of every point)
-        const dim3 g2 = grid_2d_points(gf), b2(32, 8, 1);
+        const dim3 g2 = grid_2d_points(gf), g4 = grid_2d_points4(gf), b2(32, 8, 1);
         if (space)
-            k_interp_x2d<true, Tv, Tz, Tx><<<g2, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc, xc_stride,
+            k_interp_x2d<true, Tv, Tz, Tx><<<g4, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc, xc_stride,
                                                             yc, x, done);
         else
-            k_interp_x2d<false, Tv, Tz, Tx><<<g2, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc,
+            k_interp_x2d<false, Tv, Tz, Tx><<<g4, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc,
                                                              xc_stride, yc, x, done);
         k_apply_2d<Tx, Tw, Tc><<<g2, b2, 0, s>>>(gf, a, b, L, x, wout, done);
         count_launch();

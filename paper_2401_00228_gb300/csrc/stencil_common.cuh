@@ -91,10 +91,18 @@ __device__ __forceinline__ bool point_index(int &i, int &j, int &chunk) {
 }
 
 
-// 2D interpolation + correction, element-wise (one thread per space-time point, 32 x 8 x 1
-// blocks over (i, j, k)):  x_k = sigma v_k - (Z vt)_{K(k)},  K(0) = 0, K(k) = (k-1)/nu + 1,
-// vt = sum_m y_m Xc_m (Xc itself when yc is null); aggregates of Z are 2 x 2 with SPACE.
-// Each x is formed once; w = A x follows in a separate stencil kernel that reads x back.
+// 2D interpolation + correction, element-wise: x_k = sigma v_k - (Z vt)_{K(k)}, K(0) = 0,
+// K(k) = (k-1)/nu + 1, vt = sum_m y_m Xc_m (Xc itself when yc is null); aggregates of Z are
+// 2 x 2 with SPACE.  A thread takes four consecutive points of one row (16-byte stores of x,
+// 16-byte loads of v); blocks are 32 x 8 threads over (i / 4, j), blockIdx.z = k.  Each x is
+// formed once; w = A x follows in a separate stencil kernel that reads x back.  A row holds
+// ldx >= nx + 1 elements with ldx a multiple of 8, so the four points of a thread whose first
+// point is interior stay inside the row (points beyond nx are written as 0, the padding).
+template <typename Tv, typename Tx>
+__device__ __forceinline__ Tx x2d_vload(const Tv *p) { return (Tx)*p; }
+template <>
+__device__ __forceinline__ float x2d_vload<float2, float>(const float2 *p) { return p->x; }
+
 template <bool SPACE, typename Tv, typename Tz, typename Tx>
 __global__ void __launch_bounds__(256) k_interp_x2d(Geom gf, Geom gc, int nu,
                                                     const Tv *__restrict__ v,
@@ -105,26 +113,40 @@ __global__ void __launch_bounds__(256) k_interp_x2d(Geom gf, Geom gc, int nu,
                                                     Tx *__restrict__ x,
                                                     const int *__restrict__ done) {
     if (done && *done) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
-    if (i >= gf.nx || j >= gf.ny) return;
+    if (i0 >= gf.nx || j >= gf.ny) return;
     const int K = (k == 0) ? 0 : (k - 1) / nu + 1;
-    const int64_t ci = gc.at(K, SPACE ? (j >> 1) : j, SPACE ? (i >> 1) : i);
-    Tx zt;
-    if (!yc) {
-        zt = (Tx)Xc[ci];
-    } else {
-        zt = (Tx)0;
-        for (int m = 0; m < mc; ++m) zt += (Tx)yc[m] * (Tx)Xc[ci + m * xc_stride];
-    }
+    const int J = SPACE ? (j >> 1) : j;
+    const Tz *crow = Xc + gc.at(K, J, 0);
     const Tx sig = sigma ? (Tx)(*sigma) : (Tx)1;
-    const int64_t idx = gf.at(k, j, i);
-    x[idx] = sig * ldv<Tx>(v, idx) - zt;
+    const int64_t idx = gf.at(k, j, i0);
+    Tx out[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int i = i0 + p;
+        const int I = SPACE ? (i >> 1) : i;
+        Tx zt = (Tx)0;
+        if (i < gf.nx) {
+            if (!yc) {
+                zt = (Tx)crow[I];
+            } else {
+                for (int m = 0; m < mc; ++m) zt += (Tx)yc[m] * (Tx)crow[I + m * xc_stride];
+            }
+        }
+        out[p] = (i < gf.nx) ? sig * x2d_vload<Tv, Tx>(v + idx + p) - zt : (Tx)0;
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) x[idx + p] = out[p];
 }
 
+// one point per thread (32 x 8 blocks) / four points per thread (k_interp_x2d)
 inline dim3 grid_2d_points(const Geom &g) {
     return dim3((g.nx + 31) / 32, (g.ny + 7) / 8, g.nt + 1);
+}
+inline dim3 grid_2d_points4(const Geom &g) {
+    return dim3((g.nx + 127) / 128, (g.ny + 7) / 8, g.nt + 1);
 }
 
 static inline int grid_for(int64_t n, int block) {
