@@ -164,7 +164,22 @@ def bench_2d(mk, torch, dev, args, steps=2):
             e1.record()
             e1.synchronize()
             ts.append(e0.elapsed_time(e1) / 1e3)
+        # the sequential theta-march on the GPU (one sine-transform solve per step)
+        um = torch.empty_like(u)
+        mk.mk_march(p.handle, u0, um)
+        tm = []
+        for _ in range(steps):
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mk.mk_march(p.handle, u0, um)
+            e1.record()
+            e1.synchronize()
+            tm.append(e0.elapsed_time(e1) / 1e3)
+        march_err = float(((um - u).abs().max() / um.abs().max()).item())
     return {"s": statistics.mean(ts), "iterations": int(info.iterations),
+            "march_gpu_s": statistics.mean(tm), "max_rel_diff_vs_march": march_err,
             "rel_residual": info.rel_residual, "points": int(P.nx * P.ny * (P.nt + 1)),
             "workload": "heat2d_255x255_nt1024_theta0.5_T0.05_L4_nu2_2x2space", "tol": args.tol}
 

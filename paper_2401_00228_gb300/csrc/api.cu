@@ -92,6 +92,7 @@ static mk_status ensure_device() {
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CK(slab_set_attributes());
     CK(dst_set_attributes());
+    CK(march2d_set_attributes());
     g_num_sms = sms > 0 ? sms : 1;
     return MK_OK;
 }
@@ -367,7 +368,14 @@ mk_status mk_march(mk_problem *p, const double *u0, double *u_out, void *stream)
         launch_march_1d(P.g, b, op, P.m_alpha.as<double>(), P.m_gamma.as<double>(),
                         P.m_binv.as<double>(), P.m_npad, P.m_nlev, fbuf.as<double>(),
                         ubuf.as<double>(), s);
-    else
+    else if (P.m_dst2d) {
+        // u_0 = f_0 (guard and plane 0), then the steps
+        CK(cudaMemcpyAsync(ubuf.p, fbuf.p, sizeof(double) * (size_t)(P.g.guard + P.g.plane),
+                           cudaMemcpyDeviceToDevice, s));
+        launch_march_2d_dst(P.g, a, b, P.m_cx, P.m_cy, P.m_lamx.as<double>(), P.m_lamy.as<double>(),
+                            P.m_twx.as<double2>(), P.m_twy.as<double2>(), fbuf.as<double>(),
+                            ubuf.as<double>(), P.m_t1.as<double>(), s);
+    } else
         launch_march_2d(P.g, a, b, op, P.m_Sx.as<double>(), P.m_Sxi.as<double>(),
                         P.m_lamx.as<double>(), P.m_Sy.as<double>(), P.m_Syi.as<double>(),
                         P.m_lamy.as<double>(), fbuf.as<double>(), ubuf.as<double>(), s);

@@ -125,6 +125,16 @@ void launch_slab_2d_fdm(const Geom &g, double a, double b, const T *Sx, const T 
                         const T *lamx, const T *Sy, const T *Syi, const T *lamy, int n_cgs,
                         T *rh, const T *r, T *x, const int *done, cudaStream_t s);
 
+// Sequential 2D theta-march with a sine-transform solve per step (march2d.cu): FP64, for the
+// uniform fine-level operator, n + 1 a power of two (march2d_transform_size != 0) in both
+// directions.  u's plane 0 must hold u_0; t1 is nx ny doubles of scratch.  3 n_t launches.
+int march2d_transform_size(int n);
+cudaError_t march2d_set_attributes();
+void launch_march_2d_dst(const Geom &g, double a, double b, double cx, double cy,
+                         const double *lamx, const double *lamy, const double2 *twx,
+                         const double2 *twy, const double *f, double *u, double *t1,
+                         cudaStream_t s);
+
 // Coarsest decoupled slabs by sine-transform diagonalisation (slab_dst.cu), FP32, for a
 // uniform 1D operator.  dst_transform_size(n) = 2(n+1) when that is a power of two <= 4096,
 // else 0 (not supported).  tab = [alpha (n) | beta (n)], tw = FFT twiddle table,

@@ -822,6 +822,30 @@ mk_status prepare_march(Problem &P) {
             spike_tables(Lx, a, P.m_spikeU, spike_threads(P.nx), tab);
             MKCK(upload<double>(P.m_spike, tab));
         }
+    } else if (march2d_transform_size(P.nx) && march2d_transform_size(P.ny)) {
+        // uniform fine-level operator: analytic eigenvalues, sine transform per step
+        const double pi = 3.14159265358979323846;
+        double cx = 0.0, cy = 0.0;
+        if (!tri_uniform(Lx, cx) || !tri_uniform(Ly, cy)) return MK_ERR_INVALID;
+        std::vector<double> lx(P.nx), ly(P.ny), tab, twx, twy;
+        for (int i = 0; i < P.nx; ++i) {
+            const double sn = std::sin(pi * (i + 1) / (2.0 * (P.nx + 1)));
+            lx[i] = -4.0 * cx * sn * sn;
+        }
+        for (int j = 0; j < P.ny; ++j) {
+            const double sn = std::sin(pi * (j + 1) / (2.0 * (P.ny + 1)));
+            ly[j] = -4.0 * cy * sn * sn;
+        }
+        dst_tables(P.nx, cx, 0.0, 0.0, tab, twx);
+        dst_tables(P.ny, cy, 0.0, 0.0, tab, twy);
+        MKCK(upload<double>(P.m_lamx, lx));
+        MKCK(upload<double>(P.m_lamy, ly));
+        MKCK(upload<double>(P.m_twx, twx));
+        MKCK(upload<double>(P.m_twy, twy));
+        MKCK(P.m_t1.alloc(sizeof(double) * (size_t)P.nx * P.ny));
+        P.m_cx = cx;
+        P.m_cy = cy;
+        P.m_dst2d = true;
     } else {
         if (P.nx > 48 || P.ny > 48) return MK_ERR_INVALID;
         std::vector<double> lx, Sx, Sxi, ly, Sy, Syi;

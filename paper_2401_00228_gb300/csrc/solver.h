@@ -99,6 +99,10 @@ struct Problem {
     int m_npad = 0, m_nlev = 0;
     DevMem m_spike;
     int m_spikeU = 0;
+    // 2D march by a sine-transform solve per step (n + 1 a power of two)
+    bool m_dst2d = false;
+    double m_cx = 0.0, m_cy = 0.0;
+    DevMem m_twx, m_twy, m_t1;
 };
 
 template <typename T>
