@@ -140,6 +140,34 @@ def run_reference(args, world, rank):
 DRAM_TRAFFIC_RATIO = {"multidot@level1": 1.0026, "update@level1": 0.9979}
 
 
+def profiled_classes(mk, torch, dev, solve):
+    """Per (kernel class, level) device time, algorithmic bytes and launches of one solve,
+    measured by the library's event brackets (a first solve captures the timed graph)."""
+    import ctypes
+    lib = mk.lib()
+    lib.mk_set_profiling(1)
+    solve()
+    lib.mk_profile_reset()
+    solve()
+    torch.cuda.synchronize(dev)
+    rows = []
+    for cls in range(9):
+        for lvl in range(0, 13):
+            ms_, by_, n_ = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+            lib.mk_profile_read(cls, lvl, ctypes.byref(ms_), ctypes.byref(by_), ctypes.byref(n_))
+            if n_.value:
+                rows.append((ms_.value, by_.value, n_.value, lib.mk_profile_class_name(cls).decode(), lvl))
+    lib.mk_set_profiling(0)
+    rows.sort(reverse=True)
+    return rows
+
+
+def class_table(rows, top=10):
+    total_ms = sum(r[0] for r in rows)
+    return [{"kernel": f"{r[3]}@level{r[4]}", "ms": round(r[0], 4), "share": round(r[0] / total_ms, 4),
+             "launches": int(r[2]), "GBps": round(r[1] / (r[0] * 1e-3) / 1e9, 1)} for r in rows[:top]]
+
+
 def bench_2d(mk, torch, dev, args, steps=2):
     """The 2D workload: 255 x 255 interior points, theta = 1/2, n_t = 1024, T = 0.05, mixed
     precision, 4 levels nu = 2 with 2 x 2 agglomeration per coarsening (66.7 M space-time
@@ -178,10 +206,55 @@ def bench_2d(mk, torch, dev, args, steps=2):
             e1.synchronize()
             tm.append(e0.elapsed_time(e1) / 1e3)
         march_err = float(((um - u).abs().max() / um.abs().max()).item())
-    return {"s": statistics.mean(ts), "iterations": int(info.iterations),
+        classes = class_table(profiled_classes(mk, torch, dev, lambda: mk.mk_solve(p.handle, u0, u, o)))
+    return {"s": statistics.mean(ts), "iterations": int(info.iterations), "kernel_classes": classes,
             "march_gpu_s": statistics.mean(tm), "max_rel_diff_vs_march": march_err,
             "rel_residual": info.rel_residual, "points": int(P.nx * P.ny * (P.nt + 1)),
             "workload": "heat2d_255x255_nt1024_theta0.5_T0.05_L4_nu2_2x2space", "tol": args.tol}
+
+
+def bench_alternate(mk, torch, dev, steps=2):
+    """The Table 3 workload (Sec. 4.2): 2D 192 x 192, n_t = 2^11, C = 0.16, theta = 1/2,
+    alternate time-space coarsening with 7, 9 and 11 levels (mk_schedule_alternate), mixed
+    precision, tol 1e-6 (the paper's criterion), against the GPU theta-march of the same
+    problem (the paper reports its MK time relative to the sequential theta-scheme)."""
+    P = W.heat2d_alternate(7)
+    u0 = torch.from_numpy(P.u0).to(dev)
+    u = torch.empty((P.nt + 1,) + P.space_shape(), dtype=torch.float64, device=dev)
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(steps):
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return statistics.mean(ts), r
+
+    out = {"workload": "heat2d_192x192_nt2048_C0.16_theta0.5_alternate_TS", "tol": 1e-6,
+           "points": int(P.nx * P.ny * (P.nt + 1))}
+    with mk.Problem(P.dim, P.nx, P.tau, P.theta, P.dt, P.nt, None, ny=P.ny) as p:
+        um = torch.empty_like(u)
+        t_march, _ = timed(lambda: mk.mk_march(p.handle, u0, um))
+        out["march_gpu_s"] = t_march
+        for levels in (7, 9, 11):
+            o = mk.mk_schedule_alternate(2, P.nx, P.ny, P.nt, P.tau, P.dt, levels, n_cgs=16,
+                                         tol=1e-6, precision="mixed", max_iters=200)
+            t, info = timed(lambda: mk.mk_solve(p.handle, u0, u, o))
+            err = float(((u - um).abs().max() / um.abs().max()).item())
+            out[f"L{levels}"] = {"s": t, "iterations": int(info.iterations),
+                                 "rel_residual": info.rel_residual,
+                                 "relative_to_march": t / t_march,
+                                 "max_rel_diff_vs_march": err}
+            if levels == 7:
+                out["L7"]["kernel_classes"] = class_table(
+                    profiled_classes(mk, torch, dev, lambda: mk.mk_solve(p.handle, u0, u, o)), 8)
+    return out
 
 
 def bench_batch(mk, torch, dev, count_1d=12, count_2d=4, max_iters=600):
@@ -364,6 +437,12 @@ def main():
         except Exception as e:
             line["paths"]["mk_mixed_2d"] = {"error": str(e)[:200]}
 
+        # ---------------- Table 3 workload: alternate time-space coarsening, 7-11 levels ----
+        try:
+            line["paths"]["mk_alternate_2d"] = bench_alternate(mk, torch, dev)
+        except Exception as e:
+            line["paths"]["mk_alternate_2d"] = {"error": str(e)[:200]}
+
         # ---------------- batched uneven problems ----------------
         try:
             line["paths"]["mk_batch"] = bench_batch(mk, torch, dev)
@@ -371,23 +450,7 @@ def main():
             line["paths"]["mk_batch"] = {"error": str(e)[:200]}
 
         # ---------------- roofline: kernel-class timing of one profiled solve ----------------
-        lib = mk.lib()
-        lib.mk_set_profiling(1)
-        mk.mk_solve(prob.handle, u0_dev, u_dev, o_mixed)     # capture with timing events
-        lib.mk_profile_reset()
-        mk.mk_solve(prob.handle, u0_dev, u_dev, o_mixed)
-        torch.cuda.synchronize(dev)
-        import ctypes
-        rows = []
-        for cls in range(9):
-            for lvl in range(0, 13):
-                ms_, by_, n_ = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
-                lib.mk_profile_read(cls, lvl, ctypes.byref(ms_), ctypes.byref(by_), ctypes.byref(n_))
-                if n_.value:
-                    rows.append((ms_.value, by_.value, n_.value, lib.mk_profile_class_name(cls).decode(), lvl))
-        lib.mk_set_profiling(0)
-        rows.sort(reverse=True)
-        total_ms = sum(r[0] for r in rows)
+        rows = profiled_classes(mk, torch, dev, lambda: mk.mk_solve(prob.handle, u0_dev, u_dev, o_mixed))
         peak, peak_kind = _peaks()
         top = rows[0]
         ach = top[1] / (top[0] * 1e-3) / 1e9
@@ -400,9 +463,7 @@ def main():
                             "traffic_unit": "bytes per launch",
                             "alg_bytes_per_launch": top[1] / top[2],
                             "launches": int(top[2]), "avg_launch_us": top[0] / top[2] * 1e3}
-        line["kernel_classes"] = [
-            {"kernel": f"{r[3]}@level{r[4]}", "ms": round(r[0], 4), "share": round(r[0] / total_ms, 4),
-             "launches": int(r[2]), "GBps": round(r[1] / (r[0] * 1e-3) / 1e9, 1)} for r in rows[:10]]
+        line["kernel_classes"] = class_table(rows)
 
         # ---------------- e2e through host buffers ----------------
         g_h = torch.from_numpy(P.g).pin_memory()

@@ -110,6 +110,24 @@ typedef struct mk_problem mk_problem;
 /* Defaults listed above. */
 void mk_default_opts(mk_solve_opts *opts);
 
+/* Alternate time-space coarsening schedule (Sec. 4.2, Table 3).  Fills opts->levels, nu[],
+   space[], m_inner[] and n_cgs for a hierarchy of `levels` levels on a problem with nx (x ny)
+   interior points, nt steps of size dt and diffusion tau; other fields are left as they are.
+   Level l has the Courant number C_l = c_d tau dT_l / dX_l^2 (c_d = 2 in 1D, 3 in 2D, as the
+   paper defines them in Sec. 3.3.1 and 3.3.2), with dT_l its step (a_l + b_l) and dX_l^2 =
+   2^s h^2 after s pair / 2x2 agglomerations (the Galerkin operator of an agglomerated uniform
+   stencil has twice the squared spacing).  Coarsening is in time (nu = 2, space kept) while
+   C_l <= c_max; from the first level whose C_l exceeds c_max, space-only coarsenings (nu = 1,
+   pairs / 2x2) and time coarsenings alternate, space first.  Inner FGMRES iterations: 2 on the
+   intermediate levels, 1 on the level just above the coarsest (Sec. 4.2).
+   Errors (opts untouched): MK_ERR_INVALID for a null opts, levels outside 2..MK_MAX_LEVELS,
+   dim not 1 or 2, nx, ny, nt, n_cgs < 1, tau, dt, c_max <= 0, a time coarsening of a level
+   whose n_t is odd, a space coarsening of a direction with fewer than 2 points, or a coarsest
+   n_t not divisible by n_cgs.  Host only: no device is touched. */
+mk_status mk_schedule_alternate(int32_t dim, int32_t nx, int32_t ny, int32_t nt, double tau,
+                                double dt, int32_t levels, int32_t n_cgs, double c_max,
+                                mk_solve_opts *opts);
+
 /* Human-readable status name. */
 const char *mk_status_string(mk_status s);
 

@@ -18,7 +18,7 @@ from ._lib import (MK_MAX_LEVELS, MKError, mk_level_desc, mk_solve_info, mk_solv
                    mk_stencil)
 
 __all__ = ["mk_default_opts", "mk_create_problem", "mk_set_source", "mk_destroy", "mk_solve",
-           "mk_solve_rhs", "mk_march", "mk_adjoint", "mk_level_info", "mk_op_rhs", "mk_op_apply",
+           "mk_solve_rhs", "mk_march", "mk_schedule_alternate", "mk_adjoint", "mk_level_info", "mk_op_rhs", "mk_op_apply",
            "mk_op_residual", "mk_op_residual_noalloc", "mk_op_restrict", "mk_op_interp_correct", "mk_op_coarsest",
            "mk_op_precond", "mk_op_orthogonalize", "mk_op_lsq", "mk_kernel_launch_count",
            "mk_create_batch", "mk_solve_batch", "mk_destroy_batch", "Batch",
@@ -97,6 +97,17 @@ def make_opts(levels: int = 3, nu: Sequence[int] = (), space: Sequence[bool] = (
     o.use_graph = 1 if use_graph else 0
     o.orth = int(orth)
     o.autotune = 1 if autotune else 0
+    return o
+
+
+def mk_schedule_alternate(dim: int, nx: int, ny: int, nt: int, tau: float, dt: float, levels: int,
+                          n_cgs: int = 16, c_max: float = 1.0, opts: mk_solve_opts | None = None,
+                          **kw) -> mk_solve_opts:
+    """Alternate time-space coarsening (Sec. 4.2): levels, nu, space, m_inner and n_cgs filled
+    in by the library into `opts` (or into make_opts(**kw))."""
+    o = make_opts(**kw) if opts is None else opts
+    _lib.check(lib().mk_schedule_alternate(dim, nx, ny if dim == 2 else 1, nt, tau, dt, levels,
+                                           n_cgs, c_max, ctypes.byref(o)), "mk_schedule_alternate")
     return o
 
 

@@ -53,6 +53,10 @@ _I = ctypes.c_int32
 SIGNATURES = {
     "mk_default_opts": (None, [ctypes.POINTER(mk_solve_opts)]),
     "mk_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mk_schedule_alternate": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                             ctypes.POINTER(mk_solve_opts)]),
     "mk_last_cuda_error": (ctypes.c_char_p, []),
     "mk_kernel_launch_count": (ctypes.c_int64, []),
     "mk_set_profiling": (None, [_I]),

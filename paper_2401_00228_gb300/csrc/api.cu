@@ -179,6 +179,46 @@ void mk_default_opts(mk_solve_opts *o) {
     o->orth = 1;
 }
 
+mk_status mk_schedule_alternate(int32_t dim, int32_t nx, int32_t ny, int32_t nt, double tau,
+                                double dt, int32_t levels, int32_t n_cgs, double c_max,
+                                mk_solve_opts *opts) {
+    if (!opts || (dim != 1 && dim != 2) || levels < 2 || levels > MK_MAX_LEVELS) return MK_ERR_INVALID;
+    if (dim == 1) ny = 1;
+    if (nx < 1 || ny < 1 || nt < 1 || n_cgs < 1) return MK_ERR_INVALID;
+    if (!(tau > 0.0) || !(dt > 0.0) || !(c_max > 0.0)) return MK_ERR_INVALID;
+    const double cd = dim == 1 ? 2.0 : 3.0;
+    const double h = 1.0 / (nx + 1);
+    mk_solve_opts o = *opts;
+    double dT = dt, dx2 = h * h;
+    int n_t = nt, mx = nx, my = ny;
+    bool alternating = false, next_space = true;
+    for (int l = 0; l + 1 < levels; ++l) {
+        if (!alternating && cd * tau * dT / dx2 > c_max) alternating = true;
+        const bool space = alternating && next_space;
+        if (alternating) next_space = !next_space;
+        if (space) {
+            if (mx < 2 || (dim == 2 && my < 2)) return MK_ERR_INVALID;
+            mx = (mx + 1) / 2;
+            if (dim == 2) my = (my + 1) / 2;
+            dx2 *= 2.0;
+            o.nu[l] = 1;
+            o.space[l] = 1;
+        } else {
+            if (n_t % 2) return MK_ERR_INVALID;
+            n_t /= 2;
+            dT *= 2.0;
+            o.nu[l] = 2;
+            o.space[l] = 0;
+        }
+    }
+    if (n_t % n_cgs) return MK_ERR_INVALID;
+    for (int l = 0; l + 2 < levels; ++l) o.m_inner[l] = (l + 3 == levels) ? 1 : 2;
+    o.levels = levels;
+    o.n_cgs = n_cgs;
+    *opts = o;
+    return MK_OK;
+}
+
 const char *mk_status_string(mk_status s) {
     switch (s) {
         case MK_OK: return "MK_OK";
@@ -368,17 +408,15 @@ mk_status mk_march(mk_problem *p, const double *u0, double *u_out, void *stream)
         launch_march_1d(P.g, b, op, P.m_alpha.as<double>(), P.m_gamma.as<double>(),
                         P.m_binv.as<double>(), P.m_npad, P.m_nlev, fbuf.as<double>(),
                         ubuf.as<double>(), s);
-    else if (P.m_dst2d) {
-        // u_0 = f_0 (guard and plane 0), then the steps
+    else {
+        // 2D: u_0 = f_0 (guard and plane 0), then the steps
         CK(cudaMemcpyAsync(ubuf.p, fbuf.p, sizeof(double) * (size_t)(P.g.guard + P.g.plane),
                            cudaMemcpyDeviceToDevice, s));
         launch_march_2d_dst(P.g, a, b, P.m_cx, P.m_cy, P.m_lamx.as<double>(), P.m_lamy.as<double>(),
-                            P.m_twx.as<double2>(), P.m_twy.as<double2>(), fbuf.as<double>(),
-                            ubuf.as<double>(), P.m_t1.as<double>(), s);
-    } else
-        launch_march_2d(P.g, a, b, op, P.m_Sx.as<double>(), P.m_Sxi.as<double>(),
-                        P.m_lamx.as<double>(), P.m_Sy.as<double>(), P.m_Syi.as<double>(),
-                        P.m_lamy.as<double>(), fbuf.as<double>(), ubuf.as<double>(), s);
+                            P.m_twx.as<double2>(), P.m_twy.as<double2>(), P.m_Sx.as<double>(),
+                            P.m_Sy.as<double>(), fbuf.as<double>(), ubuf.as<double>(),
+                            P.m_t1.as<double>(), s);
+    }
     launch_unpack<double, double>(P.g, ubuf.as<double>(), os.dev, s);
     CK(cudaGetLastError());
     CKS(finish_out(os, s));

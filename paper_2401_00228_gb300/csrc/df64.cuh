@@ -76,6 +76,14 @@ __device__ __forceinline__ df lap3_exact(float l, float c, float r) {
     return fast_two_sum(s2.hi, s2.lo + s1.lo);
 }
 
+// (l + r) + (d + u) - 4 c of five floats as a double-float: the pair sums exact, their sum
+// and the -4 c term with roundings of order 2^-48 of the largest operand
+__device__ __forceinline__ df lap5_df(float l, float r, float d, float u, float c) {
+    const df s = df_add(two_sum(l, r), two_sum(d, u));
+    const df t = two_sum(s.hi, -4.f * c);
+    return fast_two_sum(t.hi, t.lo + s.lo);
+}
+
 __host__ __device__ __forceinline__ float2 df_pack(df x) { return make_float2(x.hi, x.lo); }
 __host__ __device__ __forceinline__ df df_unpack(float2 v) { return {v.x, v.y}; }
 

@@ -197,6 +197,36 @@ __global__ void __launch_bounds__(256) k_apply_df_2d_uni(Geom g, const float2 *_
     w[idx] = df_pack(r);
 }
 
+// The same for cx == cy (a square grid): one five-point bracket per plane and one
+// double-float product per time weight.  u = [a c, b c, a c, b c].
+template <bool HAS_B>
+__global__ void __launch_bounds__(256) k_apply_df_2d_sq(Geom g, const float2 *__restrict__ u,
+                                                        const float *__restrict__ x,
+                                                        float2 *__restrict__ w,
+                                                        const int *__restrict__ done) {
+    if (done && *done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const int64_t idx = g.at(k, j, i);
+    const float c = x[idx];
+    df r;
+    if (k == 0) {
+        r = df_from_float(c);
+    } else {
+        const int64_t ip = idx - g.plane;
+        const float p = x[ip];
+        const df aL = df_mul(df_unpack(u[0]), lap5_df(x[idx - 1], x[idx + 1], x[idx - g.ldx],
+                                                      x[idx + g.ldx], c));
+        r = df_sub(df_from_sum(c, -p), aL);
+        if (HAS_B)
+            r = df_sub(r, df_mul(df_unpack(u[1]), lap5_df(x[ip - 1], x[ip + 1], x[ip - g.ldx],
+                                                          x[ip + g.ldx], p)));
+    }
+    w[idx] = df_pack(r);
+}
+
 template <int DIM, bool SPACE>
 __global__ void __launch_bounds__(256) k_interp_df(Geom gf, Geom gc, int nu,
                                                    const float2 *__restrict__ ca,
@@ -355,7 +385,8 @@ __global__ void __launch_bounds__(256) k_interp_df_1d(Geom gf, Geom gc, int nu,
 void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const float2 *ca,
                       const float2 *cb, bool has_b, const float2 *v, const double *sigma,
                       const float *Xc, int mc, int64_t xc_stride, const double *yc, float *x,
-                      float2 *wout, const int *done, cudaStream_t s, const float2 *uniform_ab) {
+                      float2 *wout, const int *done, cudaStream_t s, const float2 *uniform_ab,
+                      bool uniform_square) {
     int kc = choose_kc(gf.npts(), gf.nt + 1);
     int nch = (gf.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(gf.dim, gf.nx, gf.ny, nch);
@@ -388,7 +419,11 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
         else
             k_interp_x2d<false, float2, float, float><<<g4, b2, 0, s>>>(gf, gc, nu, v, sigma, Xc, mc,
                                                                        xc_stride, yc, x, done);
-        if (uniform_ab && hb) k_apply_df_2d_uni<true><<<g2, b2, 0, s>>>(gf, uniform_ab, x, wout, done);
+        if (uniform_ab && uniform_square && hb)
+            k_apply_df_2d_sq<true><<<g2, b2, 0, s>>>(gf, uniform_ab, x, wout, done);
+        else if (uniform_ab && uniform_square)
+            k_apply_df_2d_sq<false><<<g2, b2, 0, s>>>(gf, uniform_ab, x, wout, done);
+        else if (uniform_ab && hb) k_apply_df_2d_uni<true><<<g2, b2, 0, s>>>(gf, uniform_ab, x, wout, done);
         else if (uniform_ab) k_apply_df_2d_uni<false><<<g2, b2, 0, s>>>(gf, uniform_ab, x, wout, done);
         else k_apply_df_2d<<<g2, b2, 0, s>>>(gf, ca, cb, hb, x, wout, done);
         count_launch();

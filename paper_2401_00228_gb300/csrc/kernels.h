@@ -126,14 +126,17 @@ void launch_slab_2d_fdm(const Geom &g, double a, double b, const T *Sx, const T 
                         T *rh, const T *r, T *x, const int *done, cudaStream_t s);
 
 // Sequential 2D theta-march with a sine-transform solve per step (march2d.cu): FP64, for the
-// uniform fine-level operator, n + 1 a power of two (march2d_transform_size != 0) in both
-// directions.  u's plane 0 must hold u_0; t1 is nx ny doubles of scratch.  3 n_t launches.
+// uniform fine-level operator.  Per direction the transform is an FFT when n + 1 is a power of
+// two (march2d_transform_size != 0, twiddles tw) and otherwise the dense sine matrix S (n x n,
+// n <= MARCH2D_DENSE_MAX).  u's plane 0 must hold u_0; t1 is nx ny doubles of scratch.
+// 3 n_t launches.
+constexpr int MARCH2D_DENSE_MAX = 1024;
 int march2d_transform_size(int n);
 cudaError_t march2d_set_attributes();
 void launch_march_2d_dst(const Geom &g, double a, double b, double cx, double cy,
                          const double *lamx, const double *lamy, const double2 *twx,
-                         const double2 *twy, const double *f, double *u, double *t1,
-                         cudaStream_t s);
+                         const double2 *twy, const double *Sx, const double *Sy, const double *f,
+                         double *u, double *t1, cudaStream_t s);
 
 // Coarsest decoupled slabs by sine-transform diagonalisation (slab_dst.cu), FP32, for a
 // uniform 1D operator.  dst_transform_size(n) = 2(n+1) when that is a power of two <= 4096,
@@ -175,7 +178,7 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
                       const float2 *cb, bool has_b, const float2 *v, const double *sigma,
                       const float *Xc, int mc, int64_t xc_stride, const double *yc, float *x,
                       float2 *wout, const int *done, cudaStream_t s,
-                      const float2 *uniform_ab = nullptr);
+                      const float2 *uniform_ab = nullptr, bool uniform_square = false);
 // u += sum_{i < jf} y_i X_i for FP32 X in double-float arithmetic (mixed level 1)
 void launch_combine_df(int64_t len, double *u, const float *X, int64_t xstride, KState ks,
                        cudaStream_t s);
@@ -208,13 +211,10 @@ void launch_slab_2d(const Geom &g, double a, double b, SpaceOp<T> L, const T *Sx
                     const T *lamx, const T *Sy, const T *Syi, const T *lamy, int n_cgs,
                     const T *r, T *x, const int *done, cudaStream_t s);
 
-// Sequential theta-march on the GPU (FP64): the same direct solvers, one slab of nt steps
-// with the coupling kept (1D: one CTA; 2D: one CTA per step-solve).
+// Sequential 1D theta-march on the GPU (FP64): the same direct solver, one slab of nt steps
+// with the coupling kept, in one CTA.
 void launch_march_1d(const Geom &g, double b, SpaceOp<double> L, const double *alpha,
                      const double *gamma, const double *binv, int npad, int nlev,
                      const double *f, double *u, cudaStream_t s);
-void launch_march_2d(const Geom &g, double a, double b, SpaceOp<double> L, const double *Sx,
-                     const double *Sxi, const double *lamx, const double *Sy, const double *Syi,
-                     const double *lamy, const double *f, double *u, cudaStream_t s);
 
 }  // namespace mk

@@ -8,7 +8,8 @@
 // step (rows: stencil + DST in x; columns: DST in y, divide, inverse DST in y; rows: inverse DST
 // in x), all in FP64; the time loop stays sequential.
 //
-// DST-I through a complex FFT of length N2 = 2(n+1) (a power of two): the odd extension
+// When n + 1 is a power of two, the DST-I runs through a complex FFT of length N2 = 2(n+1);
+// otherwise (n <= MARCH2D_DENSE_MAX) as a dense product with the sine matrix.  The odd extension
 //     y_0 = 0, y_m = v_{m-1} (1 <= m <= n), y_{n+1} = 0, y_{N2-m} = -v_{m-1}
 // has Y_m = -2i sum_j v_j sin(pi m (j+1)/(n+1)), so DST(v)_j = -Im(Y_{j+1}) / 2.  The FFT is the
 // Stockham auto-sort form with radix-8 passes and one radix-4 or radix-2 pass, twiddles from a
@@ -108,10 +109,24 @@ __device__ __forceinline__ void zfft(double2 *a, int N, int logN, const double2 
     else if (p == 1) zpass<2>(a, N, Ns, tw);
 }
 
-// DST-I of the n values get(m), m = 0..n-1, into put(j, value), j = 0..n-1
+// DST-I of the n values get(m), m = 0..n-1, into put(j, value), j = 0..n-1.  With S non-null
+// (n + 1 not a power of two) the transform is the dense product with the symmetric matrix
+// S[m][j] = sin(pi (m+1)(j+1) / (n+1)), one output per thread, v staged in shared memory.
 template <typename Get, typename Put>
 __device__ __forceinline__ void zdst(double2 *a, int n, int N2, int logN2, const double2 *tw,
-                                     Get get, Put put) {
+                                     const double *__restrict__ S, Get get, Put put) {
+    if (S) {
+        double *v = reinterpret_cast<double *>(a);
+        for (int m = threadIdx.x; m < n; m += M2_THREADS) v[m] = get(m);
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += M2_THREADS) {
+            double acc = 0.0;
+            for (int m = 0; m < n; ++m) acc = fma(S[(int64_t)m * n + j], v[m], acc);
+            put(j, acc);
+        }
+        __syncthreads();
+        return;
+    }
     const int N = n + 1;
     for (int m = threadIdx.x; m < N2; m += M2_THREADS) {
         double v = 0.0;
@@ -129,6 +144,7 @@ struct March2D {
     Geom g;
     double b, cx, cy;
     int N2x, logx, N2y, logy;
+    const double *Sx, *Sy;   // dense transforms (null: FFT)
 };
 
 // rows j: t1[j][:] = DST_x(f_k + u_{k-1} + b L u_{k-1})[j][:]
@@ -149,7 +165,7 @@ __global__ void __launch_bounds__(M2_THREADS) k_march2d_rows(March2D M, int k,
         return f[base + i] + (c + M.b * (M.cx * lx + M.cy * ly));
     };
     auto put = [&](int i, double v) { t1[(int64_t)j * g.nx + i] = v; };
-    zdst(zs, g.nx, M.N2x, M.logx, twx, get, put);
+    zdst(zs, g.nx, M.N2x, M.logx, twx, M.Sx, get, put);
 }
 
 // columns i: t1[:][i] <- S_y^{-1}-scaled solve in the eigenbasis, back through S_y
@@ -166,9 +182,9 @@ __global__ void __launch_bounds__(M2_THREADS) k_march2d_cols(March2D M, double a
     auto put_div = [&](int j, double v) {
         t1[(int64_t)j * g.nx + i] = v / (1.0 - a * (lx + lamy[j]));
     };
-    zdst(zs, g.ny, M.N2y, M.logy, twy, get, put_div);
+    zdst(zs, g.ny, M.N2y, M.logy, twy, M.Sy, get, put_div);
     auto put = [&](int j, double v) { t1[(int64_t)j * g.nx + i] = v; };
-    zdst(zs, g.ny, M.N2y, M.logy, twy, get, put);
+    zdst(zs, g.ny, M.N2y, M.logy, twy, M.Sy, get, put);
 }
 
 // rows j: u_k[j][:] = (4 / ((nx+1)(ny+1))) DST_x(t1[j][:])
@@ -183,7 +199,7 @@ __global__ void __launch_bounds__(M2_THREADS) k_march2d_out(March2D M, int k,
     auto get = [&](int i) -> double { return t1[(int64_t)j * g.nx + i]; };
     const int64_t base = g.at(k, j, 0);
     auto put = [&](int i, double v) { u[base + i] = sc * v; };
-    zdst(zs, g.nx, M.N2x, M.logx, twx, get, put);
+    zdst(zs, g.nx, M.N2x, M.logx, twx, M.Sx, get, put);
 }
 
 }  // namespace
@@ -195,6 +211,11 @@ int march2d_transform_size(int n) {
 }
 
 size_t march2d_smem_bytes(int N2) { return sizeof(double2) * ((size_t)N2 + (size_t)N2 / 32 + 1); }
+
+static size_t march2d_smem_for(int n) {
+    const int N2 = march2d_transform_size(n);
+    return N2 ? march2d_smem_bytes(N2) : sizeof(double) * (size_t)n;
+}
 
 cudaError_t march2d_set_attributes() {
     const int mx = (int)march2d_smem_bytes(4096);
@@ -208,8 +229,8 @@ cudaError_t march2d_set_attributes() {
 
 void launch_march_2d_dst(const Geom &g, double a, double b, double cx, double cy,
                          const double *lamx, const double *lamy, const double2 *twx,
-                         const double2 *twy, const double *f, double *u, double *t1,
-                         cudaStream_t s) {
+                         const double2 *twy, const double *Sx, const double *Sy, const double *f,
+                         double *u, double *t1, cudaStream_t s) {
     March2D M;
     M.g = g;
     M.b = b;
@@ -221,7 +242,9 @@ void launch_march_2d_dst(const Geom &g, double a, double b, double cx, double cy
     while ((1 << M.logx) < M.N2x) ++M.logx;
     M.logy = 0;
     while ((1 << M.logy) < M.N2y) ++M.logy;
-    const size_t shx = march2d_smem_bytes(M.N2x), shy = march2d_smem_bytes(M.N2y);
+    M.Sx = M.N2x ? nullptr : Sx;
+    M.Sy = M.N2y ? nullptr : Sy;
+    const size_t shx = march2d_smem_for(g.nx), shy = march2d_smem_for(g.ny);
     prof_begin(s);
     for (int k = 1; k <= g.nt; ++k) {
         k_march2d_rows<<<g.ny, M2_THREADS, shx, s>>>(M, k, f, u, t1, twx);

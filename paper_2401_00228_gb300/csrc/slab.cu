@@ -727,12 +727,6 @@ void launch_slab_2d(const Geom &g, double a, double b, SpaceOp<T> L, const T *Sx
                           done, s);
 }
 
-void launch_march_2d(const Geom &g, double a, double b, SpaceOp<double> L, const double *Sx,
-                     const double *Sxi, const double *lamx, const double *Sy, const double *Syi,
-                     const double *lamy, const double *f, double *u, cudaStream_t s) {
-    slab_2d_launch<double>(g, a, b, L, Sx, Sxi, lamx, Sy, Syi, lamy, 1, g.nt, 1, f, u, nullptr, s);
-}
-
 // Opt in to large dynamic shared memory once, before any launch or graph capture.
 cudaError_t slab_set_attributes() {
     const int big = SLAB_SMEM_LIMIT;

@@ -280,6 +280,7 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
                                      df_pack_host(lv->w.a * cy), df_pack_host(lv->w.b * cy)};
                 MKCK(lv->cuni.alloc(sizeof(u)));
                 MKCK(cudaMemcpy(lv->cuni.p, u, sizeof(u), cudaMemcpyHostToDevice));
+                lv->cuni_square = P.dim == 2 && cx == cy;
             }
         }
         if (st != MK_OK) return st;
@@ -387,7 +388,7 @@ struct InterpStep<float2, float, float, float2, double> {
         const float2 *ca = L.cdf.as<float2>();
         launch_interp_df(L.g, C.g, L.nu, L.space, ca, ca + nc, L.w.b != 0.0, vj, sig, Xc, mc,
                          C.stride, yc, L.X.as<float>() + (int64_t)j * L.stride, L.W.as<float2>(),
-                         done, s, L.cuni.p ? L.cuni.as<float2>() : nullptr);
+                         done, s, L.cuni.p ? L.cuni.as<float2>() : nullptr, L.cuni_square);
     }
 };
 template <typename Tv, typename Tc, typename Tx, typename Tw, typename Tcw>
@@ -822,7 +823,8 @@ mk_status prepare_march(Problem &P) {
             spike_tables(Lx, a, P.m_spikeU, spike_threads(P.nx), tab);
             MKCK(upload<double>(P.m_spike, tab));
         }
-    } else if (march2d_transform_size(P.nx) && march2d_transform_size(P.ny)) {
+    } else if ((march2d_transform_size(P.nx) || P.nx <= MARCH2D_DENSE_MAX) &&
+               (march2d_transform_size(P.ny) || P.ny <= MARCH2D_DENSE_MAX)) {
         // uniform fine-level operator: analytic eigenvalues, sine transform per step
         const double pi = 3.14159265358979323846;
         double cx = 0.0, cy = 0.0;
@@ -842,21 +844,25 @@ mk_status prepare_march(Problem &P) {
         MKCK(upload<double>(P.m_lamy, ly));
         MKCK(upload<double>(P.m_twx, twx));
         MKCK(upload<double>(P.m_twy, twy));
+        // dense sine matrices for directions whose n + 1 is not a power of two
+        // (the angle reduced modulo 2 pi exactly, in integers, before the sine)
+        auto sine_matrix = [&](int n, DevMem &m) -> cudaError_t {
+            if (march2d_transform_size(n)) return cudaSuccess;
+            std::vector<double> S((size_t)n * n);
+            const int64_t period = 2 * (int64_t)(n + 1);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j)
+                    S[(size_t)i * n + j] =
+                        std::sin(pi * (double)(((int64_t)(i + 1) * (j + 1)) % period) / (n + 1));
+            return upload<double>(m, S);
+        };
+        MKCK(sine_matrix(P.nx, P.m_Sx));
+        MKCK(sine_matrix(P.ny, P.m_Sy));
         MKCK(P.m_t1.alloc(sizeof(double) * (size_t)P.nx * P.ny));
         P.m_cx = cx;
         P.m_cy = cy;
-        P.m_dst2d = true;
     } else {
-        if (P.nx > 48 || P.ny > 48) return MK_ERR_INVALID;
-        std::vector<double> lx, Sx, Sxi, ly, Sy, Syi;
-        tri_eigen(Lx, lx, Sx, Sxi);
-        tri_eigen(Ly, ly, Sy, Syi);
-        MKCK(upload<double>(P.m_Sx, Sx));
-        MKCK(upload<double>(P.m_Sxi, Sxi));
-        MKCK(upload<double>(P.m_lamx, lx));
-        MKCK(upload<double>(P.m_Sy, Sy));
-        MKCK(upload<double>(P.m_Syi, Syi));
-        MKCK(upload<double>(P.m_lamy, ly));
+        return MK_ERR_INVALID;
     }
     P.march_ready = true;
     return MK_OK;

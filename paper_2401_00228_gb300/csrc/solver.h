@@ -48,6 +48,7 @@ struct Level {
     DevMem c64, c32;   // [3nx | 3ny] coefficients
     DevMem cdf;        // mixed level 1: double-float a*L then b*L, each [3nx | 3ny]
     DevMem cuni;       // mixed level 1 with uniform L: double-float (a cx, b cx, a cy, b cy)
+    bool cuni_square = false;   // ... and cx == cy
     SpaceOp<double> op64{nullptr, nullptr};
     SpaceOp<float> op32{nullptr, nullptr};
     // vectors (level 1: V, W in FP64, X in the cycle precision; others in cycle precision)
@@ -95,12 +96,14 @@ struct Problem {
     std::unique_ptr<Hierarchy> H; // cached for the last options
     // march tables (fine level, FP64)
     bool march_ready = false;
-    DevMem m_c64, m_alpha, m_gamma, m_binv, m_Sx, m_Sxi, m_lamx, m_Sy, m_Syi, m_lamy;
+    DevMem m_c64, m_alpha, m_gamma, m_binv;
+    // 2D march: eigenvalues of L_x, L_y and, where n + 1 is not a power of two, the dense
+    // sine matrices
+    DevMem m_lamx, m_lamy, m_Sx, m_Sy;
     int m_npad = 0, m_nlev = 0;
     DevMem m_spike;
     int m_spikeU = 0;
-    // 2D march by a sine-transform solve per step (n + 1 a power of two)
-    bool m_dst2d = false;
+    // 2D march by a sine-transform solve per step (FFT twiddles, scratch)
     double m_cx = 0.0, m_cy = 0.0;
     DevMem m_twx, m_twy, m_t1;
 };

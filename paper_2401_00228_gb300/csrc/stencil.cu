@@ -220,8 +220,8 @@ void launch_residual(const Geom &g, const Weights &w, SpaceOp<double> L, const d
 //   Thread -> coarse spatial point (aggregate), loop over a chunk of coarse blocks; the
 //   fine points of the aggregate (1, 2 or 4) each carry their own (v_{k-1}, L v_{k-1}).
 // ---------------------------------------------------------------------------------------
-template <int DIM, bool SPACE, typename Tin, typename Tout, typename Tc>
-__global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu, Tc a, Tc b, Tc mu,
+template <int DIM, bool SPACE, typename Tin, typename Tout, typename Tc, int NU = 0>
+__global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu_rt, Tc a, Tc b, Tc mu,
                                                   SpaceOp<Tc> L, const Tin *__restrict__ v,
                                                   const double *__restrict__ sigma,
                                                   Tout *__restrict__ vhat, int kc,
@@ -230,6 +230,9 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu, Tc a
     if (done && *done) return;
     constexpr int PX = SPACE ? 2 : 1;
     constexpr int PY = (SPACE && DIM == 2) ? 2 : 1;
+    // NU > 0: the coarsening factor fixed at compile time (the fine steps of a coarse block
+    // unrolled, their loads issued together)
+    const int nu = NU > 0 ? NU : nu_rt;
     int I, J, chunk;
     point_index<DIM>(I, J, chunk);
     double acc2 = 0.0;
@@ -285,7 +288,8 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu, Tc a
                         }
                     }
             } else {
-                for (int s = 1; s <= nu; ++s) {
+#pragma unroll
+                for (int s = 1; s <= (NU > 0 ? NU : nu); ++s) {
                     int kf = nu * (K - 1) + s;
 #pragma unroll
                     for (int q = 0; q < PY; ++q)
@@ -408,9 +412,15 @@ void launch_restrict(const Geom &gf, const Geom &gc, int nu, bool space, const W
     int nch = (gc.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(gf.dim, gc.nx, gc.ny, nch);
     Tc a = (Tc)w.a, b = (Tc)w.b, mu = (Tc)w.mu;
-#define MK_RESTRICT(D, S) \
-    k_restrict<D, S, Tin, Tout, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, nu, a, b, mu, L, v, sigma, \
-                                                                vhat, kc, rs, slot, ks_c, done)
+#define MK_RESTRICT(D, S)                                                                     \
+    do {                                                                                      \
+        if (nu == 2)                                                                          \
+            k_restrict<D, S, Tin, Tout, Tc, 2><<<l.grid, l.block, 0, s>>>(                    \
+                gf, gc, nu, a, b, mu, L, v, sigma, vhat, kc, rs, slot, ks_c, done);           \
+        else                                                                                  \
+            k_restrict<D, S, Tin, Tout, Tc><<<l.grid, l.block, 0, s>>>(                       \
+                gf, gc, nu, a, b, mu, L, v, sigma, vhat, kc, rs, slot, ks_c, done);           \
+    } while (0)
 #define MK_RESTRICT1(S) \
     k_restrict_1d<S, Tin, Tout, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, nu, a, b, mu, L, v, sigma, \
                                                                 vhat, kc, rs, slot, ks_c, done)

@@ -1,6 +1,6 @@
 """Sequential 2D theta-march on the GPU (Eq. (timemarch)) by one sine-transform solve per
-step, for fine grids whose n + 1 is a power of two in both directions; other 2D grids up to
-48 x 48 use the dense eigenbasis march, larger ones are rejected.
+step: an FFT in directions whose n + 1 is a power of two (n <= 2047), the dense sine matrix
+in the others (n <= 1024); larger grids are rejected.
 
 Against the oracle's march (sparse LU per step, FP64), max relative error within
 max(1e-12, 8 eps n_t (1 + 4 max(a, b)(cx + cy))): each step rounds the explicit part
@@ -36,6 +36,10 @@ def _bound(P, steps=None):
     (31, 255, 16, 0.5, True),
     (7, 3, 40, 1.0, True),
     (1023, 15, 8, 0.5, False),
+    (100, 60, 16, 0.5, True),
+    (192, 192, 12, 0.5, False),
+    (127, 50, 10, 1.0, True),
+    (1, 1, 5, 0.5, True),
 ])
 def test_march2d_sine_vs_oracle(nx, ny, nt, theta, src):
     P = W.custom(2, nx, nt, 0.05, 1.0, theta, S, seed=nx + ny, ny=ny, with_source=src)
@@ -60,7 +64,7 @@ def test_march2d_full_size_sampled():
 
 
 def test_march2d_unsupported_size():
-    P = W.custom(2, 100, 8, 0.05, 1.0, 1.0, S, seed=5, ny=60)
+    P = W.custom(2, 1100, 4, 0.05, 1.0, 1.0, S, seed=5, ny=3)
     with mk.Problem(P.dim, P.nx, P.tau, P.theta, P.dt, P.nt, P.g, ny=P.ny) as p:
         u = np.empty((P.nt + 1,) + P.space_shape())
         with pytest.raises(mk.MKError, match="MK_ERR_INVALID"):

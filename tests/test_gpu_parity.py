@@ -52,6 +52,15 @@ SMALL = {
                                     seed=14, ny=13, with_source=True),
     "2d_33x31_T": lambda: W.custom(2, 33, 16, 0.02, 0.5, 0.5, W.Schedule((2,), (False,), (), 4),
                                    seed=15, ny=31),
+    "2d_31x31_TS": lambda: W.custom(2, 31, 32, 0.05, 1.0, 0.5, W.Schedule((2, 2), (True, True), (2,), 4),
+                                    seed=18, ny=31, with_source=True),
+    # alternate schedules (Sec. 4.2): space-only coarsenings with nu = 1 between time coarsenings
+    "1d_n90_alt": lambda: W.custom(1, 90, 64, 0.05, 1.0, 0.5,
+                                   W.Schedule((2, 1, 2), (False, True, False), (2, 1), 4),
+                                   seed=16, with_source=True),
+    "2d_24x22_alt": lambda: W.custom(2, 24, 32, 0.02, 1.0, 0.5,
+                                     W.Schedule((2, 1, 2, 1), (False, True, False, True), (2, 2, 1), 4),
+                                     seed=17, ny=22, with_source=True),
 }
 
 
@@ -253,9 +262,6 @@ def test_solve_small(case, precision, bound):
 
 def test_march_small(case):
     P, H, p = case
-    pow2 = all(((n + 1) & n) == 0 for n in (P.nx, P.ny))
-    if P.dim == 2 and max(P.nx, P.ny) > 48 and not pow2:
-        pytest.skip("2D march: n + 1 a power of two, or at most 48 x 48")
     u = np.empty((P.nt + 1,) + P.space_shape())
     mk.mk_march(p.handle, P.u0, u)
     ref = O.theta_march(P.dim, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)

@@ -185,6 +185,22 @@ def heat2d_adjoint(seed: int = 3) -> Problem:
                    tol=1e-12, precision="fp64", u_target=target)
 
 
+def heat2d_alternate(levels: int = 7, seed: int = 5, precision: str = "mixed") -> Problem:
+    """The multilevel-count workload of Table 3 (Sec. 4.2): 2D 192x192, theta=1/2,
+    n_t=2^11, C = 3 tau dt / h^2 = 0.16 (dt = 1.43e-6, T = 2.93e-3), g=0, alternate
+    time-space coarsening (three time coarsenings, then space and time alternately), 16
+    decoupled slabs, 2 inner iterations (1 on the level above the coarsest), tol 1e-6."""
+    rng = np.random.default_rng(seed)
+    n, nt = 192, 2048
+    dt = 0.16 / (3.0 * (n + 1) ** 2)
+    kinds = ("TTT" + "ST" * 4)[:levels - 1]
+    sched = Schedule(nu=tuple(1 if k == "S" else 2 for k in kinds),
+                     space=tuple(k == "S" for k in kinds),
+                     m_inner=tuple([2] * (levels - 3) + [1]), n_cgs=16)
+    return Problem(f"heat2d_192x192_nt2048_C0.16_L{levels}", 2, n, n, nt, nt * dt, 1.0, 0.5,
+                   smooth_modes_2d(rng, n, n), None, sched, tol=1e-6, precision=precision)
+
+
 def batched_problems(seed: int = 4, count_1d: int = 48, count_2d: int = 16) -> List[Problem]:
     """Uneven problems: 1D n in {63..2047}, n_t in {256..8192}; 2D side in {63..255},
     n_t in {128..1024}; tau log-uniform in [0.1, 10]; theta in {1/2, 1}."""
