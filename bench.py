@@ -257,6 +257,24 @@ def bench_alternate(mk, torch, dev, steps=2):
     return out
 
 
+def profile_2d():
+    """A few outer iterations of the 2D workload's solver on 255 x 255 x 513 (33.4 M points,
+    double-float vectors of 267 MB: larger than L2, a few GB on the device in all)."""
+    import torch
+    import paper_2401_00228_gb300 as mk
+    n, nt = 255, 512
+    P = W.heat2d_large()
+    s = P.schedule
+    u0 = torch.from_numpy(P.u0).cuda()
+    u = torch.empty((nt + 1, n, n), dtype=torch.float64, device="cuda")
+    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=s.n_cgs,
+                     tol=1e-12, restart=10, max_iters=3, precision="mixed")
+    with mk.Problem(2, n, P.tau, P.theta, P.dt, nt, None, ny=n) as p:
+        info = mk.mk_solve(p.handle, u0, u, o, allow_not_converged=True)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile_2d": "heat2d_255x255_nt512", "iterations": int(info.iterations)}))
+
+
 def bench_batch(mk, torch, dev, count_1d=12, count_2d=4, max_iters=600):
     """16 members of the uneven batched workload (1D n 63..2047 x n_t 256..8192, 2D side
     63..255 x n_t 128..1024, tau log-uniform [0.1, 10], theta in {1/2, 1}; mixed, tol 1e-10):
@@ -318,7 +336,14 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="run one warm-up solve and one solve of the workload, no timing (the "
                          "command that ncu captures)")
+    ap.add_argument("--profile-2d", action="store_true",
+                    help="run a short 2D solve (255 x 255, n_t = 512, the 2D workload's schedule, "
+                         "restart 10, 3 outer iterations), no timing: the small case on which ncu "
+                         "captures the 2D level-1 transfer kernels")
     args = ap.parse_args()
+    if args.profile_2d:
+        profile_2d()
+        return
     args.warmup = max(args.warmup, 3)
     world, rank, local = _dist()
 

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) k_residual_df(Geom g, double a, double b,
 void launch_residual_df(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
                         const double *u, float2 *r, const ReduceScratch &rs, int slot, KState ks,
                         int epi, cudaStream_t s) {
-    int kc = choose_kc(g.npts(), g.nt + 1);
+    int kc = cap_kc(choose_kc(g.npts(), g.nt + 1), g.nt + 1, g.dim, g.nx, g.ny);
     int nch = (g.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(g.dim, g.nx, g.ny, nch);
     prof_begin(s);
@@ -387,7 +387,7 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
                       const float *Xc, int mc, int64_t xc_stride, const double *yc, float *x,
                       float2 *wout, const int *done, cudaStream_t s, const float2 *uniform_ab,
                       bool uniform_square) {
-    int kc = choose_kc(gf.npts(), gf.nt + 1);
+    int kc = cap_kc(choose_kc(gf.npts(), gf.nt + 1), gf.nt + 1, gf.dim, gf.nx, gf.ny);
     int nch = (gf.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(gf.dim, gf.nx, gf.ny, nch);
     const int hb = has_b ? 1 : 0;

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) k_apply_2d(Geom g, Tc a, Tc b, SpaceOp<Tc
 template <typename Tin, typename Tout, typename Tc>
 void launch_apply(const Geom &g, const Weights &w, SpaceOp<Tc> L, const Tin *x, Tout *out,
                   cudaStream_t s) {
-    int kc = choose_kc(g.npts(), g.nt + 1);
+    int kc = cap_kc(choose_kc(g.npts(), g.nt + 1), g.nt + 1, g.dim, g.nx, g.ny);
     int nch = (g.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(g.dim, g.nx, g.ny, nch);
     if (g.dim == 1)
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) k_residual(Geom g, double a, double b, Sp
 void launch_residual(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
                      const double *u, double *r, const ReduceScratch &rs, int slot, KState ks,
                      int epi, cudaStream_t s) {
-    int kc = choose_kc(g.npts(), g.nt + 1);
+    int kc = cap_kc(choose_kc(g.npts(), g.nt + 1), g.nt + 1, g.dim, g.nx, g.ny);
     int nch = (g.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(g.dim, g.nx, g.ny, nch);
     prof_begin(s);
@@ -409,6 +409,16 @@ void launch_restrict(const Geom &gf, const Geom &gc, int nu, bool space, const W
                      const ReduceScratch &rs, int slot, KState ks_c, const int *done,
                      cudaStream_t s) {
     int kc = choose_kc(gc.npts() * (space ? (gf.dim == 2 ? 4 : 2) : 1) * nu, gc.nt + 1);
+    if (gf.dim == 2) {
+        // a thread walks its chunk of coarse steps serially: enough chunks for one full wave
+        // of 2048 threads per SM, but at least four fine steps per chunk (the fine step before
+        // each chunk is read again)
+        const int64_t want = (int64_t)g_num_sms * 2048;
+        const int64_t k2 = (gc.npts() * (int64_t)(gc.nt + 1)) / want;
+        const int kmin = (4 + nu - 1) / nu;
+        if (k2 < kc) kc = k2 < kmin ? kmin : (int)k2;
+    }
+    kc = cap_kc(kc, gc.nt + 1, gf.dim, gc.nx, gc.ny);
     int nch = (gc.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(gf.dim, gc.nx, gc.ny, nch);
     Tc a = (Tc)w.a, b = (Tc)w.b, mu = (Tc)w.mu;
@@ -617,7 +627,7 @@ void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Wei
                    SpaceOp<Tc> L, const Tv *v, const double *sigma, const Tz *Xc, int mc,
                    int64_t xc_stride, const double *yc, Tx *x, Tw *wout, const int *done,
                    cudaStream_t s) {
-    int kc = choose_kc(gf.npts(), gf.nt + 1);
+    int kc = cap_kc(choose_kc(gf.npts(), gf.nt + 1), gf.nt + 1, gf.dim, gf.nx, gf.ny);
     int nch = (gf.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(gf.dim, gf.nx, gf.ny, nch);
     Tc a = (Tc)w.a, b = (Tc)w.b;
@@ -738,7 +748,7 @@ void launch_adjoint_grads(const Geom &g, double theta, double dt, double tau, Sp
                           const double *y, const double *b, const double *upad, double *lam,
                           double *grad_u0, double *grad_g, const ReduceScratch &rs, KState ks,
                           cudaStream_t s) {
-    int kc = choose_kc(g.npts(), g.nt + 1);
+    int kc = cap_kc(choose_kc(g.npts(), g.nt + 1), g.nt + 1, g.dim, g.nx, g.ny);
     int nch = (g.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(g.dim, g.nx, g.ny, nch);
     double bw = (1.0 - theta) * dt;

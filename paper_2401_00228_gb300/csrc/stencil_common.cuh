@@ -77,6 +77,20 @@ static inline Launch2 point_launch(int dim, int nx, int ny, int nchunks) {
     return L;
 }
 
+// Smallest chunk depth >= kc for which the point_launch grid over nsteps steps has at most
+// 60000 blocks (the reduction partials hold 65536; this also keeps a 2D grid's z extent in
+// range).  choose_kc estimates the blocks per chunk from the point count, which undercounts
+// thin 2D grids (32 x 8 blocks); this counts them exactly.
+static inline int cap_kc(int kc, int nsteps, int dim, int nx, int ny) {
+    const Launch2 one = point_launch(dim, nx, ny, 1);
+    const int64_t per = (int64_t)one.grid.x * one.grid.y;
+    if (kc < 1) kc = 1;
+    const int64_t need = (per * (int64_t)nsteps + 59999) / 60000;
+    if (need > kc) kc = (int)need;
+    while (per * (((int64_t)nsteps + kc - 1) / kc) > 60000) ++kc;
+    return kc;
+}
+
 template <int DIM>
 __device__ __forceinline__ bool point_index(int &i, int &j, int &chunk) {
     i = blockIdx.x * blockDim.x + threadIdx.x;

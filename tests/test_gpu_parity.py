@@ -248,6 +248,23 @@ def test_residual(case):
     assert abs(nrm - np.linalg.norm(ref)) <= 1e-12 * np.linalg.norm(ref)
 
 
+def test_residual_thin_2d_grid():
+    """A 1 x 4000 grid over 8192 steps: 500 blocks of 32 x 8 threads per time chunk, so the
+    chunk depth must grow until the launch stays within the reduction's 65536 partials."""
+    nx, ny, nt = 1, 4000, 8192
+    P = W.custom(2, nx, nt, 1e-3, 1.0, 0.5, W.Schedule((2,), (False,), (), 16), seed=19, ny=ny)
+    lv = O.build_levels(2, nx, ny, nt, P.tau, P.theta, P.dt, (), (), "one")[0]
+    rng = np.random.default_rng(30)
+    f = rng.standard_normal(lv.shape())
+    u = rng.standard_normal(lv.shape())
+    r = np.empty_like(f)
+    with _prob(P) as p:
+        nrm = mk.mk_op_residual(p.handle, f, u, r)
+    ref = f - lv.apply_A(u)
+    assert _rel(r, ref) <= 1e-12
+    assert abs(nrm - np.linalg.norm(ref)) <= 1e-12 * np.linalg.norm(ref)
+
+
 # --------------------------------------------------------------------------- end to end
 @pytest.mark.parametrize("precision,bound", [("fp64", 1e-10), ("mixed", 1e-8)])
 def test_solve_small(case, precision, bound):
