@@ -117,6 +117,34 @@ __device__ __forceinline__ Tx x2d_vload(const Tv *p) { return (Tx)*p; }
 template <>
 __device__ __forceinline__ float x2d_vload<float2, float>(const float2 *p) { return p->x; }
 
+// the four values v[0..3] (16-byte aligned: the first point's index is a multiple of 4) as
+// the arithmetic type; a double-float element contributes its leading float
+template <typename Tv, typename Tx>
+__device__ __forceinline__ void x2d_vload4(const Tv *p, Tx (&o)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = x2d_vload<Tv, Tx>(p + q);
+}
+template <>
+__device__ __forceinline__ void x2d_vload4<float2, float>(const float2 *p, float (&o)[4]) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    const float4 b = *reinterpret_cast<const float4 *>(p + 2);
+    o[0] = a.x; o[1] = a.z; o[2] = b.x; o[3] = b.z;
+}
+template <>
+__device__ __forceinline__ void x2d_vload4<float, float>(const float *p, float (&o)[4]) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+template <typename Tx>
+__device__ __forceinline__ void x2d_store4(Tx *p, const Tx (&o)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p[q] = o[q];
+}
+template <>
+__device__ __forceinline__ void x2d_store4<float>(float *p, const float (&o)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+
 template <bool SPACE, typename Tv, typename Tz, typename Tx>
 __global__ void __launch_bounds__(256) k_interp_x2d(Geom gf, Geom gc, int nu,
                                                     const Tv *__restrict__ v,
@@ -136,7 +164,8 @@ __global__ void __launch_bounds__(256) k_interp_x2d(Geom gf, Geom gc, int nu,
     const Tz *crow = Xc + gc.at(K, J, 0);
     const Tx sig = sigma ? (Tx)(*sigma) : (Tx)1;
     const int64_t idx = gf.at(k, j, i0);
-    Tx out[4];
+    Tx vin[4], out[4];
+    x2d_vload4<Tv, Tx>(v + idx, vin);
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const int i = i0 + p;
@@ -149,10 +178,9 @@ __global__ void __launch_bounds__(256) k_interp_x2d(Geom gf, Geom gc, int nu,
                 for (int m = 0; m < mc; ++m) zt += (Tx)yc[m] * (Tx)crow[I + m * xc_stride];
             }
         }
-        out[p] = (i < gf.nx) ? sig * x2d_vload<Tv, Tx>(v + idx + p) - zt : (Tx)0;
+        out[p] = (i < gf.nx) ? sig * vin[p] - zt : (Tx)0;
     }
-#pragma unroll
-    for (int p = 0; p < 4; ++p) x[idx + p] = out[p];
+    x2d_store4<Tx>(x + idx, out);
 }
 
 // one point per thread (32 x 8 blocks) / four points per thread (k_interp_x2d)
