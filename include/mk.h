@@ -193,7 +193,11 @@ mk_status mk_solve_rhs(mk_problem *p, const double *f, const mk_solve_opts *opts
 /*
  * mk_march -- sequential theta-march on the GPU, Eq. (timemarch): block forward
  * substitution of A_h u = f_h, FP64, one step after another (the baseline the MK
- * solve is compared with).  u_out: (nt+1) x n.
+ * solve is compared with).  u_out: (nt+1) x n.  Each step is a direct solve of
+ * (I - theta dt A_n) u_k = rhs: a tridiagonal solve in 1D (nx <= 4096), a sine-transform
+ * solve in 2D (FFT in a direction whose n + 1 is a power of two up to 2048, the dense sine
+ * matrix in one with n <= 1024).  Larger grids: MK_ERR_INVALID.  Allocates its staging
+ * and step buffers per call; returns after the stream has finished the march.
  */
 mk_status mk_march(mk_problem *p, const double *u0, double *u_out, void *stream);
 
