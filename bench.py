@@ -176,7 +176,7 @@ def bench_2d(mk, torch, dev, args, steps=2):
     P = W.heat2d_large()
     s = P.schedule
     o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=s.n_cgs,
-                     tol=args.tol, restart=args.restart, precision="mixed", orth=args.orth,
+                     tol=args.tol_2d, restart=args.restart, precision="mixed", orth=args.orth,
                      autotune=not args.no_autotune)
     u0 = torch.from_numpy(P.u0).to(dev)
     u = torch.empty((P.nt + 1,) + P.space_shape(), dtype=torch.float64, device=dev)
@@ -210,7 +210,7 @@ def bench_2d(mk, torch, dev, args, steps=2):
     return {"s": statistics.mean(ts), "iterations": int(info.iterations), "kernel_classes": classes,
             "march_gpu_s": statistics.mean(tm), "max_rel_diff_vs_march": march_err,
             "rel_residual": info.rel_residual, "points": int(P.nx * P.ny * (P.nt + 1)),
-            "workload": "heat2d_255x255_nt1024_theta0.5_T0.05_L4_nu2_2x2space", "tol": args.tol}
+            "workload": "heat2d_255x255_nt1024_theta0.5_T0.05_L4_nu2_2x2space", "tol": args.tol_2d}
 
 
 def bench_alternate(mk, torch, dev, steps=2):
@@ -325,9 +325,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mk", choices=["mk", "reference"])
-    ap.add_argument("--tol", type=float, default=1e-9,
-                    help="relative residual target; 1e-9 gives a max error ~2e-10 on this workload "
-                         "(checked against the oracle in the same run)")
+    ap.add_argument("--tol", type=float, default=1e-8,
+                    help="relative residual target of the 1D solves; on this workload 1e-8 gives a "
+                         "max error of 2.5e-9 against the oracle (mixed; 3.4e-9 FP64), below the "
+                         "metric's 1e-8, checked in the same run")
+    ap.add_argument("--tol-2d", type=float, default=1e-9,
+                    help="relative residual target of the 2D solve: its error is ~4x its residual "
+                         "(1e-9 gives 4.2e-9 against the GPU march, 3e-9 gives 1.7e-8)")
     ap.add_argument("--restart", type=int, default=40)
     ap.add_argument("--orth", type=int, default=0, help="Gram-Schmidt passes: 0 one, 1 conditional, 2 two")
     ap.add_argument("--no-aux", action="store_true", help="skip the secondary paths")
@@ -528,6 +532,9 @@ def main():
             "march_gpu_fp64": {"s": statistics.mean(tm) / 1e3, "max_rel_err": O.max_rel_error(u_march, ref)},
             "oracle_cpu": {"s": statistics.median(tc)},
         })
+        # the metric is time to a solution within 1e-8 max relative error of the oracle
+        line["error_target"] = 1e-8
+        line["error_target_met"] = bool(line["paths"]["mk_mixed"]["max_rel_err"] <= 1e-8)
     prob.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
