@@ -45,6 +45,17 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over all ranks (the job's time is its slowest replica's); the value
+    itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -420,11 +431,7 @@ def main():
     clocks.start()
     t_mixed, inf_mixed, launches = timed(o_mixed, args.steps, args.warmup)
     clk = clocks.stop()
-    ms_mixed = statistics.mean(t_mixed)
-    if dist is not None:
-        t = torch.tensor([ms_mixed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_mixed = float(t.item())
+    ms_mixed = max_over_ranks(statistics.mean(t_mixed), dist, dev)
     u_mixed = u_dev.cpu().numpy().copy()
 
     line = {"metric": METRIC, "value": ms_mixed / 1e3, "unit": "s", "n_gpus": world,
