@@ -158,6 +158,8 @@ def test_pairs_give_sqrt2_spacing():
     (1, 7, 1, 6, 2, False, 0.5), (1, 7, 1, 6, 3, False, 1.0), (1, 7, 1, 8, 4, False, 0.3),
     (1, 8, 1, 6, 2, True, 0.5), (1, 9, 1, 6, 3, True, 1.0), (1, 5, 1, 4, 2, True, 0.0),
     (2, 4, 3, 4, 2, False, 0.5), (2, 5, 4, 4, 2, True, 1.0), (2, 3, 5, 6, 3, True, 0.7),
+    # space-only coarsenings of the alternate schedule (Sec. 4.2): nu = 1
+    (1, 8, 1, 5, 1, True, 0.5), (1, 7, 1, 3, 1, True, 1.0), (2, 5, 4, 3, 1, True, 0.5),
 ])
 def test_galerkin_is_modified_theta_scheme(dim, nx, ny, nt, nu, space, theta):
     """Y^T A_h Z (dense, brute force) equals the next level built as a theta-scheme with
@@ -181,10 +183,11 @@ def test_printed_coarse_formula_differs_off_half():
         assert np.allclose(printed, galerkin) == agree
 
 
-@pytest.mark.parametrize("dim,space", [(1, False), (1, True), (2, True)])
-def test_restrict_interpolate_are_dense_Y_Z(dim, space):
+@pytest.mark.parametrize("dim,space,nu", [(1, False, 3), (1, True, 3), (2, True, 2), (1, True, 1),
+                                          (2, True, 1)])
+def test_restrict_interpolate_are_dense_Y_Z(dim, space, nu):
     rng = np.random.default_rng(3)
-    nx, ny, nt, nu = (7, 1, 6, 3) if dim == 1 else (5, 3, 4, 2)
+    nx, ny, nt = (7, 1, 6) if dim == 1 else (5, 3, 4)
     lv = O.build_levels(dim, nx, ny, nt, 1.0, 0.5, 0.01, (nu,), (space,), "one")
     Y, Z = O.dense_transfers(lv[0], nu, space)
     v = rng.standard_normal(lv[0].shape())
