@@ -22,7 +22,7 @@ __all__ = ["mk_default_opts", "mk_create_problem", "mk_set_source", "mk_destroy"
            "mk_op_residual", "mk_op_residual_noalloc", "mk_op_restrict", "mk_op_interp_correct", "mk_op_coarsest",
            "mk_op_precond", "mk_op_orthogonalize", "mk_op_lsq", "mk_kernel_launch_count",
            "mk_create_batch", "mk_solve_batch", "mk_destroy_batch", "Batch",
-           "make_opts", "Problem", "HeatSolve", "MKError", "lib"]
+           "make_opts", "Problem", "HeatSolve", "MKError", "lib", "solve"]
 
 
 def lib():
@@ -334,6 +334,35 @@ class Problem:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def solve(u0, g=None, tau: float = 1.0, theta: float = 1.0, dt: float = 0.0, nt: int = 0,
+          opts: Optional[mk_solve_opts] = None, **kw):
+    """One call: the solution of Eq. (finesys) for initial state u0 ((nx,) in 1D, (ny, nx) in
+    2D) and source g ((nt+1, ...) or None) by the MK solver, as an (nt+1, ...) array of the
+    same kind as u0 (a torch tensor on u0's device, or a numpy array).  The problem is created
+    and freed inside; options from `opts` or make_opts(**kw)."""
+    if nt < 1 or not dt > 0.0:
+        raise ValueError("nt >= 1 and dt > 0 are required")
+    shape = tuple(u0.shape)
+    if len(shape) not in (1, 2):
+        raise ValueError("u0 must have shape (nx,) or (ny, nx)")
+    dim = len(shape)
+    nx, ny = shape[-1], (shape[0] if dim == 2 else 1)
+    o = make_opts(**kw) if opts is None else opts
+    out_shape = (nt + 1,) + shape
+    try:
+        import torch
+        is_torch = isinstance(u0, torch.Tensor)
+    except ImportError:
+        is_torch = False
+    if is_torch:
+        u = torch.empty(out_shape, dtype=torch.float64, device=u0.device)
+    else:
+        u = np.empty(out_shape, dtype=np.float64)
+    with Problem(dim, nx, tau, theta, dt, nt, g, ny=ny) as p:
+        mk_solve(p.handle, u0, u, o)
+    return u
 
 
 class HeatSolve:

@@ -439,3 +439,20 @@ def test_full_size_2d_workload_sampled():
     lv = O.build_levels(2, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, (), (), "one")[0]
     f = O.assemble_rhs(P.u0, None, P.nt, P.theta, P.dt)
     assert np.linalg.norm(f - lv.apply_A(u)) / np.linalg.norm(f) <= 1e-11
+
+
+def test_one_call_solve_matches_problem_solve():
+    """mk.solve (problem created and freed inside) gives the same solution as mk_solve on an
+    explicit problem, for numpy (host) and torch (device) inputs."""
+    torch = pytest.importorskip("torch")
+    P = SMALL["2d_15x13_TS"]()
+    o = _opts(P.schedule, precision="fp64")
+    with _prob(P) as p:
+        ref = np.empty((P.nt + 1,) + P.space_shape())
+        mk.mk_solve(p.handle, P.u0, ref, o)
+    u = mk.solve(P.u0, P.g, tau=P.tau, theta=P.theta, dt=P.dt, nt=P.nt, opts=o)
+    assert isinstance(u, np.ndarray) and np.array_equal(u, ref)
+    dev = torch.device("cuda:0")
+    ut = mk.solve(torch.from_numpy(P.u0).to(dev), torch.from_numpy(P.g).to(dev), tau=P.tau,
+                  theta=P.theta, dt=P.dt, nt=P.nt, opts=o)
+    assert ut.device == dev and np.array_equal(ut.cpu().numpy(), ref)
