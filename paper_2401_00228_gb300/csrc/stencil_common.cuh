@@ -154,7 +154,15 @@ __global__ void __launch_bounds__(256) k_interp_x2d(Geom gf, Geom gc, int nu,
                                                     const double *__restrict__ yc,
                                                     Tx *__restrict__ x,
                                                     const int *__restrict__ done) {
-    if (done && *done) return;
+    if (done && *done) return;   // the same flag for every thread of the block
+    // sigma and the coarse weights y_m, converted once per block (a double -> float
+    // conversion issues at the FP64 rate)
+    __shared__ Tx s_w[MK_MAX_INNER + 1];
+    const int nm = yc ? (mc < MK_MAX_INNER ? mc : MK_MAX_INNER) : 0;
+    const int t = threadIdx.x + blockDim.x * threadIdx.y;
+    if (t == 0) s_w[0] = sigma ? (Tx)(*sigma) : (Tx)1;
+    else if (t <= nm) s_w[t] = (Tx)yc[t - 1];
+    __syncthreads();
     const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
@@ -162,7 +170,7 @@ __global__ void __launch_bounds__(256) k_interp_x2d(Geom gf, Geom gc, int nu,
     const int K = (k == 0) ? 0 : (k - 1) / nu + 1;
     const int J = SPACE ? (j >> 1) : j;
     const Tz *crow = Xc + gc.at(K, J, 0);
-    const Tx sig = sigma ? (Tx)(*sigma) : (Tx)1;
+    const Tx sig = s_w[0];
     const int64_t idx = gf.at(k, j, i0);
     Tx vin[4], out[4];
     x2d_vload4<Tv, Tx>(v + idx, vin);
@@ -175,7 +183,7 @@ __global__ void __launch_bounds__(256) k_interp_x2d(Geom gf, Geom gc, int nu,
             if (!yc) {
                 zt = (Tx)crow[I];
             } else {
-                for (int m = 0; m < mc; ++m) zt += (Tx)yc[m] * (Tx)crow[I + m * xc_stride];
+                for (int m = 0; m < nm; ++m) zt += s_w[1 + m] * (Tx)crow[I + m * xc_stride];
             }
         }
         out[p] = (i < gf.nx) ? sig * vin[p] - zt : (Tx)0;

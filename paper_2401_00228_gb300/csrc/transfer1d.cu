@@ -270,10 +270,16 @@ __global__ void __launch_bounds__(TT) k_interp_1d_t(Geom gf, Geom gc, Tc a, Tc b
     const int nf = gf.nx;
     const bool act = i0 < nf;
     const int k0 = blockIdx.y * KC;
+    // sigma and the coarse weights, converted once per block
+    __shared__ Tx s_w[CR::NY + 1];
+    if (threadIdx.x == 0) s_w[0] = sigma ? (Tx)(*sigma) : (Tx)1;
+    else if (threadIdx.x <= CR::NY)
+        s_w[threadIdx.x] = (yc && (int)threadIdx.x - 1 < mc) ? (Tx)yc[threadIdx.x - 1] : (Tx)0;
+    __syncthreads();
     Tx y[CR::NY];
 #pragma unroll
-    for (int m = 0; m < CR::NY; ++m) y[m] = (yc && m < mc) ? (Tx)yc[m] : (Tx)0;
-    const Tx sig = sigma ? (Tx)(*sigma) : (Tx)1;
+    for (int m = 0; m < CR::NY; ++m) y[m] = s_w[1 + m];
+    const Tx sig = s_w[0];
     // fine rows
     Tx vv[R][PT], vl[R], vr[R];
 #pragma unroll
@@ -353,10 +359,16 @@ __global__ void __launch_bounds__(TT) k_interp_df_1d_t(Geom gf, Geom gc,
     const int nf = gf.nx;
     const bool act = i0 < nf;
     const int k0 = blockIdx.y * KC;
+    // sigma and the coarse weights, converted from FP64 once per block
+    __shared__ float s_w[CR::NY + 1];
+    if (threadIdx.x == 0) s_w[0] = sigma ? (float)(*sigma) : 1.f;
+    else if (threadIdx.x <= CR::NY)
+        s_w[threadIdx.x] = (yc && (int)threadIdx.x - 1 < mc) ? (float)yc[threadIdx.x - 1] : 0.f;
+    __syncthreads();
     float y[CR::NY];
 #pragma unroll
-    for (int m = 0; m < CR::NY; ++m) y[m] = (yc && m < mc) ? (float)yc[m] : 0.f;
-    const float sig = sigma ? (float)(*sigma) : 1.f;
+    for (int m = 0; m < CR::NY; ++m) y[m] = s_w[1 + m];
+    const float sig = s_w[0];
     float vv[R][PT], vl[R], vr[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
