@@ -30,6 +30,12 @@ Multilevel Krylov Methods: A Prototype"):
   iterations (zero initial guess) preconditioned by the next level.
 * Algorithm 2: FGMRES (Arnoldi with modified Gram-Schmidt, least squares on
   the Hessenberg matrix, u = u0 + X_J y_J).
+* Sec. 3.2, Eqs. (mgritY), (mgritZ), with Eq. (coarsemat): the comparison
+  two-level method with MGRIT intergrid operators.  Y^T injects the coarse
+  time points (steps 0, nu, 2 nu, ...), Z is the ideal interpolation
+  [-(A_ff)^{-1} A_fc; I_c], and A_H is not the Galerkin product but the
+  theta-scheme with the same theta and the larger step Delta T = nu dt
+  (Psi_n, Phi_n of Eq. (timemarchdT)).  Two-level only, time coarsening only.
 
 Functions that have a plain definition (the march, the operators, the dense
 builders) are written as that definition.  The MK cycle and FGMRES follow the
@@ -336,6 +342,53 @@ def interpolate(fine: Level, nu: int, space: bool, vt: np.ndarray) -> np.ndarray
     return out
 
 
+def restrict_inject(fine: Level, nu: int, v: np.ndarray) -> np.ndarray:
+    """Y^T v for Y of Eq. (mgritY): the coarse time points, steps 0, nu, 2 nu, ..., n_t."""
+    return v[::nu].copy()
+
+
+def interpolate_ideal(fine: Level, nu: int, vt: np.ndarray) -> np.ndarray:
+    """Z vt for the ideal interpolation of Eq. (mgritZ), Z = [-(A_ff)^{-1} A_fc; I_c].
+    Coarse points take vt: x_{nu K} = vt_K.  The fine points nu K + 1 .. nu K + nu - 1 of
+    interval K solve A_ff y = -A_fc vt: A_ff is lower block bidiagonal (psi on the
+    diagonal, -phi below) and A_fc couples the first of them to x_{nu K} by -phi, so
+    psi x_{nu K + i} = phi x_{nu K + i - 1}, i = 1 .. nu - 1 (the homogeneous march)."""
+    out = np.empty((fine.nt + 1,) + vt.shape[1:])
+    out[::nu] = vt
+    ns = fine.space_shape()
+    if nu > 1:
+        psi = np.eye(int(np.prod(ns))) - fine.a * fine.spatial_dense()
+        lu = sla.lu_factor(psi)
+        for K in range(fine.nt // nu):
+            for i in range(1, nu):
+                k = nu * K + i
+                prev = out[k - 1]
+                rhs = prev + fine.b * fine.apply_L(prev)
+                out[k] = sla.lu_solve(lu, rhs.reshape(-1)).reshape(ns)
+    return out
+
+
+def coarse_theta_level(fine: Level, nu: int, theta: float, mu_mode: str = "lambda_max",
+                       mu_value: Optional[float] = None) -> Level:
+    """The coarse time-grid matrix of Eq. (coarsemat): the theta-scheme with the same theta
+    and step Delta T = nu dt, Psi_n = I - theta Delta T A_n, Phi_n = I + (1-theta) Delta T A_n
+    (Eq. (timemarchdT)); not the Galerkin product Y^T A_h Z."""
+    if fine.nt % nu:
+        raise ValueError("n_t not divisible by the coarsening factor")
+    dt = fine.a + fine.b            # a = theta dt, b = (1 - theta) dt on the fine level
+    DT = nu * dt
+    lv = Level(fine.dim, fine.nt // nu, theta * DT, (1.0 - theta) * DT, fine.Lx, fine.Ly)
+    if mu_mode == "lambda_max":
+        lv.mu = lv.lambda_max()
+    elif mu_mode == "one":
+        lv.mu = 1.0
+    elif mu_mode == "value":
+        lv.mu = float(mu_value)
+    else:
+        raise ValueError(mu_mode)
+    return lv
+
+
 # -----------------------------------------------------------------------------
 # Coarsest level: perturbed, decoupled matrix (Sec. 3.3.2, Eq. (Qhtilde)).
 # -----------------------------------------------------------------------------
@@ -373,14 +426,23 @@ class Hierarchy:
     space: Tuple[bool, ...]
     m_inner: Tuple[int, ...]   # fixed FGMRES iterations on levels 2..L-1
     n_cgs: int
+    transfer: str = "mk"       # "mk" (Sec. 3.2 block sums) or "mgrit" (Eqs. (mgritY), (mgritZ))
 
 
 def make_hierarchy(dim, nx, ny, nt, tau, theta, dt, nu, space, m_inner, n_cgs,
-                   mu_mode="lambda_max", mu_value=None) -> Hierarchy:
-    lv = build_levels(dim, nx, ny, nt, tau, theta, dt, nu, space, mu_mode, mu_value)
+                   mu_mode="lambda_max", mu_value=None, transfer="mk") -> Hierarchy:
+    if transfer == "mgrit":
+        if len(nu) != 1 or any(space):
+            raise ValueError("the MGRIT comparison is two-level with time coarsening only")
+        lv = build_levels(dim, nx, ny, nt, tau, theta, dt, (), (), mu_mode, mu_value)
+        lv.append(coarse_theta_level(lv[0], nu[0], theta, mu_mode, mu_value))
+    elif transfer == "mk":
+        lv = build_levels(dim, nx, ny, nt, tau, theta, dt, nu, space, mu_mode, mu_value)
+    else:
+        raise ValueError(transfer)
     if len(m_inner) != max(0, len(lv) - 2):
         raise ValueError("m_inner must give one count per intermediate level")
-    return Hierarchy(lv, tuple(nu), tuple(space), tuple(m_inner), n_cgs)
+    return Hierarchy(lv, tuple(nu), tuple(space), tuple(m_inner), n_cgs, transfer)
 
 
 def coarse_solve(H: Hierarchy, l: int, vhat: np.ndarray) -> np.ndarray:
@@ -395,9 +457,15 @@ def precondition(H: Hierarchy, l: int, v: np.ndarray) -> np.ndarray:
     """x = Q_l v by substeps 4.1-4.5."""
     lv = H.levels[l]
     s = lv.apply_A(v)                                    # 4.1
-    vhat = restrict(lv, H.nu[l], H.space[l], s - lv.mu * v)   # 4.2
+    if H.transfer == "mgrit":
+        vhat = restrict_inject(lv, H.nu[l], s - lv.mu * v)   # 4.2, Y of Eq. (mgritY)
+    else:
+        vhat = restrict(lv, H.nu[l], H.space[l], s - lv.mu * v)   # 4.2
     vtil = coarse_solve(H, l, vhat)                      # 4.3
-    t = interpolate(lv, H.nu[l], H.space[l], vtil)       # 4.4
+    if H.transfer == "mgrit":
+        t = interpolate_ideal(lv, H.nu[l], vtil)         # 4.4, Z of Eq. (mgritZ)
+    else:
+        t = interpolate(lv, H.nu[l], H.space[l], vtil)   # 4.4
     return v - t                                         # 4.5
 
 
@@ -527,6 +595,40 @@ def dense_transfers(fine: Level, nu: int, space: bool) -> Tuple[np.ndarray, np.n
             Z[k * n:(k + 1) * n, K * m:(K + 1) * m] = Zs
             Y[k * n:(k + 1) * n, K * m:(K + 1) * m] = Ys
     return Y, Z
+
+
+def dense_transfers_mgrit(fine: Level, nu: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Dense Y, Z of Eqs. (mgritY), (mgritZ) from the C/F partition of A_h: the coarse
+    (C) points are the blocks of steps 0, nu, 2 nu, ...; Y = [0; I_c] and
+    Z = [-(A_ff)^{-1} A_fc; I_c], both scattered back to the natural ordering."""
+    n = int(np.prod(fine.space_shape()))
+    A = dense_A(fine)
+    N = A.shape[0]
+    cblocks = list(range(0, fine.nt + 1, nu))
+    c = np.concatenate([np.arange(k * n, (k + 1) * n) for k in cblocks])
+    f = np.setdiff1d(np.arange(N), c)
+    Y = np.zeros((N, c.size))
+    Y[c, np.arange(c.size)] = 1.0
+    Z = Y.copy()
+    if f.size:
+        Z[f, :] = -np.linalg.solve(A[np.ix_(f, f)], A[np.ix_(f, c)])
+    return Y, Z
+
+
+def dense_coarse_theta(fine: Level, nu: int, theta: float) -> np.ndarray:
+    """A_H of Eq. (coarsemat) as a dense matrix: I, then Psi_n on the diagonal and -Phi_n
+    below, Psi_n = I - theta nu dt A_n, Phi_n = I + (1-theta) nu dt A_n."""
+    n = int(np.prod(fine.space_shape()))
+    An = fine.spatial_dense()
+    DT = nu * (fine.a + fine.b)
+    I = np.eye(n)
+    nT = fine.nt // nu
+    AH = np.zeros(((nT + 1) * n, (nT + 1) * n))
+    AH[:n, :n] = I
+    for K in range(1, nT + 1):
+        AH[K * n:(K + 1) * n, K * n:(K + 1) * n] = I - theta * DT * An
+        AH[K * n:(K + 1) * n, (K - 1) * n:K * n] = -(I + (1.0 - theta) * DT * An)
+    return AH
 
 
 def dense_decoupled(level: Level, n_cgs: int) -> np.ndarray:
