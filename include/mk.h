@@ -93,7 +93,22 @@ typedef struct mk_solve_opts {
                             variants on its own buffers and keep the fastest (a few ms, once per
                             hierarchy); 0: built-in heuristics (default; bitwise reproducible
                             across processes) */
+    int32_t transfer;    /* intergrid operators of the two-level method (Sec. 3.2):
+                            MK_TRANSFER_MK (default): Y, Z of Eq. (blockYZ) -- sums of nu steps,
+                            optional space agglomeration -- and Galerkin coarse levels
+                            (Eqs. (timecoarse1)-(timecoarse3)).
+                            MK_TRANSFER_MGRIT: the paper's comparison method -- Y of Eq. (mgritY)
+                            (injection of the coarse time points 0, nu, 2 nu, ...), Z of
+                            Eq. (mgritZ) (ideal interpolation: the fine steps between two coarse
+                            points follow psi x_k = phi x_{k-1} from the coarse value) and the
+                            non-Galerkin coarse matrix of Eq. (coarsemat) (the theta-scheme with
+                            step nu dt).  Requires dim = 1, levels = 2, space[0] = 0,
+                            nu[0] >= 2 and n_t / nu[0] <= 65535; MK_ERR_INVALID otherwise.
+                            mk_op_restrict and mk_op_interp_correct take MK_TRANSFER_MK only. */
 } mk_solve_opts;
+
+#define MK_TRANSFER_MK 0
+#define MK_TRANSFER_MGRIT 1
 
 typedef struct mk_solve_info {
     int32_t iterations;      /* outer FGMRES iterations */

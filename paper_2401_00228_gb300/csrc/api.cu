@@ -660,6 +660,7 @@ mk_status mk_op_restrict(mk_problem *p, const mk_solve_opts *opts, int32_t level
     Hierarchy *H = nullptr;
     mk_solve_opts o;
     CKS(get_level(p, opts, level, H, o));
+    if (o.transfer != MK_TRANSFER_MK) return MK_ERR_INVALID;
     if (level >= (int)H->lv.size()) return MK_ERR_INVALID;
     Level &L = *H->lv[level - 1];
     Level &C = *H->lv[level];
@@ -707,6 +708,7 @@ mk_status mk_op_interp_correct(mk_problem *p, const mk_solve_opts *opts, int32_t
     Hierarchy *H = nullptr;
     mk_solve_opts o;
     CKS(get_level(p, opts, level, H, o));
+    if (o.transfer != MK_TRANSFER_MK) return MK_ERR_INVALID;
     if (level >= (int)H->lv.size()) return MK_ERR_INVALID;
     Level &L = *H->lv[level - 1];
     Level &C = *H->lv[level];

@@ -189,6 +189,23 @@ void launch_update_df(int64_t len, const float2 *W, float2 *V, int64_t vstride, 
                       const ReduceScratch &rs, KState ks, int mode, bool second_pass,
                       const int *done, cudaStream_t s);
 
+// ---- MGRIT intergrid operators, 1D (mgrit.cu; Sec. 3.2 Eqs. (mgritY), (mgritZ)) ----------
+// vhat_K = sigma ((A v)_{nu K} - mu v_{nu K}), K = 0 .. gc.nt (injection of the coarse points).
+template <typename Tin, typename Tc>
+void launch_inject_restrict_1d(const Geom &gf, const Geom &gc, int nu, const Weights &w,
+                               SpaceOp<Tc> L, const Tin *v, const double *sigma, Tc *vhat,
+                               const int *done, cudaStream_t s);
+// Ideal interpolation, first part: rp row 1 + K (nu - 1) = (I + bL) xt_K, K < gc.nt, on the
+// propagation geometry gp (gc.nt (nu - 1) steps; its other rows are left untouched).
+template <typename Tc>
+void launch_ideal_interp_rhs_1d(const Geom &gc, const Geom &gp, int nu, double b, SpaceOp<Tc> L,
+                                const Tc *xt, Tc *rp, const int *done, cudaStream_t s);
+// Ideal interpolation, last part: t_{nu K} = xt_K, t_{nu K + i} = xp row 1 + K (nu - 1) + i - 1.
+template <typename Tc>
+void launch_ideal_interp_gather_1d(const Geom &gf, const Geom &gc, const Geom &gp, int nu,
+                                   const Tc *xt, const Tc *xp, Tc *t, const int *done,
+                                   cudaStream_t s);
+
 // ---- slab solvers (slab.cu) -----------------------------------------------------------
 // 1D coarsest: n_cgs slabs x s steps, tridiagonal I - aL by parallel cyclic reduction with
 // precomputed tables (alpha, gamma, binv in T); x_0 = r_0.

@@ -21,7 +21,7 @@ int64_t launches_total();
 bool OptsKey::operator==(const OptsKey &o) const {
     if (levels != o.levels || n_cgs != o.n_cgs || mu_mode != o.mu_mode ||
         precision != o.precision || restart != o.restart || mu_value != o.mu_value || orth != o.orth ||
-        autotune != o.autotune)
+        autotune != o.autotune || transfer != o.transfer)
         return false;
     for (int i = 0; i < MK_MAX_LEVELS; ++i)
         if (nu[i] != o.nu[i] || space[i] != o.space[i] || m_inner[i] != o.m_inner[i]) return false;
@@ -38,6 +38,7 @@ static OptsKey make_key(const mk_solve_opts &o) {
     k.restart = o.restart;
     k.orth = o.orth;
     k.autotune = o.autotune ? 1 : 0;
+    k.transfer = o.transfer;
     k.mu_value = o.mu_mode == 2 ? o.mu_value : 0.0;
     for (int i = 0; i < o.levels - 1 && i < MK_MAX_LEVELS; ++i) {
         k.nu[i] = o.nu[i];
@@ -55,6 +56,11 @@ mk_status validate_opts(const Problem &P, const mk_solve_opts &o) {
     if (o.mu_mode < 0 || o.mu_mode > 2) return MK_ERR_INVALID;
     if (o.orth < 0 || o.orth > 2) return MK_ERR_INVALID;
     if (o.n_cgs < 0) return MK_ERR_INVALID;
+    if (o.transfer != MK_TRANSFER_MK && o.transfer != MK_TRANSFER_MGRIT) return MK_ERR_INVALID;
+    if (o.transfer == MK_TRANSFER_MGRIT &&
+        (P.dim != 1 || o.levels != 2 || o.space[0] != 0 || o.nu[0] < 2 ||
+         P.nt % o.nu[0] != 0 || P.nt / o.nu[0] > 65535))
+        return MK_ERR_INVALID;
     int nt = P.nt, nx = P.nx, ny = P.dim == 2 ? P.ny : 1;
     for (int l = 0; l < o.levels - 1; ++l) {
         if (o.nu[l] < 1) return MK_ERR_INVALID;
@@ -247,10 +253,17 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
             bool sp = o.space[l - 1] != 0;
             lv->Lx = sp ? agglomerate(pv.Lx) : pv.Lx;
             if (P.dim == 2) lv->Ly = sp ? agglomerate(pv.Ly) : pv.Ly;
-            // Galerkin coarse operator as a theta-scheme with a larger step (Eqs.
-            // (timecoarse1)-(timecoarse3), literal product nu psi - (nu-1) phi)
-            lv->w.a = nu * pv.w.a + (nu - 1) * pv.w.b;
-            lv->w.b = pv.w.b;
+            if (o.transfer == MK_TRANSFER_MGRIT) {
+                // non-Galerkin coarse matrix of Eq. (coarsemat): the theta-scheme with the same
+                // theta and step nu dt (Psi_n, Phi_n of Eq. (timemarchdT))
+                lv->w.a = P.theta * nu * P.dt;
+                lv->w.b = (1.0 - P.theta) * nu * P.dt;
+            } else {
+                // Galerkin coarse operator as a theta-scheme with a larger step (Eqs.
+                // (timecoarse1)-(timecoarse3), literal product nu psi - (nu-1) phi)
+                lv->w.a = nu * pv.w.a + (nu - 1) * pv.w.b;
+                lv->w.b = pv.w.b;
+            }
             lv->g = make_geom(P.dim, lv->Lx.n(), P.dim == 2 ? lv->Ly.n() : 1, pv.g.nt / nu);
         }
         if (l < L - 1) {
@@ -309,6 +322,24 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
         }
         H->lv.push_back(std::move(lv));
     }
+    if (o.transfer == MK_TRANSFER_MGRIT) {
+        // ideal interpolation: the fine steps of every coarse interval as one decoupled slab
+        const Level &F0 = *H->lv[0];
+        const int nu = o.nu[0], nT = P.nt / nu;
+        std::unique_ptr<Level> fp(new Level());
+        fp->Lx = F0.Lx;
+        fp->w = F0.w;
+        fp->g = make_geom(1, P.nx, 1, nT * (nu - 1));
+        fp->coarsest = true;
+        mk_status st = upload_coefs(*fp, 1);
+        if (st != MK_OK) return st;
+        MKCK(fp->R.alloc(cs * (size_t)fp->g.len));
+        MKCK(fp->X.alloc(cs * (size_t)fp->g.len));
+        st = build_coarsest_tables(*fp, 1, fp64, nT);
+        if (st != MK_OK) return st;
+        H->fprop = std::move(fp);
+        MKCK(H->zt.alloc(cs * (size_t)F0.g.len));
+    }
     const size_t len0 = (size_t)P.g.len;
     MKCK(H->f.alloc(sizeof(double) * len0));
     MKCK(H->u.alloc(sizeof(double) * len0));
@@ -325,29 +356,34 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
 // ---------------------------------------------------------------------------------------
 // MK cycle (enqueue only)
 // ---------------------------------------------------------------------------------------
+// Decoupled slab solve on level C (n_cgs slabs; 0 = one coupled march).
 template <typename Tc>
-void enqueue_coarsest_t(Hierarchy &H, const int *done, cudaStream_t s) {
-    Level &C = *H.lv.back();
+static void enqueue_slabs_t(Level &C, int n_cgs, const int *done, cudaStream_t s) {
     const int kind = C.coarse_kind;   // 0: sine transform, else partitioned, else PCR
     if constexpr (std::is_same<Tc, float>::value) {
         if (C.dstN2 > 0 && (kind == 0 || kind == 1)) {
-            launch_slab_1d_dst(C.g, C.dst.as<float>(), C.dsttw.as<float2>(), C.dstN2, H.key.n_cgs,
+            launch_slab_1d_dst(C.g, C.dst.as<float>(), C.dsttw.as<float2>(), C.dstN2, n_cgs,
                                C.dstbuf.as<float>(), C.dstld, C.R.as<float>(), C.X.as<float>(),
                                done, s);
             return;
         }
     }
     if (C.g.dim == 1 && C.spikeU > 0 && kind != 3)
-        launch_slab_1d_warp<Tc>(C.g, C.w.b, C.spike.as<Tc>(), C.spikeU, H.key.n_cgs, C.R.as<Tc>(),
+        launch_slab_1d_warp<Tc>(C.g, C.w.b, C.spike.as<Tc>(), C.spikeU, n_cgs, C.R.as<Tc>(),
                                 C.X.as<Tc>(), done, s, PROF_SLAB);
     else if (C.g.dim == 1)
         launch_slab_1d<Tc>(C.g, C.w.b, op_of<Tc>(C), C.alpha.as<Tc>(), C.gamma.as<Tc>(),
-                           C.binv.as<Tc>(), C.npad, C.nlev, H.key.n_cgs, C.R.as<Tc>(), C.X.as<Tc>(),
+                           C.binv.as<Tc>(), C.npad, C.nlev, n_cgs, C.R.as<Tc>(), C.X.as<Tc>(),
                            done, s);
     else
         launch_slab_2d_fdm<Tc>(C.g, C.w.a, C.w.b, C.Sx.as<Tc>(), C.Sxi.as<Tc>(), C.lamx.as<Tc>(),
-                               C.Sy.as<Tc>(), C.Syi.as<Tc>(), C.lamy.as<Tc>(), H.key.n_cgs,
+                               C.Sy.as<Tc>(), C.Syi.as<Tc>(), C.lamy.as<Tc>(), n_cgs,
                                C.fdmbuf.as<Tc>(), C.R.as<Tc>(), C.X.as<Tc>(), done, s);
+}
+
+template <typename Tc>
+void enqueue_coarsest_t(Hierarchy &H, const int *done, cudaStream_t s) {
+    enqueue_slabs_t<Tc>(*H.lv.back(), H.key.n_cgs, done, s);
 }
 
 void enqueue_coarsest(Hierarchy &H, const int *done, cudaStream_t s) {
@@ -371,30 +407,61 @@ static void set_ctx(const Level &L, int level) {
 
 // x_j = sigma_j V_j - Z vt and w = A x_j (K4).  Level 1 of the mixed solve keeps V and w as
 // double-float pairs and evaluates w in double-float arithmetic.
+// gc, nu, space, cstride: geometry, coarsening and stride of the vectors Xc that Z acts on
+// (the next level's, or the fine geometry with nu = 1 when Z has been applied already).
 template <typename Tv, typename Tc, typename Tx, typename Tw, typename Tcw>
 struct InterpStep {
-    static void run(Level &L, Level &C, const Tv *vj, const double *sig, const Tc *Xc, int mc,
-                    const double *yc, int j, const int *done, cudaStream_t s) {
-        launch_interp<Tv, Tc, Tx, Tw, Tcw>(L.g, C.g, L.nu, L.space, L.w, op_of<Tcw>(L), vj, sig, Xc,
-                                           mc, C.stride, yc, L.X.as<Tx>() + (int64_t)j * L.stride,
+    static void run(Level &L, const Geom &gc, int nu, bool space, int64_t cstride, const Tv *vj,
+                    const double *sig, const Tc *Xc, int mc, const double *yc, int j,
+                    const int *done, cudaStream_t s) {
+        launch_interp<Tv, Tc, Tx, Tw, Tcw>(L.g, gc, nu, space, L.w, op_of<Tcw>(L), vj, sig, Xc,
+                                           mc, cstride, yc, L.X.as<Tx>() + (int64_t)j * L.stride,
                                            L.W.as<Tw>(), done, s);
     }
 };
 template <>
 struct InterpStep<float2, float, float, float2, double> {
-    static void run(Level &L, Level &C, const float2 *vj, const double *sig, const float *Xc,
-                    int mc, const double *yc, int j, const int *done, cudaStream_t s) {
+    static void run(Level &L, const Geom &gc, int nu, bool space, int64_t cstride,
+                    const float2 *vj, const double *sig, const float *Xc, int mc,
+                    const double *yc, int j, const int *done, cudaStream_t s) {
         const int64_t nc = 3 * (int64_t)L.g.nx + (L.g.dim == 2 ? 3 * (int64_t)L.g.ny : 0);
         const float2 *ca = L.cdf.as<float2>();
-        launch_interp_df(L.g, C.g, L.nu, L.space, ca, ca + nc, L.w.b != 0.0, vj, sig, Xc, mc,
-                         C.stride, yc, L.X.as<float>() + (int64_t)j * L.stride, L.W.as<float2>(),
+        launch_interp_df(L.g, gc, nu, space, ca, ca + nc, L.w.b != 0.0, vj, sig, Xc, mc,
+                         cstride, yc, L.X.as<float>() + (int64_t)j * L.stride, L.W.as<float2>(),
                          done, s, L.cuni.p ? L.cuni.as<float2>() : nullptr, L.cuni_square);
     }
 };
 template <typename Tv, typename Tc, typename Tx, typename Tw, typename Tcw>
 static void interp_step(Level &L, Level &C, const Tv *vj, const double *sig, const Tc *Xc, int mc,
                         const double *yc, int j, const int *done, cudaStream_t s) {
-    InterpStep<Tv, Tc, Tx, Tw, Tcw>::run(L, C, vj, sig, Xc, mc, yc, j, done, s);
+    InterpStep<Tv, Tc, Tx, Tw, Tcw>::run(L, C.g, L.nu, L.space, C.stride, vj, sig, Xc, mc, yc, j,
+                                         done, s);
+}
+
+// Substeps 4.1-4.5 with the MGRIT transfers (two levels, 1D): injection of the shifted
+// residual at the coarse points, the coarse theta-scheme solve, the ideal interpolation
+// (phi xt_K on the first fine step of every interval, the decoupled march of the interval's
+// nu - 1 fine steps, gather), then x = sigma v - Z xt and w = A x by the interpolation kernel
+// with nu = 1 on the gathered vector.
+template <typename Tc, typename Tv, typename Tx, typename Tw, typename Tcw>
+static void mgrit_step_t(Hierarchy &H, int j, const Tv *vj, const double *sig, const int *done,
+                         cudaStream_t s) {
+    Level &L = *H.lv[0];
+    Level &C = *H.lv[1];
+    Level &F = *H.fprop;
+    set_ctx(L, 0);
+    launch_inject_restrict_1d<Tv, Tc>(L.g, C.g, L.nu, L.w, op_of<Tc>(L), vj, sig, C.R.as<Tc>(),
+                                      done, s);                          // 4.1-4.2, Eq. (mgritY)
+    set_ctx(C, 1);
+    enqueue_coarsest_t<Tc>(H, done, s);                                  // 4.3, Eq. (coarsemat)
+    set_ctx(L, 0);
+    launch_ideal_interp_rhs_1d<Tc>(C.g, F.g, L.nu, L.w.b, op_of<Tc>(L), C.X.as<Tc>(),
+                                   F.R.as<Tc>(), done, s);               // 4.4, Eq. (mgritZ)
+    enqueue_slabs_t<Tc>(F, C.g.nt, done, s);
+    launch_ideal_interp_gather_1d<Tc>(L.g, C.g, F.g, L.nu, C.X.as<Tc>(), F.X.as<Tc>(),
+                                      H.zt.as<Tc>(), done, s);
+    InterpStep<Tv, Tc, Tx, Tw, Tcw>::run(L, L.g, 1, false, L.stride, vj, sig, H.zt.as<Tc>(), 1,
+                                         nullptr, j, done, s);           // 4.5 and step 5
 }
 
 template <typename Tc, typename Tv, typename Tx, typename Tw, typename Tcw>
@@ -403,6 +470,10 @@ static void cycle_step_t(Hierarchy &H, int l, int j, const int *done, cudaStream
     Level &C = *H.lv[l + 1];
     const Tv *vj = L.V.as<Tv>() + (int64_t)j * L.stride;
     const double *sig = L.ks.sigma() + j;
+    if (H.fprop && l == 0) {   // MGRIT transfers: two levels only
+        mgrit_step_t<Tc, Tv, Tx, Tw, Tcw>(H, j, vj, sig, done, s);
+        return;
+    }
     // 4.1-4.2: restriction of the shifted residual of the basis vector
     set_ctx(L, l);
     if (C.coarsest) {
@@ -734,12 +805,12 @@ static void tune_interp(Hierarchy &H, int l, cudaStream_t s, cudaEvent_t e0, cud
         set_tile_hint(0, kc);
         const float t = time_launch([&] {
             if (l == 0 && H.precision == 1)
-                InterpStep<float2, float, float, float2, double>::run(L, C, L.V.as<float2>(), nullptr,
-                                                                      C.X.as<float>(), mc, yc, 0,
-                                                                      nullptr, s);
+                interp_step<float2, float, float, float2, double>(L, C, L.V.as<float2>(), nullptr,
+                                                                  C.X.as<float>(), mc, yc, 0,
+                                                                  nullptr, s);
             else
-                InterpStep<Tc, Tc, Tc, Tc, Tc>::run(L, C, L.V.as<Tc>(), nullptr, C.X.as<Tc>(), mc,
-                                                    yc, 0, nullptr, s);
+                interp_step<Tc, Tc, Tc, Tc, Tc>(L, C, L.V.as<Tc>(), nullptr, C.X.as<Tc>(), mc, yc,
+                                                0, nullptr, s);
         }, s, e0, e1);
         if (t < best) {
             best = t;

@@ -31,7 +31,7 @@ struct DevMem {
 };
 
 struct OptsKey {
-    int levels, n_cgs, mu_mode, precision, restart, orth, autotune;
+    int levels, n_cgs, mu_mode, precision, restart, orth, autotune, transfer;
     int nu[MK_MAX_LEVELS], space[MK_MAX_LEVELS], m_inner[MK_MAX_LEVELS];
     double mu_value;
     bool operator==(const OptsKey &o) const;
@@ -76,6 +76,11 @@ struct Hierarchy {
     OptsKey key;
     int precision = 0;  // 0 FP64, 1 mixed
     std::vector<std::unique_ptr<Level>> lv;
+    // MGRIT transfers (transfer = MK_TRANSFER_MGRIT): the fine-step march between coarse
+    // points as decoupled slabs (fine a, b and L; n_T slabs of nu - 1 steps; R = phi xt_K on
+    // each slab's first row, X = the marched points) and zt = Z xt on the fine geometry
+    std::unique_ptr<Level> fprop;
+    DevMem zt;
     DevMem f, u;        // level-1 right-hand side and iterate (FP64)
     DevMem partials, counters;
     ReduceScratch rs{nullptr, nullptr, 0};
