@@ -268,6 +268,50 @@ def bench_alternate(mk, torch, dev, steps=2):
     return out
 
 
+def bench_two_level(mk, torch, dev, steps=1):
+    """Table 2's largest row (Sec. 3.3.1): 1D n = 1024, n_t = 8192, C = 0.64, theta = 1/2,
+    mu = 1, exact coarse solve, tol 1e-6 on the relative residual, FP64, u_0 seeded uniform
+    random.  Time to solution and iterations of the two-level method with T-coarsening,
+    TS-coarsening and the MGRIT intergrid operators (Eqs. (mgritY), (mgritZ) with the coarse
+    matrix of Eq. (coarsemat)) for nu = 2, 4, 8, beside the GPU theta-march of the problem."""
+    n, nt = 1024, 8192
+    h = 1.0 / (n + 1)
+    dt = 0.32 * h * h
+    u0 = torch.from_numpy(np.random.default_rng(7).uniform(size=n)).to(dev)
+    u = torch.empty((nt + 1, n), dtype=torch.float64, device=dev)
+    um = torch.empty_like(u)
+
+    def timed(fn):
+        r = fn()
+        ts = []
+        for _ in range(steps):
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return statistics.mean(ts), r
+
+    out = {"workload": "heat1d_n1024_nt8192_C0.64_theta0.5_two_level_exact_coarse", "tol": 1e-6,
+           "precision": "fp64"}
+    with mk.Problem(1, n, 1.0, 0.5, dt, nt) as p:
+        t_march, _ = timed(lambda: mk.mk_march(p.handle, u0, um))
+        out["march_gpu_s"] = t_march
+        for name, kw in (("T", {}), ("TS", {"space": (True,)}), ("MGRIT", {"transfer": "mgrit"})):
+            for nu in (2, 4, 8):
+                o = mk.make_opts(levels=2, nu=(nu,), n_cgs=0, mu="one", tol=1e-6, restart=64,
+                                 max_iters=200, precision="fp64", **kw)
+                t, info = timed(lambda: mk.mk_solve(p.handle, u0, u, o))
+                err = float(((u - um).abs().max() / um.abs().max()).item())
+                out[f"{name}_nu{nu}"] = {"s": t, "iterations": int(info.iterations),
+                                         "relative_to_march": t / t_march,
+                                         "max_rel_diff_vs_march": err}
+    return out
+
+
 def profile_2d():
     """A few outer iterations of the 2D workload's solver on 255 x 255 x 513 (33.4 M points,
     double-float vectors of 267 MB: larger than L2, a few GB on the device in all)."""
@@ -478,6 +522,12 @@ def main():
             line["paths"]["mk_alternate_2d"] = bench_alternate(mk, torch, dev)
         except Exception as e:
             line["paths"]["mk_alternate_2d"] = {"error": str(e)[:200]}
+
+        # ---------------- Table 2: two-level T / TS / MGRIT transfers ----------------
+        try:
+            line["paths"]["two_level_table2"] = bench_two_level(mk, torch, dev)
+        except Exception as e:
+            line["paths"]["two_level_table2"] = {"error": str(e)[:200]}
 
         # ---------------- batched uneven problems ----------------
         try:
