@@ -70,6 +70,39 @@ int main(void) {
                      ctypes.sizeof(_lib.mk_solve_info), ctypes.sizeof(_lib.mk_level_desc)]
 
 
+def test_struct_field_offsets_match_header():
+    """Every field of the ctypes mirrors sits at the offset the C compiler gives it (equal sizes
+    alone would not catch two fields swapped)."""
+    from paper_2401_00228_gb300 import _lib
+    import subprocess
+    import tempfile
+    structs = [_lib.mk_stencil, _lib.mk_solve_opts, _lib.mk_solve_info, _lib.mk_level_desc]
+    lines = []
+    for st in structs:
+        for name, _ in st._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({st.__name__}, {name}));')
+    code = "#include <stddef.h>\n#include <stdio.h>\n#include \"mk.h\"\nint main(void) {\n" + \
+        "\n".join(lines) + "\n  return 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(code)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        offs = list(map(int, subprocess.check_output([exe]).split()))
+    want = [getattr(st, name).offset for st in structs for name, _ in st._fields_]
+    assert offs == want
+
+
+def test_transfer_option_values():
+    from paper_2401_00228_gb300 import _lib, make_opts, mk_default_opts
+    assert mk_default_opts().transfer == _lib.MK_TRANSFER_MK == 0
+    assert make_opts(levels=2, transfer="mgrit").transfer == _lib.MK_TRANSFER_MGRIT == 1
+    hdr = open(HEADER).read()
+    assert "#define MK_TRANSFER_MK 0" in hdr and "#define MK_TRANSFER_MGRIT 1" in hdr
+    with pytest.raises(KeyError):
+        make_opts(transfer="parareal")
+
+
 def test_product_path_does_not_import_oracle():
     """The package never references the oracle (no CPU fallback)."""
     pkg = os.path.join(ROOT, "paper_2401_00228_gb300")
