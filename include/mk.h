@@ -104,7 +104,8 @@ typedef struct mk_solve_opts {
                             non-Galerkin coarse matrix of Eq. (coarsemat) (the theta-scheme with
                             step nu dt).  Requires dim = 1, levels = 2, space[0] = 0,
                             nu[0] >= 2 and n_t / nu[0] <= 65535; MK_ERR_INVALID otherwise.
-                            mk_op_restrict and mk_op_interp_correct take MK_TRANSFER_MK only. */
+                            mk_op_restrict, mk_op_interp_correct and mk_create_batch take
+                            MK_TRANSFER_MK only. */
 } mk_solve_opts;
 
 #define MK_TRANSFER_MK 0
@@ -311,8 +312,8 @@ mk_status mk_op_lsq(int32_t j, const double *H, double beta, double *y, double *
    mk_create_batch: problems = count distinct handles (not owned; they must outlive the
      batch and keep their source); opts = NULL or count option structs.  The batch holds
      its hierarchies, graph and streams on the current device until mk_destroy_batch.
-     Errors: MK_ERR_INVALID (count < 1, a NULL or repeated handle, bad options),
-     MK_ERR_NOMEM, MK_ERR_CUDA.
+     Errors: MK_ERR_INVALID (count < 1, a NULL or repeated handle, bad options, options
+     with transfer != MK_TRANSFER_MK), MK_ERR_NOMEM, MK_ERR_CUDA.
    mk_solve_batch: u0[i] = initial state of problem i (nx or ny x nx), u_out[i] = its
      (nt+1) x n solution; each pointer host or device as elsewhere in this ABI.  infos =
      NULL or count structs (solve_ms and kernel_launches are those of the whole batch).

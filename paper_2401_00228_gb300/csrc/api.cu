@@ -971,6 +971,7 @@ mk_status mk_create_batch(mk_problem *const *problems, int32_t count, const mk_s
         mk_solve_opts o = resolve_opts(opts ? &opts[i] : nullptr);
         Problem &P = problems[i]->P;
         CKS(validate_opts(P, o));
+        if (o.transfer != MK_TRANSFER_MK) return MK_ERR_INVALID;   // batches: block transfers
         std::unique_ptr<Hierarchy> H;
         CKS(build_hierarchy_new(P, o, H));
         if (autotune) CKS(autotune_hierarchy(*H, s0));
