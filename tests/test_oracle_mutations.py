@@ -2,8 +2,11 @@
 
 One plausible mistake at a time is planted in a scratch copy of the oracle: a swapped theta
 weight, a wrong sign, an off-by-one time block, a missing average, a wrong Arnoldi index, a
-dropped adjoint term, each piece of the MGRIT comparison.  The pins aimed at that part of the
-oracle (tests/test_oracle.py, selected by -k) must then fail, and pass on the unchanged copy.
+dropped adjoint term, each piece of the MGRIT comparison, and in the plain-C march a wrong
+elimination sign, off-by-one or mixed-up neighbour indices, a dropped source term, a band
+limit off by one (the scratch copy then compiles the changed C source).  The pins aimed at
+that part of the oracle (tests/test_oracle.py, selected by -k) must then fail, and pass on the
+unchanged copy.
 Each case runs pytest in a subprocess on the scratch copy; the repository is not modified.
 """
 import os
@@ -14,7 +17,6 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-ORACLE = os.path.join(ROOT, "oracle", "mk_oracle.py")
 
 # (name, text in mk_oracle.py, planted replacement, -k selector of the pins that must catch it)
 MUTATIONS = [
@@ -95,6 +97,26 @@ MUTATIONS = [
     ("mgrit_coarse_step", "DT = nu * dt\n", "DT = (nu - 1) * dt\n", "mgrit_coarse_level_is"),
 ]
 
+# the same for the plain-C march (oracle/march.c)
+MUTATIONS_C = [
+    ("thomas_forward_sign", "if (i > 0) r -= sub * rhs[i - 1];", "if (i > 0) r += sub * rhs[i - 1];"),
+    ("explicit_lo_off_by_one", "if (i > 0) lx += lo[i] * x[i - 1];",
+     "if (i > 1) lx += lo[i] * x[i - 1];"),
+    ("u0_not_copied", "memcpy(u, f, sizeof(double) * n); /* u_0 = f_0 */",
+     "memset(u, 0, sizeof(double) * n);"),
+    ("apply2d_y_index", "if (j > 0) s += ylo[j] * v[p - nx];",
+     "if (j > 0) s += ylo[i % ny] * v[p - nx];"),
+    ("band_x_sign", "if (i > 0) B(p, p - 1) = -a * xlo[i];", "if (i > 0) B(p, p - 1) = a * xlo[i];"),
+    ("band_y_index", "if (j > 0) B(p, p - nx) = -a * ylo[j];",
+     "if (j > 0) B(p, p - nx) = -a * ylo[i % ny];"),
+    ("rhs2d_drops_source", "rhs[p] = prev[p] + b * lv[p] + fk[p];", "rhs[p] = prev[p] + b * lv[p];"),
+    ("forward_band_limit", "int first = (p - w > 0) ? p - w : 0;",
+     "int first = (p - w + 1 > 0) ? p - w + 1 : 0;"),
+]
+MARCH_PINS = "march_eigenmode or march_equals_dense_solve"
+CASES = ([("mk_oracle.py",) + m for m in MUTATIONS] +
+         [("march.c", n, o, r, MARCH_PINS) for n, o, r in MUTATIONS_C])
+
 
 def _run(base, selector):
     env = dict(os.environ)
@@ -102,6 +124,12 @@ def _run(base, selector):
     return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                            "tests/test_oracle.py", "-k", selector],
                           cwd=base, capture_output=True, text=True, timeout=600, env=env)
+
+
+def _drop_march_library(base):
+    so = os.path.join(base, "oracle", "liboracle_march.so")
+    if os.path.exists(so):
+        os.remove(so)
 
 
 @pytest.fixture(scope="module")
@@ -118,19 +146,24 @@ def scratch(tmp_path_factory):
 
 
 def test_unchanged_copy_passes_the_targeted_pins(scratch):
-    selector = " or ".join(sorted({m[3] for m in MUTATIONS}))
+    selector = " or ".join(sorted({c[4] for c in CASES}))
+    _drop_march_library(scratch)
     r = _run(scratch, selector)
     assert r.returncode == 0, r.stdout[-3000:]
 
 
-@pytest.mark.parametrize("name,old,new,selector", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_planted_mistake_is_caught(scratch, name, old, new, selector):
-    src = open(ORACLE).read()
+@pytest.mark.parametrize("fname,name,old,new,selector", CASES, ids=[c[1] for c in CASES])
+def test_planted_mistake_is_caught(scratch, fname, name, old, new, selector):
+    src = open(os.path.join(ROOT, "oracle", fname)).read()
     assert src.count(old) == 1, name
-    path = os.path.join(scratch, "oracle", "mk_oracle.py")
+    path = os.path.join(scratch, "oracle", fname)
     open(path, "w").write(src.replace(old, new))
+    if fname.endswith(".c"):
+        _drop_march_library(scratch)
     try:
         r = _run(scratch, selector)
     finally:
         open(path, "w").write(src)
+        if fname.endswith(".c"):
+            _drop_march_library(scratch)
     assert r.returncode == 1, (name, r.stdout[-3000:])
