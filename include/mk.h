@@ -180,7 +180,8 @@ mk_status mk_create_problem(const mk_stencil *A_n, double theta, double dt, int3
                             const double *g, mk_problem **out);
 
 /* Replace the source g of an existing problem ((nt+1) x n samples, host or device, or
-   NULL for g = 0): recomputes f_k, k >= 1.  Copied; not retained. */
+   NULL for g = 0): recomputes f_k, k >= 1 (Eq. (finesys)).  Copied; not retained.
+   Errors: MK_ERR_INVALID (NULL p), MK_ERR_NOMEM, MK_ERR_CUDA. */
 mk_status mk_set_source(mk_problem *p, const double *g, void *stream);
 
 /* Frees the problem and all its workspace.  NULL is ignored. */
@@ -202,6 +203,7 @@ mk_status mk_solve(mk_problem *p, const double *u0, const mk_solve_opts *opts,
 /*
  * mk_solve_rhs -- same solver for an arbitrary right-hand side f ((nt+1) x n), u^0 = 0.
  * mk_solve(p, u0, ...) equals mk_solve_rhs with f_0 = u0 and the problem's source blocks.
+ * Errors: as mk_solve (MK_ERR_INVALID also for a NULL f or u_out).
  */
 mk_status mk_solve_rhs(mk_problem *p, const double *f, const mk_solve_opts *opts,
                        double *u_out, mk_solve_info *info, void *stream);
@@ -214,6 +216,7 @@ mk_status mk_solve_rhs(mk_problem *p, const double *f, const mk_solve_opts *opts
  * solve in 2D (FFT in a direction whose n + 1 is a power of two up to 2048, the dense sine
  * matrix in one with n <= 1024).  Larger grids: MK_ERR_INVALID.  Allocates its staging
  * and step buffers per call; returns after the stream has finished the march.
+ * Errors: MK_ERR_INVALID (NULL p, u0 or u_out; grid too large), MK_ERR_NOMEM, MK_ERR_CUDA.
  */
 mk_status mk_march(mk_problem *p, const double *u0, double *u_out, void *stream);
 
@@ -229,12 +232,16 @@ mk_status mk_march(mk_problem *p, const double *u0, double *u_out, void *stream)
  *   dJdu   : (nt+1) x n.
  *   grad_u0: n, or NULL.  grad_g: (nt+1) x n, or NULL.  grad_tau: one double, or NULL.
  *   lam_out: (nt+1) x n adjoint state, or NULL.
+ * Errors: MK_ERR_INVALID (NULL p or dJdu, grad_tau without u, options as in mk_solve),
+ *         MK_ERR_NOT_CONVERGED (the outputs are formed from the last adjoint iterate),
+ *         MK_ERR_NONFINITE, MK_ERR_NOMEM, MK_ERR_CUDA.
  */
 mk_status mk_adjoint(mk_problem *p, const double *u, const double *dJdu,
                      const mk_solve_opts *opts, double *grad_u0, double *grad_g,
                      double *grad_tau, double *lam_out, mk_solve_info *info, void *stream);
 
-/* Problem geometry (host ints / doubles). */
+/* Problem geometry (host ints / doubles); NULL outputs are skipped.  Host only.
+   Errors: MK_ERR_INVALID (NULL p). */
 mk_status mk_problem_shape(const mk_problem *p, int32_t *dim, int32_t *nx, int32_t *ny, int32_t *nt,
                            double *theta, double *dt, double *tau);
 
@@ -243,7 +250,10 @@ mk_status mk_problem_shape(const mk_problem *p, int32_t *dim, int32_t *nx, int32
  * of the given level so that it can be checked on its own.  `level` is 1-based
  * (1 = fine).  `precision` 0 computes in FP64, 1 in FP32 (inputs rounded to FP32 first,
  * as in the mixed cycle; outputs widened back to FP64).  The hierarchy is the one `opts`
- * describes (NULL = defaults).
+ * describes (NULL = defaults).  Arrays are host or device as elsewhere; the entry points
+ * allocate their staging buffers per call and return after the stream has finished.
+ * Errors (all of them): MK_ERR_INVALID for a NULL problem or array, a level or precision
+ * out of range, or options the problem rejects; MK_ERR_NOMEM; MK_ERR_CUDA.
  * ------------------------------------------------------------------------------------ */
 
 typedef struct mk_level_desc {
@@ -253,9 +263,13 @@ typedef struct mk_level_desc {
 } mk_level_desc;
 
 /* Level geometry and weights (Galerkin coarse operator of Eqs. (timecoarse1)-(timecoarse3)):
-   a_{l+1} = nu a_l + (nu-1) b_l, b_{l+1} = b_l, nt_{l+1} = nt_l / nu.
+   a_{l+1} = nu a_l + (nu-1) b_l, b_{l+1} = b_l, nt_{l+1} = nt_l / nu; with
+   transfer = MK_TRANSFER_MGRIT the coarse level is the theta-scheme of Eq. (coarsemat),
+   a_2 = theta nu dt, b_2 = (1-theta) nu dt.
    If xcoef/ycoef are non-NULL they receive the spatial operator L_l = Y^T L_{l-1} Z as
-   3 x nx (resp. 3 x ny) host doubles: rows lo, di, up. */
+   3 x nx (resp. 3 x ny) host doubles: rows lo, di, up.
+   Errors: MK_ERR_INVALID (NULL p, level outside 1..levels, bad options), MK_ERR_NOMEM,
+   MK_ERR_CUDA (the hierarchy for opts is built if it does not exist yet). */
 mk_status mk_level_info(mk_problem *p, const mk_solve_opts *opts, int32_t level,
                         mk_level_desc *desc, double *xcoef, double *ycoef);
 
@@ -279,11 +293,13 @@ mk_status mk_op_interp_correct(mk_problem *p, const mk_solve_opts *opts, int32_t
                                int32_t precision, const double *v, const double *vt,
                                double *x, double *w, void *stream);
 
-/* x = Atilde_L^{-1} r on the coarsest level (decoupled slabs, Eq. (Qhtilde)). */
+/* x = Atilde_L^{-1} r on the coarsest level (decoupled slabs, Eq. (Qhtilde); n_cgs = 0: the
+   exact coarse matrix; with MK_TRANSFER_MGRIT the theta-scheme of Eq. (coarsemat)). */
 mk_status mk_op_coarsest(mk_problem *p, const mk_solve_opts *opts, int32_t precision,
                          const double *r, double *x, void *stream);
 
-/* x = Q_l v: one full MK cycle from level l (inner FGMRES on intermediate levels). */
+/* x = Q_l v: one full MK cycle from level l (inner FGMRES on intermediate levels); with
+   MK_TRANSFER_MGRIT the two-level cycle with the transfers of Eqs. (mgritY), (mgritZ). */
 mk_status mk_op_precond(mk_problem *p, const mk_solve_opts *opts, int32_t level,
                         const double *v, double *x, void *stream);
 
