@@ -51,7 +51,9 @@ typedef enum mk_status {
     MK_ERR_CUDA = 3,           /* a CUDA runtime call failed (see mk_last_cuda_error) */
     MK_ERR_NONFINITE = 4,      /* NaN/Inf in an input or in the iteration */
     MK_ERR_NOT_CONVERGED = 5,  /* max_iters reached: u_out holds the last iterate, info the residual */
-    MK_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
+    MK_ERR_TIMEOUT = 6,        /* reserved: no entry point returns it.  The library's kernels
+                                  never wait on one another (no spin on a flag or barrier);
+                                  cross-block reductions finish in the last arriving block */
     MK_ERR_TOO_LARGE = 7       /* the input needs more than a fixed-size static buffer holds
                                   (mk_op_residual_noalloc) */
 } mk_status;
@@ -369,7 +371,10 @@ void mk_destroy_batch(mk_batch *batch);
    library's device code is loaded, and every completed launch leaves it at zero.
    Set-up: the first call on each device looks up the scratch's address
    (cudaGetSymbolAddress, with that device current), which may load the library's device
-   code; make one call on each device before any stream capture.
+   code; make one call on each device before any stream capture.  The address is kept for
+   the life of the process: after a device reset (cudaDeviceReset, or a primary-context
+   reset by other code) the library's device code is reloaded and calls of this entry point
+   are undefined.
    Concurrency: every call on a device uses the same scratch, so calls whose executions
    overlap on one device (other streams, other host threads, without event ordering)
    race and return wrong results.  Order them on one stream.  Calls on different devices

@@ -19,7 +19,7 @@ from ._lib import (MK_MAX_LEVELS, MKError, mk_level_desc, mk_solve_info, mk_solv
 
 __all__ = ["mk_default_opts", "mk_create_problem", "mk_set_source", "mk_destroy", "mk_solve",
            "mk_solve_rhs", "mk_march", "mk_schedule_alternate", "mk_adjoint", "mk_level_info", "mk_op_rhs", "mk_op_apply",
-           "mk_op_residual", "mk_op_residual_noalloc", "mk_op_restrict", "mk_op_interp_correct", "mk_op_coarsest",
+           "mk_op_residual", "mk_op_residual_noalloc", "mk_problem_shape", "mk_op_restrict", "mk_op_interp_correct", "mk_op_coarsest",
            "mk_op_precond", "mk_op_orthogonalize", "mk_op_lsq", "mk_kernel_launch_count",
            "mk_create_batch", "mk_solve_batch", "mk_destroy_batch", "Batch",
            "make_opts", "Problem", "HeatSolve", "MKError", "lib", "solve"]
@@ -262,11 +262,32 @@ def mk_op_residual(p: int, f, u, r, stream=None) -> float:
     return nrm.value
 
 
+def mk_problem_shape(p: int):
+    """(dim, nx, ny, nt) of a problem handle (host only)."""
+    d, nx, ny, nt = (ctypes.c_int32() for _ in range(4))
+    _lib.check(lib().mk_problem_shape(p, ctypes.byref(d), ctypes.byref(nx), ctypes.byref(ny),
+                                      ctypes.byref(nt), None, None, None), "mk_problem_shape")
+    return d.value, nx.value, ny.value, nt.value
+
+
+def _numel(a) -> int:
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
 def mk_op_residual_noalloc(p: int, f, u, r, rnorm, rnorm_steps=None, stream=None) -> None:
     """r = f - A_h u, rnorm[0] = ||r||_2, rnorm_steps[k] = ||r_k||_2; every array on the device.
 
     The library allocates nothing in this call (its reduction scratch is static device
-    memory); r and rnorm_steps may be None.  Results are ready in stream order."""
+    memory); r and rnorm_steps may be None.  Results are ready in stream order.  The library
+    receives bare pointers and cannot see array sizes, so they are checked here against the
+    problem's shape: f, u (and r) need (n_t+1)*nx*ny elements, rnorm one, rnorm_steps n_t+1;
+    a short array raises ValueError before anything is launched."""
+    _, nx, ny, nt = mk_problem_shape(p)
+    need = (nt + 1) * nx * ny
+    for name, a, n in (("f", f, need), ("u", u, need), ("r", r, need), ("rnorm", rnorm, 1),
+                       ("rnorm_steps", rnorm_steps, nt + 1)):
+        if a is not None and _numel(a) < n:
+            raise ValueError(f"mk_op_residual_noalloc: {name} has {_numel(a)} elements, needs {n}")
     s = _stream(stream) or _current_stream_for(f, u)
     _lib.check(lib().mk_op_residual_noalloc(p, _ptr(f), _ptr(u), _ptr(r), _ptr(rnorm),
                                             _ptr(rnorm_steps), s), "mk_op_residual_noalloc")
@@ -305,14 +326,27 @@ def mk_op_lsq(j: int, H, beta: float, y, stream=None) -> float:
     return res.value
 
 
+def _copy(a):
+    if a is None:
+        return None
+    return a.copy() if isinstance(a, np.ndarray) else a.detach().clone()
+
+
 class Problem:
-    """Owning handle of an mk_problem."""
+    """Owning handle of an mk_problem.  `source` is a copy of the source g the problem holds
+    (given at creation or through set_source; None for g = 0)."""
 
     def __init__(self, dim: int, nx: int, tau: float, theta: float, dt: float, nt: int, g=None,
                  ny: int = 1):
         self.dim, self.nx, self.ny, self.nt = dim, nx, (ny if dim == 2 else 1), nt
         self.tau, self.theta, self.dt = tau, theta, dt
         self.handle = mk_create_problem(dim, nx, self.ny, tau, theta, dt, nt, g)
+        self.source = _copy(g)
+
+    def set_source(self, g, stream=None) -> None:
+        """Replace the source g (None: g = 0); the object keeps a copy of it."""
+        mk_set_source(self.handle, g, stream)
+        self.source = _copy(g)
 
     @property
     def space_shape(self):
@@ -371,7 +405,9 @@ def solve(u0, g=None, tau: float = 1.0, theta: float = 1.0, dt: float = 0.0, nt:
 
 class HeatSolve:
     """torch.autograd.Function factory: u = A_h^{-1} f_h(u0, g) with the MK solver forward and
-    the adjoint MK solve backward (gradients w.r.t. u0, g and tau)."""
+    the adjoint MK solve backward (gradients w.r.t. u0, g and tau).  The forward pass solves
+    with the autograd input g and then restores the problem's own source (Problem.source), so
+    later solves on the same problem are unaffected."""
 
     @staticmethod
     def apply(problem: Problem, u0, g, tau_tensor, opts: Optional[mk_solve_opts] = None):
@@ -382,10 +418,14 @@ class HeatSolve:
             def forward(ctx, u0_, g_, tau_):
                 if abs(float(tau_) - problem.tau) > 0.0:
                     raise ValueError("tau differs from the problem's tau; create a new Problem")
+                u = torch.empty(problem.shape, dtype=torch.float64, device=u0_.device)
                 if g_ is not None:
                     mk_set_source(problem.handle, g_.contiguous())
-                u = torch.empty(problem.shape, dtype=torch.float64, device=u0_.device)
-                mk_solve(problem.handle, u0_.contiguous(), u, opts)
+                try:
+                    mk_solve(problem.handle, u0_.contiguous(), u, opts)
+                finally:
+                    if g_ is not None:
+                        mk_set_source(problem.handle, problem.source)
                 ctx.save_for_backward(u)
                 return u
 

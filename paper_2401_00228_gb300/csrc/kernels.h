@@ -141,7 +141,8 @@ void launch_march_2d_dst(const Geom &g, double a, double b, double cx, double cy
 // Coarsest decoupled slabs by sine-transform diagonalisation (slab_dst.cu), FP32, for a
 // uniform 1D operator.  dst_transform_size(n) = 2(n+1) when that is a power of two <= 4096,
 // else 0 (not supported).  tab = [alpha (n) | beta (n)], tw = FFT twiddle table,
-// rh = scratch (nt+1) x ldd.  Three launches.
+// rh = scratch (nt+1) x ldd.  Any slab length; n_cgs = 0 is the coupled march over all nt
+// steps (the exact coarse solve).  Three launches.
 int dst_transform_size(int n);
 size_t dst_smem_bytes(int N2);
 cudaError_t dst_set_attributes();

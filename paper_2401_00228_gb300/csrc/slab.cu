@@ -19,6 +19,7 @@
 // n_cgs = 0 keeps every coupling (one slab of all steps): the exact coarse solve and,
 // on the fine level, the sequential theta-march of Eq. (timemarch).
 #include "kernels.h"
+#include "scan.cuh"
 
 namespace mk {
 
@@ -388,6 +389,7 @@ bool slab_warp_supported(int n) {
 // forward transform of every row, recurrence per (mode, slab) in place, inverse transform.
 // ---------------------------------------------------------------------------------------
 constexpr int FDM_THREADS = 256;
+constexpr int FDM_SHORT_SLAB = 32;   // longer slabs (and the coupled march) take the blocked scan
 
 template <typename T>
 __device__ __forceinline__ void fdm_product(const T *__restrict__ Mleft, const T *__restrict__ Mright_t,
@@ -514,8 +516,12 @@ void launch_slab_2d_fdm(const Geom &g, double a, double b, const T *Sx, const T 
     // row 0 is transformed only when the coupling to x_0 is kept
     const int k0 = coupled ? 0 : 1;
     k_fdm_forward<T><<<g.nt + 1 - k0, FDM_THREADS, shm, s>>>(g, Sxi, Syi, r, rh, k0, done);
-    k_fdm_recurrence<T><<<dim3((nxy + FDM_THREADS - 1) / FDM_THREADS, nslabs), FDM_THREADS, 0, s>>>(
-        g.nx, g.ny, (T)a, (T)b, lamx, lamy, rh, steps, coupled, done);
+    if (!coupled && steps <= FDM_SHORT_SLAB)
+        k_fdm_recurrence<T><<<dim3((nxy + FDM_THREADS - 1) / FDM_THREADS, nslabs), FDM_THREADS, 0, s>>>(
+            g.nx, g.ny, (T)a, (T)b, lamx, lamy, rh, steps, coupled, done);
+    else   // long slabs and the coupled march: blocked scan over time
+        launch_mode_scan<T>(nxy, rh, nxy, ModeEig2D<T>{lamx, lamy, g.nx, (T)a, (T)b}, n_cgs, g.nt,
+                            done, s);
     k_fdm_inverse<T><<<g.nt + 1, FDM_THREADS, shm, s>>>(g, Sx, Sy, r, rh, x, done);
     prof_end(s, PROF_SLAB, 2.0 * sizeof(T) * (double)g.interior());
     count_launch(3);

@@ -21,8 +21,11 @@
 // thread's R-1 factors are contiguous), and the shared array has one pad slot per 32
 // elements so that the strided stores of the early passes spread over the banks.
 // Three launches: forward transform of every row, the per-mode recurrence over each slab
-// (in place on the transformed rows), inverse transform of every row.
+// (in place on the transformed rows; a thread walks a short slab, longer slabs and the
+// coupled march over all steps, n_cgs = 0, take the blocked scan of scan.cuh), inverse
+// transform of every row.
 #include "kernels.h"
+#include "scan.cuh"
 
 namespace mk {
 
@@ -122,16 +125,18 @@ __device__ __forceinline__ void fft_smem(float2 *a, int N, int logN, const float
     else if (p == 1) stockham_pass<2>(a, N, Ns, tw);
 }
 
-// rh[k][j] = DST(r_k)_j for every row k = 1..nt.  Grid: one block per row.
+// rh[k][j] = DST(r_k)_j for every row k = k0..nt (k0 = 0 when the coupling to x_0 is kept).
+// Grid: one block per row.
 __global__ void __launch_bounds__(DST_THREADS) k_dst_forward(Geom g, const float *__restrict__ r,
                                                               float *__restrict__ rh, int ldd,
                                                               const float2 *__restrict__ tw,
                                                               int N2, int logN2,
+                                                              int k0,
                                                               const int *__restrict__ done) {
     if (done && *done) return;
     extern __shared__ float2 sm_dst[];
     float2 *a = sm_dst;
-    const int k = blockIdx.x + 1;
+    const int k = blockIdx.x + k0;
     const int n = g.nx, N = n + 1;
     const float *row = r + g.guard + (int64_t)k * g.plane;
     for (int m = threadIdx.x; m < N2; m += DST_THREADS) {
@@ -147,8 +152,10 @@ __global__ void __launch_bounds__(DST_THREADS) k_dst_forward(Geom g, const float
 }
 
 // In place on rh: xh_k = alpha_j xh_{k-1} + beta_j rh_k over each slab, xh = 0 before its
-// first step.  Grid: (modes / 128, slabs); the slab's rows are loaded 8 at a time.
+// first step.  Short slabs: one thread per (mode, slab) walks the slab's steps.  Grid:
+// (modes / 128, slabs); the slab's rows are loaded 8 at a time.
 constexpr int REC_THREADS = 128;
+constexpr int DST_SHORT_SLAB = 32;   // longer slabs (and the coupled march) take the blocked scan
 __global__ void __launch_bounds__(REC_THREADS) k_dst_recurrence(int n, float *__restrict__ rh, int ldd,
                                                                 const float *__restrict__ alpha,
                                                                 const float *__restrict__ beta,
@@ -231,12 +238,17 @@ void launch_slab_1d_dst(const Geom &g, const float *tab, const float2 *tw, int N
                         cudaStream_t s) {
     int logN2 = 0;
     while ((1 << logN2) < N2) ++logN2;
-    const int steps = g.nt / n_cgs;
+    const int coupled = n_cgs <= 0 ? 1 : 0;
+    const int steps = coupled ? g.nt : g.nt / n_cgs;
+    const int k0 = coupled ? 0 : 1;   // row 0 is transformed only when its coupling is kept
     const size_t shm = dst_smem_bytes(N2);
     prof_begin(s);
-    k_dst_forward<<<g.nt, DST_THREADS, shm, s>>>(g, r, rh, ldd, tw, N2, logN2, done);
-    k_dst_recurrence<<<dim3((g.nx + REC_THREADS - 1) / REC_THREADS, n_cgs), REC_THREADS, 0, s>>>(
-        g.nx, rh, ldd, tab, tab + g.nx, steps, done);
+    k_dst_forward<<<g.nt + 1 - k0, DST_THREADS, shm, s>>>(g, r, rh, ldd, tw, N2, logN2, k0, done);
+    if (!coupled && steps <= DST_SHORT_SLAB)
+        k_dst_recurrence<<<dim3((g.nx + REC_THREADS - 1) / REC_THREADS, n_cgs), REC_THREADS, 0, s>>>(
+            g.nx, rh, ldd, tab, tab + g.nx, steps, done);
+    else
+        launch_mode_scan<float>(g.nx, rh, ldd, ModeTable<float>{tab, tab + g.nx}, n_cgs, g.nt, done, s);
     k_dst_inverse<<<g.nt + 1, DST_THREADS, shm, s>>>(g, r, rh, ldd, tw, N2, logN2, x, done);
     prof_end(s, PROF_SLAB, 2.0 * sizeof(float) * (double)g.interior());
     count_launch(3);

@@ -136,7 +136,7 @@ static mk_status alloc_kstate(Level &L, int m) {
 
 mk_status build_dst_tables(Level &C, int n_cgs) {
     C.dstN2 = 0;
-    if (C.g.dim != 1 || n_cgs < 1 || C.g.nt % n_cgs != 0 || C.g.nt / n_cgs > 64) return MK_OK;
+    if (C.g.dim != 1 || n_cgs < 0 || (n_cgs > 0 && C.g.nt % n_cgs != 0)) return MK_OK;
     const int n = C.g.nx;
     const int N2 = dst_transform_size(n);
     double c = 0.0;

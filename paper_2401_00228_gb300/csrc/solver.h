@@ -126,8 +126,8 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
 // Time the tile depths of the 1D transfers on every level and the coarsest solver variants
 // on this hierarchy's own buffers, and keep the fastest (a few ms; state is reset by a solve).
 mk_status autotune_hierarchy(Hierarchy &H, cudaStream_t s);
-// Sine-transform slab tables for coarsest level C when they apply (1D, L uniform, n + 1 a
-// power of two, 1 <= n_cgs with at most 64 steps per slab); C.dstN2 stays 0 otherwise.
+// Sine-transform slab tables for coarsest level C when they apply (1D, L uniform, 2(n + 1) a
+// power of two up to 4096; any slab length, n_cgs = 0 included); C.dstN2 stays 0 otherwise.
 mk_status build_dst_tables(Level &C, int n_cgs);
 mk_status validate_opts(const Problem &P, const mk_solve_opts &o);
 

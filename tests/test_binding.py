@@ -91,3 +91,34 @@ def test_alternate_schedule_through_the_binding():
     assert [o.nu[i] for i in range(8)] == [2, 2, 2, 1, 2, 1, 2, 1]
     with pytest.raises(mk.MKError):
         mk.mk_schedule_alternate(2, n, n, nt, 1.0, dt, 1)   # fewer than 2 levels
+
+
+def test_noalloc_residual_checks_sizes_before_the_abi(monkeypatch):
+    """The allocation-free residual takes bare device pointers, so the binding checks every
+    array against the problem's shape first: a short array raises ValueError and no compute
+    entry point is reached (the stub library records any call)."""
+    calls = []
+
+    class Stub:
+        def mk_problem_shape(self, p, dim, nx, ny, nt, *rest):
+            dim._obj.value, nx._obj.value, ny._obj.value, nt._obj.value = 1, 63, 1, 256
+            return _lib.MK_OK
+
+        def __getattr__(self, name):
+            def rec(*a):
+                calls.append(name)
+                return _lib.MK_OK
+            return rec
+
+    monkeypatch.setattr(mk, "lib", lambda: Stub())
+    assert mk.mk_problem_shape(1) == (1, 63, 1, 256)
+    full, short = np.zeros(257 * 63), np.zeros(257 * 63 - 1)
+    one, steps = np.zeros(1), np.zeros(257)
+    for args in ((short, full, None, one, None), (full, short, None, one, None),
+                 (full, full, short, one, None), (full, full, None, np.zeros(0), None),
+                 (full, full, None, one, np.zeros(256))):
+        with pytest.raises(ValueError):
+            mk.mk_op_residual_noalloc(1, *args)
+    assert calls == []
+    mk.mk_op_residual_noalloc(1, full, full, full, one, steps)
+    assert calls == ["mk_op_residual_noalloc"]

@@ -97,3 +97,22 @@ def test_autograd_vs_central_differences():
                                      torch.tensor(tau, dtype=torch.float64))))
     fd_tau = (Js[0] - Js[1]) / (2 * ht)
     assert abs(fd_tau - grads[2]) <= 1e-6 * abs(grads[2])
+
+
+def test_heatsolve_leaves_the_problem_source():
+    """HeatSolve solves with its own g, then restores the source the Problem holds: a plain
+    solve on the same problem afterwards returns what it returned before."""
+    sched = W.Schedule((2, 2), (False, False), (1,), 16)
+    P = W.custom(1, 63, 256, 0.1, 1.0, 0.5, sched, seed=41, with_source=True)
+    dev = torch.device("cuda:0")
+    o = mk.make_opts(levels=3, nu=(2, 2), m_inner=(1,), n_cgs=16, tol=1e-12)
+    u0 = torch.from_numpy(P.u0).to(dev)
+    with mk.Problem(1, P.nx, P.tau, P.theta, P.dt, P.nt, torch.from_numpy(P.g).to(dev)) as p:
+        before = torch.empty((P.nt + 1, P.nx), dtype=torch.float64, device=dev)
+        mk.mk_solve(p.handle, u0, before, o)
+        g_other = torch.from_numpy(3.0 * P.g + 1.0).to(dev)
+        u = mk.HeatSolve.apply(p, u0, g_other, torch.tensor(P.tau, dtype=torch.float64), o)
+        after = torch.empty_like(before)
+        mk.mk_solve(p.handle, u0, after, o)
+        assert torch.equal(before, after)
+        assert not torch.allclose(u, before)

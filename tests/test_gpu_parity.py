@@ -183,6 +183,45 @@ def test_coarsest_exact_coupled(case):
     assert _rel(x, O.march(lv, r)) <= 1e-11
 
 
+@pytest.mark.parametrize("nx,nt,levels,n_cgs", [
+    (1023, 8192, 5, 0), (1023, 8192, 5, 1), (1023, 8192, 5, 2), (1023, 8192, 5, 4),
+    (255, 2048, 2, 0), (255, 2048, 2, 1), (63, 192, 2, 0), (63, 200, 2, 2)])
+def test_coarsest_uniform_1d_long_slabs(nx, nt, levels, n_cgs):
+    """Sine-transform coarsest solve with slabs longer than one thread's walk: the per-mode
+    recurrence runs as a blocked scan over time.  Covers the coupled march (n_cgs = 0: every
+    step's coupling kept, x_0 = r_0), one slab, slabs spanning several scan tiles (1024 steps,
+    1025 rows coupled: a ragged last tile) and slab lengths that are not a multiple of the
+    chunk (97 rows; two 50-step slabs).  FP32 against the FP64 oracle: the
+    recurrence of the slowest mode sums about 1/(1 - alpha_1) <= 60 terms here, so its rounding
+    stays below 1e-5 relative; 1e-4 leaves room for the transforms."""
+    sched = W.Schedule((2,) * (levels - 1), (False,) * (levels - 1),
+                       (2,) * max(levels - 3, 0) + ((1,) if levels > 2 else ()), n_cgs)
+    P = W.custom(1, nx, nt, 1.0, 1.0, 1.0, sched, seed=33)
+    H = _hier(P)
+    lv = H.levels[-1]
+    r = np.random.default_rng(28).standard_normal(lv.shape())
+    x = np.empty_like(r)
+    with _prob(P) as p:
+        mk.mk_op_coarsest(p.handle, _opts(sched), 1, r, x)
+    assert _rel(x, O.coarsest_solve(lv, r, n_cgs)) <= 1e-4
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-4)])
+@pytest.mark.parametrize("n_cgs", [0, 1, 2])
+def test_coarsest_2d_long_slabs(n_cgs, precision, tol):
+    """2D eigenbasis coarsest solve (16 x 16 after one 2 x 2 agglomeration, 128 coarse steps)
+    with the blocked time scan: coupled march, one slab of 128 steps, two of 64."""
+    sched = W.Schedule((2,), (True,), (), n_cgs)
+    P = W.custom(2, 31, 256, 0.05, 1.0, 0.5, sched, seed=34, ny=31)
+    H = _hier(P)
+    lv = H.levels[-1]
+    r = np.random.default_rng(29).standard_normal(lv.shape())
+    x = np.empty_like(r)
+    with _prob(P) as p:
+        mk.mk_op_coarsest(p.handle, _opts(sched), precision, r, x)
+    assert _rel(x, O.coarsest_solve(lv, r, n_cgs)) <= tol
+
+
 # --------------------------------------------------------------------------- a5
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-3)])
 def test_precondition_cycle(case, precision, tol):
