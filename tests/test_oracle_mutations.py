@@ -121,7 +121,13 @@ CASES = ([("mk_oracle.py",) + m for m in MUTATIONS] +
 def _run(base, selector):
     env = dict(os.environ)
     env.pop("PYTHONPATH", None)
-    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+    # no bytecode: a planted mistake of the same length written within the same second as
+    # the original would otherwise match a cached .pyc (keyed by mtime and size) and run stale
+    env["PYTHONDONTWRITEBYTECODE"] = "1"
+    for d, _, _ in os.walk(base):
+        if os.path.basename(d) == "__pycache__":
+            shutil.rmtree(d, ignore_errors=True)
+    return subprocess.run([sys.executable, "-B", "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                            "tests/test_oracle.py", "-k", selector],
                           cwd=base, capture_output=True, text=True, timeout=600, env=env)
 
