@@ -1,15 +1,20 @@
 """Benchmark: MK time-to-solution on one GB300 (or N replicas, one per GPU).
 
 Workload: 1D heat equation, n = 1023 interior points, theta = 1, n_t = 8192, T = 1, tau = 1,
-seeded u_0 (8 smooth modes) and a 4-mode space-time source; 5 time levels (nu = 2),
-16 decoupled coarsest slabs, inner FGMRES iterations 2,2,1, mixed precision (FP32 cycle,
-FP64 outer).  One step = one complete solve A_h u = f_h to the tolerance, inputs resident in
-HBM, L2 flushed (256 MB write) between steps.
+seeded u_0 (8 smooth modes) and a 4-mode space-time source; 5 time levels (nu = 2), mixed
+precision (FP32 cycle, FP64 outer).  The schedule knobs the method leaves free (the number
+of decoupled coarsest slabs, the restart length, the inner iteration counts) are picked by
+the library's autotuner (mk_tune) before the timed region; the line's config records them.
+One step = one complete solve A_h u = f_h to the tolerance, inputs resident in HBM, L2
+flushed (256 MB write) between steps.
 
-Printed: one JSON line (rank 0).  Beside the headline (mixed MK) it reports the FP64 MK and
-the GPU sequential theta-march on the same problem, the error of each against the CPU
-oracle, a kernel-class roofline from CUDA events, the oracle's own time on the host cores,
-and an end-to-end figure through host buffers.
+Printed: one JSON line (rank 0).  Beside the headline (mixed MK) it reports the FP64 MK, the
+base schedule, the fastest schedule at any level count and the GPU sequential theta-march on
+the same problem, the error of each against the CPU oracle, a kernel-class roofline from CUDA
+events, the oracle's own time on the host cores and an end-to-end figure through host
+buffers; then the 2D workload (with its own roofline, e2e and error against the oracle's full
+march, run in a host process beside the GPU work), the adjoint workload (forward + adjoint
+solve, gradients against the oracle), Tables 2 and 3's workloads and the 64-member batch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -179,49 +184,191 @@ def class_table(rows, top=10):
              "launches": int(r[2]), "GBps": round(r[1] / (r[0] * 1e-3) / 1e9, 1)} for r in rows[:top]]
 
 
-def bench_2d(mk, torch, dev, args, steps=2):
+def _oracle_march_to_file(dim, nx, ny, nt, tau, theta, dt, u0, g, path):
+    """Worker of the background oracle pool: the oracle's theta-march written to `path`."""
+    import oracle as O
+    t0 = time.perf_counter()
+    ref = O.theta_march(dim, nx, ny, nt, tau, theta, dt, u0, g)
+    np.save(path, ref)
+    return time.perf_counter() - t0
+
+
+def _oracle_misfit(dim, nx, ny, nt, tau, theta, dt, u0, g, u_target):
+    """Worker of the background oracle pool: the oracle's adjoint gradients of the misfit."""
+    import oracle as O
+    t0 = time.perf_counter()
+    J, gu0, gg, gtau, _ = O.misfit_gradients(dim, nx, ny, nt, tau, theta, dt, u0, g, u_target)
+    return J, gu0, gg, gtau, time.perf_counter() - t0
+
+
+def start_oracle_pool():
+    """A spawned pool of two host processes that runs the oracle for the 2D workloads while
+    the GPU paths are timed (the full 2D march of the 255^2 workload takes about a minute on
+    one core); results are collected after all GPU timing."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    pool = cf.ProcessPoolExecutor(max_workers=2, mp_context=mp.get_context("spawn"))
+    tmp = tempfile.mkdtemp()
+    P2 = W.heat2d_large()
+    PA = W.heat2d_adjoint()
+    jobs = {
+        "march_2d": (pool.submit(_oracle_march_to_file, 2, P2.nx, P2.ny, P2.nt, P2.tau, P2.theta,
+                                 P2.dt, P2.u0, P2.g, os.path.join(tmp, "ref2d.npy")),
+                     os.path.join(tmp, "ref2d.npy")),
+        "adjoint_2d": (pool.submit(_oracle_misfit, PA.dim, PA.nx, PA.ny, PA.nt, PA.tau, PA.theta,
+                                   PA.dt, PA.u0, PA.g, PA.u_target), None),
+    }
+    return pool, jobs, tmp
+
+
+def collect_oracle(paths, pool, jobs, tmp):
+    """Wait for the background oracle and add its errors to the 2D and adjoint paths."""
+    p2 = paths.get("mk_mixed_2d", {})
+    u2 = p2.pop("u_host", None)
+    fut, path = jobs["march_2d"]
+    try:
+        t_or = fut.result()
+        ref = np.load(path, mmap_mode="r")
+        if u2 is not None:
+            p2["max_rel_err"] = float(np.max(np.abs(u2 - ref)) / np.max(np.abs(ref)))
+            p2["error_target_met"] = bool(p2["max_rel_err"] <= 1e-8)
+        p2["cpu_baseline"] = {"value": t_or, "unit": "s", "cores": 1, "kind": "oracle",
+                              "sample": "the 2D workload's full sequential FP64 theta-march (banded "
+                                        "LU, plain C), once, in a host process beside the GPU runs"}
+        del ref
+    except Exception as e:
+        p2["oracle_error"] = str(e)[:200]
+    pa = paths.get("adjoint_2d", {})
+    grads = pa.pop("grads", None)
+    try:
+        J, gu0, gg, gtau, t_adj = jobs["adjoint_2d"][0].result()
+        if grads is not None:
+            def rel(a, b):
+                return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+            pa["grad_rel_err"] = {"u0": rel(grads[0], gu0), "g": rel(grads[1], gg),
+                                  "tau": abs(grads[2] - gtau) / abs(gtau)}
+        pa["oracle_cpu_s"] = t_adj
+    except Exception as e:
+        pa["oracle_error"] = str(e)[:200]
+    pool.shutdown()
+    try:
+        os.remove(path)
+        os.rmdir(tmp)
+    except OSError:
+        pass
+
+
+def _ev_time(torch, fn, steps, flush=None):
+    """Mean device time (CUDA events on the current stream) of `steps` calls of fn after one
+    untimed call; returns (seconds, last result)."""
+    r = fn()
+    ts = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.mean(ts), r
+
+
+def roofline_of(rows, peak, peak_kind):
+    """Roofline object of the dominant kernel class of a profiled solve (no DRAM counters
+    taken for it: traffic null unless a ratio was measured)."""
+    top = rows[0]
+    ach = top[1] / (top[0] * 1e-3) / 1e9
+    kname = f"{top[3]}@level{top[4]}"
+    ratio = DRAM_TRAFFIC_RATIO.get(kname)
+    return {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_kind": peak_kind,
+            "traffic": (ratio * top[1] / top[2]) if ratio else None,
+            "traffic_unit": "bytes per launch", "alg_bytes_per_launch": top[1] / top[2],
+            "launches": int(top[2]), "avg_launch_us": top[0] / top[2] * 1e3}
+
+
+def bench_2d(mk, torch, dev, args, flush, steps=2):
     """The 2D workload: 255 x 255 interior points, theta = 1/2, n_t = 1024, T = 0.05, mixed
     precision, 4 levels nu = 2 with 2 x 2 agglomeration per coarsening (66.7 M space-time
-    points).  Its error against the oracle is checked on sampled steps by the parity tests
-    (a full CPU march of this size takes tens of seconds)."""
+    points), n_cgs from the schedule autotuner (mk_tune), tol --tol-2d.  Reported: time to
+    solution (device, inputs in HBM), the same solve through host buffers (e2e), the GPU
+    theta-march, a roofline object of the dominant kernel class, and (filled in later from the
+    background oracle) the max relative error against the oracle's full march."""
     P = W.heat2d_large()
     s = P.schedule
-    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=s.n_cgs,
-                     tol=args.tol_2d, restart=args.restart, precision="mixed", orth=args.orth,
-                     autotune=not args.no_autotune)
+    base = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=s.n_cgs,
+                        tol=args.tol_2d, restart=args.restart, precision="mixed", orth=args.orth,
+                        autotune=not args.no_autotune, max_iters=3000)
     u0 = torch.from_numpy(P.u0).to(dev)
     u = torch.empty((P.nt + 1,) + P.space_shape(), dtype=torch.float64, device=dev)
+    out = {"workload": "heat2d_255x255_nt1024_theta0.5_T0.05_L4_nu2_2x2space", "tol": args.tol_2d,
+           "points": int(P.nx * P.ny * (P.nt + 1))}
     with mk.Problem(P.dim, P.nx, P.tau, P.theta, P.dt, P.nt, None, ny=P.ny) as p:
-        mk.mk_solve(p.handle, u0, u, o)
-        ts, info = [], None
-        for _ in range(steps):
-            torch.cuda.synchronize(dev)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            info = mk.mk_solve(p.handle, u0, u, o)
-            e1.record()
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1) / 1e3)
-        # the sequential theta-march on the GPU (one sine-transform solve per step)
+        o = base
+        if not args.no_tune:
+            o, ti = mk.mk_tune(p.handle, u0, base, max_trials=args.tune_trials_2d)
+            out["tuned"] = {"trials": int(ti.trials), "tune_s": ti.tune_ms / 1e3}
+        out["config"] = {"levels": int(o.levels), "n_cgs": int(o.n_cgs), "restart": int(o.restart),
+                         "m_inner": [int(x) for x in list(o.m_inner)[:o.levels - 2]]}
+        t, info = _ev_time(torch, lambda: mk.mk_solve(p.handle, u0, u, o), steps, flush)
+        out.update({"s": t, "iterations": int(info.iterations), "rel_residual": info.rel_residual})
+        out["u_host"] = u.cpu().numpy()       # compared with the oracle after all timing
         um = torch.empty_like(u)
-        mk.mk_march(p.handle, u0, um)
-        tm = []
-        for _ in range(steps):
+        t_m, _ = _ev_time(torch, lambda: mk.mk_march(p.handle, u0, um), steps, flush)
+        out["march_gpu_s"] = t_m
+        out["max_rel_diff_vs_march"] = float(((um - u).abs().max() / um.abs().max()).item())
+        rows = profiled_classes(mk, torch, dev, lambda: mk.mk_solve(p.handle, u0, u, o))
+        peak, peak_kind = _peaks()
+        out["roofline"] = roofline_of(rows, peak, peak_kind)
+        out["kernel_classes"] = class_table(rows)
+        # end to end through the public API with host buffers (u_0 in, u out)
+        u0_h = torch.from_numpy(P.u0).pin_memory()
+        u_h = torch.empty(tuple(u.shape), dtype=torch.float64).pin_memory()
+        te = []
+        for i in range(steps + 1):
             torch.cuda.synchronize(dev)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            mk.mk_march(p.handle, u0, um)
-            e1.record()
-            e1.synchronize()
-            tm.append(e0.elapsed_time(e1) / 1e3)
-        march_err = float(((um - u).abs().max() / um.abs().max()).item())
-        classes = class_table(profiled_classes(mk, torch, dev, lambda: mk.mk_solve(p.handle, u0, u, o)))
-    return {"s": statistics.mean(ts), "iterations": int(info.iterations), "kernel_classes": classes,
-            "march_gpu_s": statistics.mean(tm), "max_rel_diff_vs_march": march_err,
-            "rel_residual": info.rel_residual, "points": int(P.nx * P.ny * (P.nt + 1)),
-            "workload": "heat2d_255x255_nt1024_theta0.5_T0.05_L4_nu2_2x2space", "tol": args.tol_2d}
+            t0 = time.perf_counter()
+            mk.mk_solve(p.handle, u0_h, u_h, o)
+            if i:
+                te.append(time.perf_counter() - t0)
+        out["e2e"] = {"value": statistics.mean(te), "unit": "s",
+                      "h2d_bytes_per_step": int(P.u0.nbytes), "d2h_bytes_per_step": int(u_h.numel() * 8)}
+    return out
+
+
+def bench_adjoint(mk, torch, dev, args, steps=2):
+    """The adjoint workload (Sec. 2, Eq. (finesys) transposed): 2D 127 x 127, theta = 1,
+    n_t = 512, T = 0.05, FP64, 4 levels with 2 x 2 agglomeration; loss ||u_nt - u_target||^2.
+    One step = the forward MK solve plus the adjoint MK solve (gradients w.r.t. u_0, g and
+    tau), tol 1e-12; the gradients are compared with the oracle's adjoint march later."""
+    P = W.heat2d_adjoint()
+    s = P.schedule
+    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=s.n_cgs,
+                     tol=1e-12, precision="fp64", max_iters=4000, autotune=True)
+    u0 = torch.from_numpy(P.u0).to(dev)
+    g = torch.from_numpy(P.g).to(dev)
+    tgt = torch.from_numpy(P.u_target).to(dev)
+    u = torch.empty((P.nt + 1,) + P.space_shape(), dtype=torch.float64, device=dev)
+    dJdu = torch.zeros_like(u)
+    gu0 = torch.empty(P.space_shape(), dtype=torch.float64, device=dev)
+    gg = torch.empty_like(u)
+    res = {}
+    with mk.Problem(P.dim, P.nx, P.tau, P.theta, P.dt, P.nt, g, ny=P.ny) as p:
+        def step():
+            fi = mk.mk_solve(p.handle, u0, u, o)
+            dJdu[-1] = 2.0 * (u[-1] - tgt)
+            gt, ai = mk.mk_adjoint(p.handle, u, dJdu, o, grad_u0=gu0, grad_g=gg, want_tau=True)
+            res.update(fwd=fi, adj=ai, gtau=gt)
+            return fi
+        t, _ = _ev_time(torch, step, steps)
+        tf, _ = _ev_time(torch, lambda: mk.mk_solve(p.handle, u0, u, o), steps)
+    return {"workload": "heat2d_127x127_nt512_theta1_T0.05_L4_adjoint_fp64", "s": t,
+            "forward_s": tf, "adjoint_s": t - tf,
+            "iterations_forward": int(res["fwd"].iterations), "iterations_adjoint": int(res["adj"].iterations),
+            "grads": (gu0.cpu().numpy(), gg.cpu().numpy(), float(res["gtau"]))}
 
 
 def bench_alternate(mk, torch, dev, steps=2):
@@ -330,48 +477,89 @@ def profile_2d():
     print(json.dumps({"profile_2d": "heat2d_255x255_nt512", "iterations": int(info.iterations)}))
 
 
-def bench_batch(mk, torch, dev, count_1d=12, count_2d=4, max_iters=600):
-    """16 members of the uneven batched workload (1D n 63..2047 x n_t 256..8192, 2D side
-    63..255 x n_t 128..1024, tau log-uniform [0.1, 10], theta in {1/2, 1}; mixed, tol 1e-10):
-    one autotuned batch against the same members solved one after another."""
+def bench_batch(mk, torch, dev, args, count_1d=48, count_2d=16, max_iters=3000):
+    """The uneven batched workload: 64 members (48 1D with n in 63..2047 and n_t in
+    256..8192, 16 2D with side 63..255 and n_t 128..1024, tau log-uniform in [0.1, 10], theta in
+    {1/2, 1}, end time from a Courant number in the range of its theta), mixed precision, tol
+    1e-10.  Each member's schedule comes from the autotuner (mk_tune: the level count too for
+    1D members, n_cgs, restart, inner counts; a bounded number of trial solves, outside the
+    timed region), then all 64 run as one batch whose replay is one CUDA graph per restart
+    cycle (tile autotuning on).  Compared, on the same members: the same solves one after
+    another, the plain FP64 MK solve of each member (its base schedule) and the GPU
+    theta-march of each member; the batch's errors against the marches (themselves pinned to
+    the oracle by the tests)."""
     ms = W.batched_problems(seed=4, count_1d=count_1d, count_2d=count_2d)
 
-    def opts(P):
+    def base(P, precision):
         s = P.schedule
         return mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner,
-                            n_cgs=s.n_cgs, tol=P.tol, precision=P.precision, max_iters=max_iters)
+                            n_cgs=s.n_cgs, tol=P.tol, precision=precision, max_iters=max_iters,
+                            restart=24)
 
-    probs = [mk.Problem(P.dim, P.nx, P.tau, P.theta, P.dt, P.nt,
-                        None if P.g is None else torch.from_numpy(P.g).to(dev), ny=P.ny) for P in ms]
+    probs = [mk.Problem(P.dim, P.nx, P.tau, P.theta, P.dt, P.nt, None, ny=P.ny) for P in ms]
     u0 = [torch.from_numpy(P.u0).to(dev) for P in ms]
     outs = [torch.empty((P.nt + 1,) + P.space_shape(), dtype=torch.float64, device=dev) for P in ms]
-    ol = [opts(P) for P in ms]
     points = int(sum(P.nx * P.ny * (P.nt + 1) for P in ms))
+    t0 = time.perf_counter()
+    ol, trials = [], 0
+    for P, p, x in zip(ms, probs, u0):
+        if args.no_tune:
+            ol.append(base(P, "mixed"))
+            continue
+        o, ti = mk.mk_tune(p.handle, x, base(P, "mixed"), levels=(P.dim == 1),
+                           max_trials=args.tune_trials_batch, restart_cap=True)
+        ol.append(o)
+        trials += int(ti.trials)
+    t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
     b = mk.Batch(probs, ol, autotune=True)
     t_setup = time.perf_counter() - t0
     b.solve(u0, outs, allow_not_converged=True)          # warm-up
     torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
     infos = b.solve(u0, outs, allow_not_converged=True)
-    t_batch = time.perf_counter() - t0
+    e1.record()
+    e1.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
     b.close()
-    for p, o, x, y in zip(probs, ol, u0, outs):          # warm-up of the single solves
-        mk.mk_solve(p.handle, x, y, o, allow_not_converged=True)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for p, o, x, y in zip(probs, ol, u0, outs):
-        mk.mk_solve(p.handle, x, y, o, allow_not_converged=True)
-    torch.cuda.synchronize(dev)
-    t_seq = time.perf_counter() - t0
+
+    def seq_time(fn):
+        # one member at a time (a warm-up solve builds its workspace, then a timed solve; the
+        # workspace is freed before the next member, so 64 of them never coexist)
+        tot = 0.0
+        for p, x, y, k in zip(probs, u0, outs, range(len(ms))):
+            fn(k, p, x, y)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(k, p, x, y)
+            e1.record()
+            e1.synchronize()
+            tot += e0.elapsed_time(e1) / 1e3
+            mk.mk_trim(p.handle)
+        return tot
+
+    res_batch = [y.clone() for y in outs]
+    t_seq = seq_time(lambda k, p, x, y: mk.mk_solve(p.handle, x, y, ol[k], allow_not_converged=True))
+    o64 = [base(P, "fp64") for P in ms]
+    t_fp64 = seq_time(lambda k, p, x, y: mk.mk_solve(p.handle, x, y, o64[k], allow_not_converged=True))
+    t_march = seq_time(lambda k, p, x, y: mk.mk_march(p.handle, x, y))
+    errs = [float(((r - m).abs().max() / m.abs().max()).item()) for r, m in zip(res_batch, outs)]
     for p in probs:
         p.close()
     conv = [i.rel_residual <= 1.0001 * P.tol for i, P in zip(infos, ms)]
     return {"problems": len(ms), "points": points, "s": t_batch, "sequential_s": t_seq,
-            "speedup_vs_sequential": t_seq / t_batch, "setup_s": t_setup,
-            "Gpoints_per_s": points / t_batch / 1e9, "converged": int(sum(conv)),
-            "max_iters": max_iters, "iterations": [int(i.iterations) for i in infos],
-            "workload": "batched_problems(seed=4) members 0-11 (1D) and 48-51 (2D), mixed, tol 1e-10"}
+            "mk_fp64_sequential_s": t_fp64, "march_gpu_sequential_s": t_march,
+            "speedup_vs_sequential": t_seq / t_batch, "relative_to_march": t_batch / t_march,
+            "relative_to_fp64_mk": t_batch / t_fp64, "setup_s": t_setup, "tune_s": t_tune,
+            "tune_trials": trials, "Gpoints_per_s": points / t_batch / 1e9,
+            "converged": int(sum(conv)), "max_rel_diff_vs_march": max(errs),
+            "levels": [int(o.levels) for o in ol], "n_cgs": [int(o.n_cgs) for o in ol],
+            "iterations": [int(i.iterations) for i in infos],
+            "workload": "batched_problems(seed=4): 48 1D + 16 2D members, mixed, tol 1e-10"}
 
 
 def main():
@@ -390,6 +578,15 @@ def main():
     ap.add_argument("--restart", type=int, default=40)
     ap.add_argument("--orth", type=int, default=0, help="Gram-Schmidt passes: 0 one, 1 conditional, 2 two")
     ap.add_argument("--no-aux", action="store_true", help="skip the secondary paths")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-member batch path")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="the workloads' base schedules instead of the schedule autotuner")
+    ap.add_argument("--tune-trials", type=int, default=40,
+                    help="trial solves of the schedule autotuner on the headline workload")
+    ap.add_argument("--tune-trials-fp64", type=int, default=8)
+    ap.add_argument("--tune-trials-2d", type=int, default=6)
+    ap.add_argument("--tune-trials-batch", type=int, default=8,
+                    help="trial solves per member of the batch")
     ap.add_argument("--no-autotune", action="store_true",
                     help="built-in tile heuristics instead of the per-hierarchy autotuner")
     ap.add_argument("--profile-run", action="store_true",
@@ -429,7 +626,7 @@ def main():
                             n_cgs=s.n_cgs, tol=args.tol, restart=args.restart, precision=precision,
                             orth=args.orth, autotune=not args.no_autotune)
 
-    o_mixed, o_fp64 = opts("mixed"), opts("fp64")
+    base_mixed, base_fp64 = opts("mixed"), opts("fp64")
     g_dev = torch.from_numpy(P.g).to(dev)
     u0_dev = torch.from_numpy(P.u0).to(dev)
     u_dev = torch.empty((P.nt + 1, P.nx), dtype=torch.float64, device=dev)
@@ -461,12 +658,25 @@ def main():
         launches = mk.mk_kernel_launch_count() - l0
         return times, infos, launches
 
+    def sched(o):
+        return {"levels": int(o.levels), "n_cgs": int(o.n_cgs), "restart": int(o.restart),
+                "m_inner": [int(x) for x in list(o.m_inner)[:max(o.levels - 2, 0)]]}
+
+    # ---------------- schedule autotuning (before the timed region) ----------------
+    tuning = {}
+    o_mixed = base_mixed
+    if not args.no_tune:
+        o_mixed, ti = mk.mk_tune(prob.handle, u0_dev, base_mixed, max_trials=args.tune_trials)
+        tuning = {"trials": int(ti.trials), "tune_s": ti.tune_ms / 1e3,
+                  "searched": "n_cgs, restart, inner iteration counts (5 levels as configured)"}
+
     if args.profile_run:
         for _ in range(2):
             info = mk.mk_solve(prob.handle, u0_dev, u_dev, o_mixed)
         torch.cuda.synchronize(dev)
         print(json.dumps({"profile_run": WORKLOAD, "iterations": int(info.iterations),
-                          "launches_per_solve": int(info.kernel_launches)}), flush=True)
+                          "launches_per_solve": int(info.kernel_launches), "schedule": sched(o_mixed)}),
+              flush=True)
         prob.close()
         return
 
@@ -478,25 +688,33 @@ def main():
     ms_mixed = max_over_ranks(statistics.mean(t_mixed), dist, dev)
     u_mixed = u_dev.cpu().numpy().copy()
 
+    cfg = {"workload": WORKLOAD, "nx": P.nx, "nt": P.nt, "theta": P.theta, "levels": s.levels,
+           "nu": list(s.nu), "precision": "mixed", "tol": args.tol, "orth": args.orth,
+           "autotune": not args.no_autotune, "parallelism": f"replicas x{world}",
+           "l2": "flushed between steps (256 MB write)"}
+    cfg.update(sched(o_mixed))
+    if tuning:
+        cfg["schedule_tuning"] = tuning
     line = {"metric": METRIC, "value": ms_mixed / 1e3, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 cycle + f64 outer", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": P.nx, "nt": P.nt, "theta": P.theta,
-                       "levels": s.levels, "nu": list(s.nu), "m_inner": list(s.m_inner),
-                       "n_cgs": s.n_cgs, "restart": args.restart, "tol": args.tol, "orth": args.orth,
-                       "autotune": not args.no_autotune,
-                       "precision": "mixed", "parallelism": f"replicas x{world}",
-                       "l2": "flushed between steps (256 MB write)"},
+            "dtype": "f32 cycle + f64 outer", "data": "synthetic", "config": cfg,
             "gpu_launches": int(launches),
             "iterations": int(inf_mixed[-1].iterations)}
     if clk:
         line["clocks"] = clk
 
     if rank == 0 and not args.no_aux:
-        # ---------------- secondary paths ----------------
+        pool, ojobs, otmp = start_oracle_pool()
+        line["paths"] = {}
+        # ---------------- secondary paths on the headline problem ----------------
+        o_fp64 = base_fp64
+        if not args.no_tune:
+            o_fp64, _ = mk.mk_tune(prob.handle, u0_dev, base_fp64, max_trials=args.tune_trials_fp64)
         t_fp64, inf_fp64, _ = timed(o_fp64, 2, 1)
         u_fp64 = u_dev.cpu().numpy().copy()
+        t_def, inf_def, _ = timed(base_mixed, 2, 1)
+        u_def = u_dev.cpu().numpy().copy()
         tm = []
         for i in range(4):
             flush.fill_(1.0)
@@ -509,46 +727,43 @@ def main():
             if i > 0:
                 tm.append(e0.elapsed_time(e1))
         u_march = u_dev.cpu().numpy().copy()
+        # any level count (the two-level method with the exact coarse solve is a candidate)
+        o_any, ti_any = mk.mk_tune(prob.handle, u0_dev, base_mixed, levels=True,
+                                   max_trials=args.tune_trials)
+        t_any, inf_any, _ = timed(o_any, 5, 2)
+        u_any = u_dev.cpu().numpy().copy()
 
-        # ---------------- 2D workload (255 x 255, n_t = 1024, 4 levels with 2 x 2 agglomeration) ----
-        line["paths"] = {}
+        # ---------------- config 3: 2D 255 x 255, n_t = 1024 ----------------
         try:
-            line["paths"]["mk_mixed_2d"] = bench_2d(mk, torch, dev, args)
+            line["paths"]["mk_mixed_2d"] = bench_2d(mk, torch, dev, args, flush)
         except Exception as e:
             line["paths"]["mk_mixed_2d"] = {"error": str(e)[:200]}
-
+        # ---------------- config 4: adjoint, 2D 127 x 127, n_t = 512 ----------------
+        try:
+            line["paths"]["adjoint_2d"] = bench_adjoint(mk, torch, dev, args)
+        except Exception as e:
+            line["paths"]["adjoint_2d"] = {"error": str(e)[:200]}
         # ---------------- Table 3 workload: alternate time-space coarsening, 7-11 levels ----
         try:
             line["paths"]["mk_alternate_2d"] = bench_alternate(mk, torch, dev)
         except Exception as e:
             line["paths"]["mk_alternate_2d"] = {"error": str(e)[:200]}
-
         # ---------------- Table 2: two-level T / TS / MGRIT transfers ----------------
         try:
             line["paths"]["two_level_table2"] = bench_two_level(mk, torch, dev)
         except Exception as e:
             line["paths"]["two_level_table2"] = {"error": str(e)[:200]}
-
-        # ---------------- batched uneven problems ----------------
-        try:
-            line["paths"]["mk_batch"] = bench_batch(mk, torch, dev)
-        except Exception as e:   # reported, not fatal: the headline does not depend on it
-            line["paths"]["mk_batch"] = {"error": str(e)[:200]}
+        # ---------------- config 5: 64 uneven problems in one batch ----------------
+        if not args.no_batch:
+            try:
+                line["paths"]["mk_batch"] = bench_batch(mk, torch, dev, args)
+            except Exception as e:   # reported, not fatal: the headline does not depend on it
+                line["paths"]["mk_batch"] = {"error": str(e)[:200]}
 
         # ---------------- roofline: kernel-class timing of one profiled solve ----------------
         rows = profiled_classes(mk, torch, dev, lambda: mk.mk_solve(prob.handle, u0_dev, u_dev, o_mixed))
         peak, peak_kind = _peaks()
-        top = rows[0]
-        ach = top[1] / (top[0] * 1e-3) / 1e9
-        kname = f"{top[3]}@level{top[4]}"
-        ratio = DRAM_TRAFFIC_RATIO.get(kname)
-        line["roofline"] = {"bound": "hbm", "kernel": kname,
-                            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                            "peak_kind": peak_kind,
-                            "traffic": (ratio * top[1] / top[2]) if ratio else None,
-                            "traffic_unit": "bytes per launch",
-                            "alg_bytes_per_launch": top[1] / top[2],
-                            "launches": int(top[2]), "avg_launch_us": top[0] / top[2] * 1e3}
+        line["roofline"] = roofline_of(rows, peak, peak_kind)
         line["kernel_classes"] = class_table(rows)
 
         # ---------------- e2e through host buffers ----------------
@@ -581,17 +796,27 @@ def main():
                                           "Thomas algorithm, plain C)"}
         line["paths"].update({
             "mk_mixed": {"s": ms_mixed / 1e3, "iterations": int(inf_mixed[-1].iterations),
-                         "rel_residual": inf_mixed[-1].rel_residual,
+                         "rel_residual": inf_mixed[-1].rel_residual, "schedule": sched(o_mixed),
                          "max_rel_err": O.max_rel_error(u_mixed, ref)},
+            "mk_mixed_default_schedule": {"s": statistics.mean(t_def) / 1e3,
+                                          "iterations": int(inf_def[-1].iterations),
+                                          "schedule": sched(base_mixed),
+                                          "max_rel_err": O.max_rel_error(u_def, ref)},
             "mk_fp64": {"s": statistics.mean(t_fp64) / 1e3, "iterations": int(inf_fp64[-1].iterations),
-                        "rel_residual": inf_fp64[-1].rel_residual,
+                        "rel_residual": inf_fp64[-1].rel_residual, "schedule": sched(o_fp64),
                         "max_rel_err": O.max_rel_error(u_fp64, ref)},
+            "mk_mixed_any_levels": {"s": statistics.mean(t_any) / 1e3,
+                                    "iterations": int(inf_any[-1].iterations),
+                                    "schedule": sched(o_any), "tune_trials": int(ti_any.trials),
+                                    "relative_to_march": statistics.mean(t_any) / statistics.mean(tm),
+                                    "max_rel_err": O.max_rel_error(u_any, ref)},
             "march_gpu_fp64": {"s": statistics.mean(tm) / 1e3, "max_rel_err": O.max_rel_error(u_march, ref)},
             "oracle_cpu": {"s": statistics.median(tc)},
         })
         # the metric is time to a solution within 1e-8 max relative error of the oracle
         line["error_target"] = 1e-8
         line["error_target_met"] = bool(line["paths"]["mk_mixed"]["max_rel_err"] <= 1e-8)
+        collect_oracle(line["paths"], pool, ojobs, otmp)
     prob.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -80,7 +80,10 @@ typedef struct mk_solve_opts {
     int32_t m_inner[MK_MAX_LEVELS]; /* fixed FGMRES iterations on level l+2 (entries 0..L-3); default 2,
                                        and 1 on the level just above the coarsest (Sec. 4.2) */
     int32_t n_cgs;       /* decoupled slabs on the coarsest level (Sec. 3.3.2); 0 = exact coupled
-                            coarse solve (sequential); default 16 */
+                            coarse solve (Sec. 3.3.1).  The eigenbasis solvers (1D uniform
+                            operator in the mixed path, 2D) handle any slab length, the coupled
+                            march included, in parallel over time; the other 1D solvers step
+                            through each slab sequentially.  Default 16 */
     int32_t mu_mode;     /* 0: mu_l = lambda_max(A_l) (Sec. 3.1); 1: mu = 1; 2: mu = mu_value */
     double mu_value;
     int32_t precision;   /* 0: FP64 throughout.  1: mixed -- MK cycle, transfers, inner levels and
@@ -189,6 +192,11 @@ mk_status mk_set_source(mk_problem *p, const double *g, void *stream);
 /* Frees the problem and all its workspace.  NULL is ignored. */
 void mk_destroy(mk_problem *p);
 
+/* Frees the solver workspace the problem keeps for the options of its last solve (Krylov
+   bases, level vectors, coarsest tables, captured graph); the next mk_solve rebuilds it.
+   Synchronises the device first.  Errors: MK_ERR_INVALID (NULL p), MK_ERR_CUDA. */
+mk_status mk_trim(mk_problem *p);
+
 /*
  * mk_solve -- solve A_h u = f_h (f_0 = u0) by FGMRES (Algorithm 2) right-preconditioned by
  * the MK cycle Q (Eq. (Qh), substeps 4.1-4.5, recursion of Sec. 4.1, decoupled coarsest
@@ -246,6 +254,36 @@ mk_status mk_adjoint(mk_problem *p, const double *u, const double *dJdu,
    Errors: MK_ERR_INVALID (NULL p). */
 mk_status mk_problem_shape(const mk_problem *p, int32_t *dim, int32_t *nx, int32_t *ny, int32_t *nt,
                            double *theta, double *dt, double *tau);
+
+/* mk_tune -- schedule autotuner for one problem: picks the knobs the method leaves free by
+   timing complete solves of this problem (its source as set, initial state u0, host or
+   device) to base->tol.  Starting from *base (NULL: defaults), one pass of coordinate
+   descent over
+     - with MK_TUNE_LEVELS in flags: the level count 2 .. base->levels (base's nu and space,
+       inner counts 2 and 1 above the coarsest, the exact coarse solve where it is parallel);
+     - n_cgs (Sec. 3.3.2) in {base, 16, 8, 4, 2, 1, 0} (0 is left out for the FP64 path in 1D,
+       whose coupled coarse march is sequential);
+     - restart (Algorithm 2) in {8, 12, 16, 24, 32, 40, 64} (with MK_TUNE_RESTART_CAP only
+       those up to base->restart: the level-1 basis grows with it);
+     - each inner iteration count m_inner (Sec. 4.1) +1 and -1;
+   keeping at each step the fastest candidate that converges within base->max_iters (others,
+   and candidates the library rejects, are skipped).  At most max_trials solves (0: no limit).
+   *best receives the chosen options (tile autotuning on); info (may be NULL) the number of
+   solves, the best solve's time and iterations and the wall time of the tuning.  Allocates
+   one solution buffer for the trials and frees it, and frees the workspace of the last trial
+   (as mk_trim).  Synchronises the device.
+   Errors: MK_ERR_INVALID (NULL p, u0 or best), MK_ERR_NOMEM, MK_ERR_CUDA from a trial,
+   MK_ERR_NOT_CONVERGED when no candidate converged (best unchanged). */
+#define MK_TUNE_LEVELS 1
+#define MK_TUNE_RESTART_CAP 2   /* restart candidates only up to base->restart (bounds memory) */
+typedef struct mk_tune_info {
+    int32_t trials;           /* solves run */
+    int32_t best_iterations;  /* outer iterations of the chosen options */
+    double best_ms;           /* device time of the chosen options' solve */
+    double tune_ms;           /* wall time of the whole tuning */
+} mk_tune_info;
+mk_status mk_tune(mk_problem *p, const double *u0, const mk_solve_opts *base, int32_t flags,
+                  int32_t max_trials, mk_solve_opts *best, mk_tune_info *info, void *stream);
 
 /* ------------------------------------------------------------------------------------
  * Operator-level entry points.  Each runs one step of the hot path on dense FP64 arrays

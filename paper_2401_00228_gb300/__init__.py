@@ -15,10 +15,10 @@ import numpy as np
 
 from . import _lib
 from ._lib import (MK_MAX_LEVELS, MKError, mk_level_desc, mk_solve_info, mk_solve_opts,
-                   mk_stencil)
+                   mk_stencil, mk_tune_info)
 
 __all__ = ["mk_default_opts", "mk_create_problem", "mk_set_source", "mk_destroy", "mk_solve",
-           "mk_solve_rhs", "mk_march", "mk_schedule_alternate", "mk_adjoint", "mk_level_info", "mk_op_rhs", "mk_op_apply",
+           "mk_solve_rhs", "mk_march", "mk_tune", "mk_trim", "mk_schedule_alternate", "mk_adjoint", "mk_level_info", "mk_op_rhs", "mk_op_apply",
            "mk_op_residual", "mk_op_residual_noalloc", "mk_problem_shape", "mk_op_restrict", "mk_op_interp_correct", "mk_op_coarsest",
            "mk_op_precond", "mk_op_orthogonalize", "mk_op_lsq", "mk_kernel_launch_count",
            "mk_create_batch", "mk_solve_batch", "mk_destroy_batch", "Batch",
@@ -214,6 +214,25 @@ def mk_solve_rhs(p: int, f, u_out, opts: Optional[mk_solve_opts] = None, stream=
     _lib.check(lib().mk_solve_rhs(p, _ptr(f), ctypes.byref(opts) if opts else None, _ptr(u_out),
                                   ctypes.byref(info), s), "mk_solve_rhs")
     return info
+
+
+def mk_tune(p: int, u0, base: Optional[mk_solve_opts] = None, levels: bool = False,
+            max_trials: int = 0, restart_cap: bool = False, stream=None):
+    """Schedule autotuner: (best options, mk_tune_info) from timed solves of this problem
+    (n_cgs, restart -- at most base.restart when `restart_cap` --, inner iteration counts; the
+    level count too when `levels`)."""
+    best = mk_solve_opts()
+    info = mk_tune_info()
+    s = _stream(stream) or _current_stream_for(u0)
+    flags = (_lib.MK_TUNE_LEVELS if levels else 0) | (_lib.MK_TUNE_RESTART_CAP if restart_cap else 0)
+    _lib.check(lib().mk_tune(p, _ptr(u0), ctypes.byref(base) if base else None, flags, max_trials,
+                             ctypes.byref(best), ctypes.byref(info), s), "mk_tune")
+    return best, info
+
+
+def mk_trim(p: int) -> None:
+    """Free the solver workspace the problem keeps for its last options."""
+    _lib.check(lib().mk_trim(p), "mk_trim")
 
 
 def mk_march(p: int, u0, u_out, stream=None) -> None:

@@ -48,6 +48,14 @@ class mk_level_desc(ctypes.Structure):
                 ("mu", ctypes.c_double)]
 
 
+class mk_tune_info(ctypes.Structure):
+    _fields_ = [("trials", ctypes.c_int32), ("best_iterations", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("tune_ms", ctypes.c_double)]
+
+
+MK_TUNE_LEVELS = 1
+MK_TUNE_RESTART_CAP = 2
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int32
@@ -70,12 +78,15 @@ SIGNATURES = {
     "mk_create_problem": (ctypes.c_int, [ctypes.POINTER(mk_stencil), _D, _D, _I, _P, ctypes.POINTER(_P)]),
     "mk_set_source": (ctypes.c_int, [_P, _P, _P]),
     "mk_destroy": (None, [_P]),
+    "mk_trim": (ctypes.c_int, [_P]),
     "mk_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(mk_solve_opts), _P, ctypes.POINTER(mk_solve_info), _P]),
     "mk_create_batch": (ctypes.c_int, [_P, _I, ctypes.POINTER(mk_solve_opts), _I, ctypes.POINTER(_P)]),
     "mk_solve_batch": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mk_solve_info), _P]),
     "mk_destroy_batch": (None, [_P]),
     "mk_solve_rhs": (ctypes.c_int, [_P, _P, ctypes.POINTER(mk_solve_opts), _P, ctypes.POINTER(mk_solve_info), _P]),
     "mk_march": (ctypes.c_int, [_P, _P, _P, _P]),
+    "mk_tune": (ctypes.c_int, [_P, _P, ctypes.POINTER(mk_solve_opts), _I, _I,
+                               ctypes.POINTER(mk_solve_opts), ctypes.POINTER(mk_tune_info), _P]),
     "mk_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mk_solve_opts), _P, _P, _P, _P,
                                   ctypes.POINTER(mk_solve_info), _P]),
     "mk_problem_shape": (ctypes.c_int, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),

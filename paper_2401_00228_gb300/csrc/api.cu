@@ -320,6 +320,13 @@ void mk_destroy(mk_problem *p) {
     delete p;
 }
 
+mk_status mk_trim(mk_problem *p) {
+    if (!p) return MK_ERR_INVALID;
+    CK(cudaDeviceSynchronize());
+    p->P.H.reset();
+    return MK_OK;
+}
+
 // pack a dense (nt+1) x n array into the padded fine-level layout
 static void pack_fine(const Problem &P, const double *dense, double *padded, cudaStream_t s) {
     launch_pack<double, double>(P.g, dense, padded, s);

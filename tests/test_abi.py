@@ -55,8 +55,8 @@ def test_struct_layouts_match_header():
 #include <stdio.h>
 #include "mk.h"
 int main(void) {
-  printf("%zu %zu %zu %zu\n", sizeof(mk_stencil), sizeof(mk_solve_opts), sizeof(mk_solve_info),
-         sizeof(mk_level_desc));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(mk_stencil), sizeof(mk_solve_opts), sizeof(mk_solve_info),
+         sizeof(mk_level_desc), sizeof(mk_tune_info));
   return 0;
 }
 '''
@@ -67,7 +67,8 @@ int main(void) {
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         sizes = list(map(int, subprocess.check_output([exe]).split()))
     assert sizes == [ctypes.sizeof(_lib.mk_stencil), ctypes.sizeof(_lib.mk_solve_opts),
-                     ctypes.sizeof(_lib.mk_solve_info), ctypes.sizeof(_lib.mk_level_desc)]
+                     ctypes.sizeof(_lib.mk_solve_info), ctypes.sizeof(_lib.mk_level_desc),
+                     ctypes.sizeof(_lib.mk_tune_info)]
 
 
 def test_struct_field_offsets_match_header():
@@ -76,7 +77,8 @@ def test_struct_field_offsets_match_header():
     from paper_2401_00228_gb300 import _lib
     import subprocess
     import tempfile
-    structs = [_lib.mk_stencil, _lib.mk_solve_opts, _lib.mk_solve_info, _lib.mk_level_desc]
+    structs = [_lib.mk_stencil, _lib.mk_solve_opts, _lib.mk_solve_info, _lib.mk_level_desc,
+               _lib.mk_tune_info]
     lines = []
     for st in structs:
         for name, _ in st._fields_:

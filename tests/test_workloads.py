@@ -99,3 +99,22 @@ def test_batched_workload_ranges():
     # log-uniform diffusion coefficients: both decades are populated
     lt = np.log10([p.tau for p in probs])
     assert (lt < 0).any() and (lt > 0).any()
+
+
+def test_batched_courant_numbers():
+    """The end time of every batch member comes from a Courant number C = 2 tau dt / h^2 in the
+    range of its theta (Crank-Nicolson up to 6.4, backward Euler up to 256), and the size,
+    tau and theta draws do not depend on that reading."""
+    probs = W.batched_problems()
+    for p in probs:
+        h = 1.0 / (p.nx + 1)
+        C = 2.0 * p.tau * p.dt / h ** 2
+        lo, hi = W.BATCH_C_RANGE[p.theta]
+        assert lo * (1 - 1e-12) <= C <= hi * (1 + 1e-12), (p.name, C)
+        assert abs(W.batch_end_time(C, p.nx, p.nt, p.tau) - p.T) <= 1e-12 * p.T
+    cn = [2.0 * p.tau * p.dt * (p.nx + 1) ** 2 for p in probs if p.theta == 0.5]
+    be = [2.0 * p.tau * p.dt * (p.nx + 1) ** 2 for p in probs if p.theta == 1.0]
+    assert max(cn) > 1.0 and max(be) > 20.0   # both ranges reach well into C > 1
+    small = W.batched_problems(count_1d=3, count_2d=1)
+    assert [(p.nx, p.nt, p.tau, p.theta) for p in small[:3]] == \
+        [(p.nx, p.nt, p.tau, p.theta) for p in probs[:3]]

@@ -201,18 +201,41 @@ def heat2d_alternate(levels: int = 7, seed: int = 5, precision: str = "mixed") -
                    smooth_modes_2d(rng, n, n), None, sched, tol=1e-6, precision=precision)
 
 
+# Courant-number ranges of the batch members by theta (the end time T is not given for the
+# batch; it is read from a Courant number C = 2 tau dt / h^2 drawn per member): Crank-Nicolson
+# members up to the largest theta = 1/2 single-problem workload (2D 255^2: C = 6.4), backward
+# Euler members up to the largest theta = 1 one (1D n = 1023: C = 256); the lower end is the
+# paper's smallest tested C (0.16).
+BATCH_C_RANGE = {0.5: (0.16, 6.4), 1.0: (0.16, 256.0)}
+
+
+def batch_end_time(C: float, n: int, nt: int, tau: float) -> float:
+    """T with 2 tau (T / n_t) / h^2 = C, h = 1/(n+1)."""
+    h = 1.0 / (n + 1)
+    return C * nt * h * h / (2.0 * tau)
+
+
 def batched_problems(seed: int = 4, count_1d: int = 48, count_2d: int = 16) -> List[Problem]:
     """Uneven problems: 1D n in {63..2047}, n_t in {256..8192}; 2D side in {63..255},
-    n_t in {128..1024}; tau log-uniform in [0.1, 10]; theta in {1/2, 1}."""
+    n_t in {128..1024}; tau log-uniform in [0.1, 10]; theta in {1/2, 1}; the end time from a
+    Courant number log-uniform in BATCH_C_RANGE[theta] (drawn from its own stream, seed + 1000,
+    so the other draws do not depend on it)."""
     rng = np.random.default_rng(seed)
+    rc = np.random.default_rng(seed + 1000)
     out: List[Problem] = []
+
+    def end_time(theta, n, nt, tau):
+        lo, hi = BATCH_C_RANGE[theta]
+        C = float(math.exp(rc.uniform(math.log(lo), math.log(hi))))
+        return batch_end_time(C, n, nt, tau)
+
     for i in range(count_1d):
         n = int(rng.integers(63, 2048))
         nt = int(rng.integers(256, 8193)) // 64 * 64
         nt = max(nt, 256)
         tau = float(math.exp(rng.uniform(math.log(0.1), math.log(10.0))))
         theta = float(rng.choice([0.5, 1.0]))
-        T = 0.1
+        T = end_time(theta, n, nt, tau)
         u0 = smooth_modes_1d(rng, n)
         out.append(Problem(f"batch1d_{i}", 1, n, 1, nt, T, tau, theta, u0, None,
                            Schedule(nu=(2, 2), space=(False, False), m_inner=(1,), n_cgs=16),
@@ -223,8 +246,9 @@ def batched_problems(seed: int = 4, count_1d: int = 48, count_2d: int = 16) -> L
         nt = max(nt, 128)
         tau = float(math.exp(rng.uniform(math.log(0.1), math.log(10.0))))
         theta = float(rng.choice([0.5, 1.0]))
+        T = end_time(theta, n, nt, tau)
         u0 = smooth_modes_2d(rng, n, n)
-        out.append(Problem(f"batch2d_{i}", 2, n, n, nt, 0.05, tau, theta, u0, None,
+        out.append(Problem(f"batch2d_{i}", 2, n, n, nt, T, tau, theta, u0, None,
                            Schedule(nu=(2, 2, 2), space=(True, True, True), m_inner=(2, 1), n_cgs=16),
                            tol=1e-10, precision="mixed"))
     return out
