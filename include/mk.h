@@ -111,7 +111,24 @@ typedef struct mk_solve_opts {
                             nu[0] >= 2 and n_t / nu[0] <= 65535; MK_ERR_INVALID otherwise.
                             mk_op_restrict, mk_op_interp_correct and mk_create_batch take
                             MK_TRANSFER_MK only. */
+    int32_t inner_kernel; /* how the inner levels 2..L run in each outer iteration:
+                            MK_INNER_AUTO (default): separate launches, or, when autotune is on
+                            and MK_INNER_COOP applies, whichever of the two the autotuner times
+                            faster on this hierarchy; MK_INNER_SEPARATE: one launch per step;
+                            MK_INNER_COOP: the whole inner recursion (restrictions, inner FGMRES
+                            iterations, coarsest solve, interpolations, Gram-Schmidt and least
+                            squares) in one cooperative launch with grid-wide barriers --
+                            requires dim = 1, precision 1, levels >= 3, nu = 2 and no space
+                            agglomeration below level 2, and the sine-transform coarsest solver
+                            (2(n+1) a power of two); MK_ERR_INVALID otherwise.  The
+                            cooperative kernel holds every SM for its duration: do not run
+                            other GPU work concurrently with such a solve (separate streams
+                            included); batches never use it. */
 } mk_solve_opts;
+
+#define MK_INNER_AUTO 0
+#define MK_INNER_SEPARATE 1
+#define MK_INNER_COOP 2
 
 #define MK_TRANSFER_MK 0
 #define MK_TRANSFER_MGRIT 1
@@ -368,8 +385,12 @@ mk_status mk_op_lsq(int32_t j, const double *H, double beta, double *y, double *
    mk_create_batch: problems = count distinct handles (not owned; they must outlive the
      batch and keep their source); opts = NULL or count option structs.  The batch holds
      its hierarchies, graph and streams on the current device until mk_destroy_batch.
+     The members' inner levels run as separate launches (inner_kernel = MK_INNER_AUTO is
+     taken as MK_INNER_SEPARATE): their branches run concurrently, and a cooperative kernel
+     sized to the whole GPU is not run beside other work.
      Errors: MK_ERR_INVALID (count < 1, a NULL or repeated handle, bad options, options
-     with transfer != MK_TRANSFER_MK), MK_ERR_NOMEM, MK_ERR_CUDA.
+     with transfer != MK_TRANSFER_MK or inner_kernel = MK_INNER_COOP), MK_ERR_NOMEM,
+     MK_ERR_CUDA.
    mk_solve_batch: u0[i] = initial state of problem i (nx or ny x nx), u_out[i] = its
      (nt+1) x n solution; each pointer host or device as elsewhere in this ABI.  infos =
      NULL or count structs (solve_ms and kernel_launches are those of the whole batch).

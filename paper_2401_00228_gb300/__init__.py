@@ -74,10 +74,12 @@ def make_opts(levels: int = 3, nu: Sequence[int] = (), space: Sequence[bool] = (
               m_inner: Sequence[int] = (), n_cgs: int = 16, tol: float = 1e-12, restart: int = 40,
               max_iters: int = 2000, precision: str = "fp64", mu: str | float = "lambda_max",
               use_graph: bool = True, orth: int = 1, autotune: bool = False,
-              transfer: str = "mk") -> mk_solve_opts:
+              transfer: str = "mk", inner: str = "auto") -> mk_solve_opts:
     """Options struct from Python values (unset per-level entries keep the defaults).
     transfer: "mk" (Sec. 3.2 block transfers, Galerkin levels) or "mgrit" (the comparison
-    two-level method of Eqs. (mgritY), (mgritZ) with the coarse matrix of Eq. (coarsemat))."""
+    two-level method of Eqs. (mgritY), (mgritZ) with the coarse matrix of Eq. (coarsemat)).
+    inner: "auto", "separate" (one launch per step of the inner levels) or "coop" (the inner
+    recursion in one cooperative kernel)."""
     o = mk_default_opts()
     o.levels = levels
     for i, v in enumerate(nu):
@@ -101,6 +103,8 @@ def make_opts(levels: int = 3, nu: Sequence[int] = (), space: Sequence[bool] = (
     o.orth = int(orth)
     o.autotune = 1 if autotune else 0
     o.transfer = {"mk": _lib.MK_TRANSFER_MK, "mgrit": _lib.MK_TRANSFER_MGRIT}[transfer]
+    o.inner_kernel = {"auto": _lib.MK_INNER_AUTO, "separate": _lib.MK_INNER_SEPARATE,
+                      "coop": _lib.MK_INNER_COOP}[inner]
     return o
 
 

@@ -29,10 +29,12 @@ class mk_solve_opts(ctypes.Structure):
                 ("space", ctypes.c_int32 * MK_MAX_LEVELS), ("m_inner", ctypes.c_int32 * MK_MAX_LEVELS),
                 ("n_cgs", ctypes.c_int32), ("mu_mode", ctypes.c_int32), ("mu_value", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("orth", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("transfer", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("transfer", ctypes.c_int32),
+                ("inner_kernel", ctypes.c_int32)]
 
 MK_TRANSFER_MK = 0      # Y, Z of Eq. (blockYZ) with Galerkin coarse levels
 MK_TRANSFER_MGRIT = 1   # Eqs. (mgritY), (mgritZ) with the coarse matrix of Eq. (coarsemat)
+MK_INNER_AUTO, MK_INNER_SEPARATE, MK_INNER_COOP = 0, 1, 2
 
 
 class mk_solve_info(ctypes.Structure):

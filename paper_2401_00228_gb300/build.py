@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libmk.so")
-SOURCES = ["stencil.cu", "krylov.cu", "dfkernels.cu", "slab.cu", "slab_dst.cu", "march2d.cu", "solver.cu", "api.cu", "noalloc.cu", "transfer1d.cu", "mgrit.cu", "setup.cpp", "tune.cpp",
+SOURCES = ["stencil.cu", "krylov.cu", "dfkernels.cu", "slab.cu", "slab_dst.cu", "march2d.cu", "solver.cu", "api.cu", "noalloc.cu", "transfer1d.cu", "mgrit.cu", "inner_coop.cu", "setup.cpp", "tune.cpp",
            "profile.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

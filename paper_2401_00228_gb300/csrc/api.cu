@@ -92,6 +92,7 @@ static mk_status ensure_device() {
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CK(slab_set_attributes());
     CK(dst_set_attributes());
+    CK(coop_set_attributes());
     CK(march2d_set_attributes());
     g_num_sms = sms > 0 ? sms : 1;
     return MK_OK;
@@ -253,7 +254,7 @@ mk_status mk_profile_read(int32_t cls, int32_t level, double *ms, double *bytes,
 
 const char *mk_profile_class_name(int32_t cls) {
     static const char *names[] = {"restrict", "interp_correct", "multidot", "update", "slab",
-                                  "residual", "combine", "march", "other"};
+                                  "residual", "combine", "march", "other", "inner_coop"};
     if (cls < 0 || cls >= PROF_NCLASS) return "";
     return names[cls];
 }
@@ -979,6 +980,10 @@ mk_status mk_create_batch(mk_problem *const *problems, int32_t count, const mk_s
         Problem &P = problems[i]->P;
         CKS(validate_opts(P, o));
         if (o.transfer != MK_TRANSFER_MK) return MK_ERR_INVALID;   // batches: block transfers
+        // members run concurrently on graph branches: a cooperative kernel sized to the whole
+        // GPU must not overlap other work, so the inner levels take separate launches here
+        if (o.inner_kernel == MK_INNER_COOP) return MK_ERR_INVALID;
+        o.inner_kernel = MK_INNER_SEPARATE;
         std::unique_ptr<Hierarchy> H;
         CKS(build_hierarchy_new(P, o, H));
         if (autotune) CKS(autotune_hierarchy(*H, s0));

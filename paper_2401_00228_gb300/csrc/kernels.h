@@ -150,6 +150,44 @@ void launch_slab_1d_dst(const Geom &g, const float *tab, const float2 *tw, int N
                         float *rh, int ldd, const float *r, float *x, const int *done,
                         cudaStream_t s);
 
+// ---- inner levels of the 1D mixed cycle in one cooperative kernel (inner_coop.cu) -------
+// Levels 2 .. L-1 (FP32, time coarsening by 2 without space agglomeration) and the
+// sine-transform coarsest level L.  Level l's fixed FGMRES iterations, the restriction to
+// l+1, the recursion, the interpolation with correction and matvec, the Gram-Schmidt
+// reductions and the small least-squares problems all run inside one launch, the phases
+// separated by grid-wide barriers of a cooperative launch.
+struct CoopLevel {
+    Geom g;
+    float a, b, mu;
+    const float *L;      // [lo | di | up] of the spatial operator, nx each
+    float *V, *X, *W;    // basis (m+1 vectors), preconditioned vectors (m), w
+    int64_t stride;
+    int m;               // fixed inner iterations
+    KState ks;
+};
+struct CoopCoarse {
+    Geom g;
+    const float *tab;    // [alpha (n) | beta (n)] of the per-mode recurrence
+    const float2 *tw;    // FFT twiddles
+    int N2, logN2, ldd, n_cgs;
+    float *rh, *R, *X;   // transformed rows (nt+1) x ldd, right-hand side, solution
+};
+struct CoopParams {
+    int nl;                          // intermediate levels: lv[0] is level 2, lv[nl-1] level L-1
+    CoopLevel lv[MK_MAX_LEVELS];
+    CoopCoarse c;
+    double *partials;                // [slot][block]
+    int max_blocks;
+};
+// Blocks of the cooperative launch (all co-resident) for an FFT length N2; 0 if the device
+// cannot run it.
+int coop_grid_size(int N2);
+cudaError_t coop_set_attributes();
+// The whole inner solve of level 2 (its right-hand side and beta already in lv[0].V and
+// lv[0].ks by the level-1 restriction): X_2 and y_2 on return.
+// Pdev: the parameters in device memory; N2: the coarsest level's FFT length.
+void launch_inner_coop(const CoopParams *Pdev, int N2, int grid, const int *done, cudaStream_t s);
+
 // Tile depth (time steps per thread) for the tiled 1D transfer launches that follow on this
 // host thread: restriction in {1, 2, 4}, interpolation in {2, 4}; 0 = built-in heuristic.
 void set_tile_hint(int kc_restrict, int kc_interp);

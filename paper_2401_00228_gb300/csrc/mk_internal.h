@@ -100,7 +100,7 @@ void set_cuda_error(cudaError_t e);
 
 enum ProfClass {
     PROF_RESTRICT = 0, PROF_INTERP, PROF_MULTIDOT, PROF_UPDATE, PROF_SLAB, PROF_RESIDUAL,
-    PROF_COMBINE, PROF_MARCH, PROF_OTHER, PROF_NCLASS
+    PROF_COMBINE, PROF_MARCH, PROF_OTHER, PROF_INNER, PROF_NCLASS
 };
 struct ProfPair {
     cudaEvent_t a, b;

@@ -48,30 +48,33 @@ struct ModeEig2D {
 
 constexpr int SCAN_CHUNKS = 16;
 
-template <typename T, int C, typename Coef>
-__global__ void __launch_bounds__(32 * SCAN_CHUNKS) k_mode_scan(int nm, T *__restrict__ rh, int64_t ld,
-                                                                Coef coef, int steps, int coupled,
-                                                                const int *__restrict__ done) {
-    if (done && *done) return;
-    __shared__ T ends[SCAN_CHUNKS][32];
+// One (group of 32 modes, slab) unit of the blocked scan by a block of 32 * CHUNKS threads.
+// CG: the rows were written earlier in the same kernel by other blocks (read through L2).
+template <typename T, int C, int CHUNKS, bool CG, typename Coef>
+__device__ __forceinline__ void mode_scan_unit(int nm, T *__restrict__ rh, int64_t ld, const Coef &coef,
+                                               int steps, int coupled, int group, int slab) {
+    __shared__ T ends[CHUNKS][32];
     const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
-    const int m = blockIdx.x * 32 + lane;
+    const int m = group * 32 + lane;
     const bool act = m < nm;
     T al = (T)0, be = (T)0;
     if (act) coef.get(m, al, be);
     T alc = al;   // alpha^C (C a power of two)
 #pragma unroll
     for (int c = 1; c < C; c *= 2) alc *= alc;
-    const int first = coupled ? 0 : 1 + blockIdx.y * steps;
+    const int first = coupled ? 0 : 1 + slab * steps;
     const int len = coupled ? steps + 1 : steps;
     T carry = (T)0;
-    for (int t0 = 0; t0 < len; t0 += SCAN_CHUNKS * C) {
+    for (int t0 = 0; t0 < len; t0 += CHUNKS * C) {
         const int c0 = t0 + q * C;
         const int cl = min(C, max(0, len - c0));
         T *p = rh + (int64_t)(first + c0) * ld + m;
         T v[C];
 #pragma unroll
-        for (int i = 0; i < C; ++i) v[i] = (act && i < cl) ? p[(int64_t)i * ld] : (T)0;
+        for (int i = 0; i < C; ++i) {
+            if (act && i < cl) v[i] = CG ? __ldcg(p + (int64_t)i * ld) : p[(int64_t)i * ld];
+            else v[i] = (T)0;
+        }
         T acc = (T)0;
 #pragma unroll
         for (int i = 0; i < C; ++i) {
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(32 * SCAN_CHUNKS) k_mode_scan(int nm, T *__res
         T cin = carry;
         for (int p2 = 0; p2 < q; ++p2) cin = alc * cin + ends[p2][lane];
         T cout = cin;
-        for (int p2 = q; p2 < SCAN_CHUNKS; ++p2) cout = alc * cout + ends[p2][lane];
+        for (int p2 = q; p2 < CHUNKS; ++p2) cout = alc * cout + ends[p2][lane];
         __syncthreads();
         T pw = al;
 #pragma unroll
@@ -96,6 +99,22 @@ __global__ void __launch_bounds__(32 * SCAN_CHUNKS) k_mode_scan(int nm, T *__res
     }
 }
 
+template <typename T, int C, typename Coef>
+__global__ void __launch_bounds__(32 * SCAN_CHUNKS) k_mode_scan(int nm, T *__restrict__ rh, int64_t ld,
+                                                                Coef coef, int steps, int coupled,
+                                                                const int *__restrict__ done) {
+    if (done && *done) return;
+    mode_scan_unit<T, C, SCAN_CHUNKS, false, Coef>(nm, rh, ld, coef, steps, coupled, blockIdx.x, blockIdx.y);
+}
+
+// Rows per warp for a slab of len rows and CHUNKS warps: the smallest power of two that
+// covers the slab in one tile, at most 32 (longer slabs take several tiles).
+__host__ __device__ inline int mode_scan_rows(int len, int chunks) {
+    int C = 2;
+    while (C < 32 && chunks * C < len) C *= 2;
+    return C;
+}
+
 // One launch over nm modes and n_cgs slabs (n_cgs = 0: the coupled march over rows 0..nt).
 template <typename T, typename Coef>
 inline void launch_mode_scan(int nm, T *rh, int64_t ld, Coef coef, int n_cgs, int nt, const int *done,
@@ -104,8 +123,7 @@ inline void launch_mode_scan(int nm, T *rh, int64_t ld, Coef coef, int n_cgs, in
     const int nslabs = coupled ? 1 : n_cgs;
     const int steps = coupled ? nt : nt / n_cgs;
     const int len = coupled ? steps + 1 : steps;
-    int C = 2;   // rows per warp: the smallest power of two covering the slab in one tile, <= 32
-    while (C < 32 && SCAN_CHUNKS * C < len) C *= 2;
+    const int C = mode_scan_rows(len, SCAN_CHUNKS);
     const dim3 grid((nm + 31) / 32, nslabs);
 #define MK_SCAN(CC)                                                                            \
     if (C == CC)                                                                               \

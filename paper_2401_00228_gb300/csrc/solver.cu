@@ -21,7 +21,7 @@ int64_t launches_total();
 bool OptsKey::operator==(const OptsKey &o) const {
     if (levels != o.levels || n_cgs != o.n_cgs || mu_mode != o.mu_mode ||
         precision != o.precision || restart != o.restart || mu_value != o.mu_value || orth != o.orth ||
-        autotune != o.autotune || transfer != o.transfer)
+        autotune != o.autotune || transfer != o.transfer || inner_kernel != o.inner_kernel)
         return false;
     for (int i = 0; i < MK_MAX_LEVELS; ++i)
         if (nu[i] != o.nu[i] || space[i] != o.space[i] || m_inner[i] != o.m_inner[i]) return false;
@@ -39,6 +39,7 @@ static OptsKey make_key(const mk_solve_opts &o) {
     k.orth = o.orth;
     k.autotune = o.autotune ? 1 : 0;
     k.transfer = o.transfer;
+    k.inner_kernel = o.inner_kernel;
     k.mu_value = o.mu_mode == 2 ? o.mu_value : 0.0;
     for (int i = 0; i < o.levels - 1 && i < MK_MAX_LEVELS; ++i) {
         k.nu[i] = o.nu[i];
@@ -57,6 +58,7 @@ mk_status validate_opts(const Problem &P, const mk_solve_opts &o) {
     if (o.orth < 0 || o.orth > 2) return MK_ERR_INVALID;
     if (o.n_cgs < 0) return MK_ERR_INVALID;
     if (o.transfer != MK_TRANSFER_MK && o.transfer != MK_TRANSFER_MGRIT) return MK_ERR_INVALID;
+    if (o.inner_kernel < MK_INNER_AUTO || o.inner_kernel > MK_INNER_COOP) return MK_ERR_INVALID;
     if (o.transfer == MK_TRANSFER_MGRIT &&
         (P.dim != 1 || o.levels != 2 || o.space[0] != 0 || o.nu[0] < 2 ||
          P.nt % o.nu[0] != 0 || P.nt / o.nu[0] > 65535))
@@ -211,6 +213,65 @@ static mk_status build_coarsest_tables(Level &C, int dim, bool fp64, int n_cgs) 
     return MK_OK;
 }
 
+// Whether the inner levels can run as one cooperative kernel (1D, mixed, time coarsening by
+// 2 without space below level 2, sine-transform coarsest solver, co-residency possible).
+static bool coop_eligible(const Hierarchy &H, const mk_solve_opts &o) {
+    const int L = (int)H.lv.size();
+    if (H.precision != 1 || o.transfer != MK_TRANSFER_MK || L < 3) return false;
+    if (H.lv[0]->g.dim != 1) return false;
+    for (int l = 1; l + 1 < L; ++l)
+        if (H.lv[l]->nu != 2 || H.lv[l]->space) return false;
+    const Level &C = *H.lv.back();
+    return C.dstN2 > 0 && coop_grid_size(C.dstN2) > 0;
+}
+
+// Parameters of the cooperative kernel for a grid of bpsm blocks per SM (device copy).
+mk_status coop_configure(Hierarchy &H, int bpsm) {
+    const Level &C = *H.lv.back();
+    const int cap = coop_grid_size(C.dstN2);
+    int grid = g_num_sms * bpsm;
+    if (grid > cap) grid = cap;
+    if (grid < 1) return MK_ERR_INVALID;
+    CoopParams cp;
+    std::memset(&cp, 0, sizeof(cp));
+    const int L = (int)H.lv.size();
+    cp.nl = L - 2;
+    for (int l = 1; l + 1 < L; ++l) {
+        const Level &Lv = *H.lv[l];
+        CoopLevel &c = cp.lv[l - 1];
+        c.g = Lv.g;
+        c.a = (float)Lv.w.a;
+        c.b = (float)Lv.w.b;
+        c.mu = (float)Lv.w.mu;
+        c.L = Lv.c32.as<float>();
+        c.V = Lv.V.as<float>();
+        c.X = Lv.X.as<float>();
+        c.W = Lv.W.as<float>();
+        c.stride = Lv.stride;
+        c.m = Lv.m;
+        c.ks = Lv.ks;
+    }
+    int logN2 = 0;
+    while ((1 << logN2) < C.dstN2) ++logN2;
+    cp.c.g = C.g;
+    cp.c.tab = C.dst.as<float>();
+    cp.c.tw = C.dsttw.as<float2>();
+    cp.c.N2 = C.dstN2;
+    cp.c.logN2 = logN2;
+    cp.c.ldd = C.dstld;
+    cp.c.n_cgs = H.key.n_cgs;
+    cp.c.rh = C.dstbuf.as<float>();
+    cp.c.R = C.R.as<float>();
+    cp.c.X = C.X.as<float>();
+    cp.partials = H.partials.as<double>();
+    cp.max_blocks = grid;
+    if (!H.coopP.p) MKCK(H.coopP.alloc(sizeof(CoopParams)));
+    MKCK(cudaMemcpy(H.coopP.p, &cp, sizeof(cp), cudaMemcpyHostToDevice));
+    H.coop_grid = grid;
+    H.coop_bpsm = bpsm;
+    return MK_OK;
+}
+
 mk_status build_hierarchy(Problem &P, const mk_solve_opts &o, Hierarchy *&out) {
     OptsKey key = make_key(o);
     if (P.H && P.H->key == key) {
@@ -349,6 +410,15 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
     MKCK(H->counters.alloc(sizeof(unsigned) * 16));
     H->rs.partials = H->partials.as<double>();
     H->rs.counter = H->counters.as<unsigned>();
+    H->coop_ok = coop_eligible(*H, o);
+    if (o.inner_kernel == MK_INNER_COOP && !H->coop_ok) return MK_ERR_INVALID;
+    // MK_INNER_COOP: the cooperative kernel; MK_INNER_AUTO: separate launches unless the
+    // autotuner measures the cooperative kernel faster (it is slower on the workloads measured)
+    if (H->coop_ok && o.inner_kernel == MK_INNER_COOP) {
+        mk_status st = coop_configure(*H, 3);
+        if (st != MK_OK) return st;
+        H->use_coop = true;
+    }
     out = std::move(H);
     return MK_OK;
 }
@@ -484,7 +554,12 @@ static void cycle_step_t(Hierarchy &H, int l, int j, const int *done, cudaStream
     } else {
         launch_restrict<Tv, Tc, Tc>(L.g, C.g, L.nu, L.space, L.w, op_of<Tc>(L), vj, sig,
                                     C.V.as<Tc>(), H.rs, 0, C.ks, done, s);
-        enqueue_inner_solve<Tc>(H, l + 1, done, s);                  // 4.3 (recursion)
+        if (l == 0 && H.use_coop) {                                  // 4.3, one cooperative kernel
+            set_ctx(C, l + 1);
+            launch_inner_coop(H.coopP.as<CoopParams>(), H.lv.back()->dstN2, H.coop_grid, done, s);
+        } else {
+            enqueue_inner_solve<Tc>(H, l + 1, done, s);              // 4.3 (recursion)
+        }
     }
     // 4.4-4.5 and step 5: x = v - Z vt, w = A x
     set_ctx(L, l);
@@ -838,6 +913,31 @@ mk_status autotune_hierarchy(Hierarchy &H, cudaStream_t s) {
     }
     // coarsest: every applicable variant of the decoupled slab solve
     Level &C = *H.lv.back();
+    // inner levels: separate launches against the cooperative kernel (1, 2 or 4 blocks per SM)
+    if (H.coop_ok && H.key.inner_kernel != MK_INNER_SEPARATE && !fp64) {
+        float best = 1e30f;
+        int best_b = 0;
+        if (H.key.inner_kernel == MK_INNER_AUTO) {
+            H.use_coop = false;
+            best = time_launch([&] { enqueue_cycle_step(H, 0, 0, nullptr, s); }, s, e0, e1);
+        }
+        for (int b : {2, 3}) {
+            if (coop_configure(H, b) != MK_OK) continue;
+            H.use_coop = true;
+            const float t = time_launch([&] { enqueue_cycle_step(H, 0, 0, nullptr, s); }, s, e0, e1);
+            if (t < best) {
+                best = t;
+                best_b = b;
+            }
+        }
+        if (best_b > 0) {
+            mk_status st = coop_configure(H, best_b);
+            if (st != MK_OK) return st;
+            H.use_coop = true;
+        } else {
+            H.use_coop = false;
+        }
+    }
     if (C.g.dim == 1) {
         float best = 1e30f;
         for (int kind : {1, 2, 3}) {

@@ -31,7 +31,7 @@ struct DevMem {
 };
 
 struct OptsKey {
-    int levels, n_cgs, mu_mode, precision, restart, orth, autotune, transfer;
+    int levels, n_cgs, mu_mode, precision, restart, orth, autotune, transfer, inner_kernel;
     int nu[MK_MAX_LEVELS], space[MK_MAX_LEVELS], m_inner[MK_MAX_LEVELS];
     double mu_value;
     bool operator==(const OptsKey &o) const;
@@ -81,6 +81,11 @@ struct Hierarchy {
     // each slab's first row, X = the marched points) and zt = Z xt on the fine geometry
     std::unique_ptr<Level> fprop;
     DevMem zt;
+    // the inner levels in one cooperative kernel (inner_coop.cu): parameters in device
+    // memory, grid size, and whether the cycle uses it
+    bool coop_ok = false, use_coop = false;
+    int coop_grid = 0, coop_bpsm = 2;
+    DevMem coopP;
     DevMem f, u;        // level-1 right-hand side and iterate (FP64)
     DevMem partials, counters;
     ReduceScratch rs{nullptr, nullptr, 0};

@@ -2,9 +2,10 @@
 hot path and end to end.  Inputs are seeded; each comparison is element by element.
 
 Tolerances: FP64 kernels 1e-12 relative to the largest output (rounding order differs);
-FP32 kernels 1e-5 (1e-3 for the FP32 slab solves, whose matrices have condition numbers up
-to ~1e4); whole solves 1e-10 (FP64) / 1e-8 (mixed) max relative error, the targets of the
-method's specification.
+FP32 kernels 1e-5; FP32 slab solves 4 s kappa 2^-24 (s steps per slab, kappa the condition
+number of the step matrix) against the oracle on FP32-rounded inputs, the FP32 cycle 2e-5
+(derivations in the tests); whole solves 1e-10 (FP64) / 1e-8 (mixed) max relative error, the
+targets of the method's specification.
 """
 import math
 
@@ -143,16 +144,39 @@ def test_interp_correct(case, precision, tol):
         assert _rel(w, lv.apply_A(xr)) <= tol, l
 
 
+U32 = 2.0 ** -24   # unit roundoff of FP32
+
+
+def _fp32(a):
+    """The FP32 rounding of an FP64 array (the values the FP32 kernels actually receive)."""
+    return a.astype(np.float32).astype(np.float64)
+
+
 # --------------------------------------------------------------------------- a6
-@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-3)])
-def test_coarsest_slabs(case, precision, tol):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coarsest_slabs(case, precision):
+    """Decoupled coarsest slabs against the oracle.  FP64: 1e-11.  FP32: the oracle solves the
+    FP32-rounded right-hand side, so only the kernel's own arithmetic is measured.  Every slab
+    step solves (I - a L) x_k = rhs_k with a backward-stable method (tridiagonal elimination or
+    an orthogonal eigenbasis), whose forward error is at most about kappa(I - a L) times the
+    roundoff of the step; a slab chains s such steps and the coupling term I + b L (norm at most
+    kappa as well) carries each step's error into the next.  Bound: 4 s kappa 2^-24, kappa the
+    2-norm condition number of the step matrix (dense, from the oracle's level)."""
     P, H, p = case
     o = _opts(P.schedule)
     lv = H.levels[-1]
     r = np.random.default_rng(24).standard_normal(lv.shape())
     x = np.empty_like(r)
     mk.mk_op_coarsest(p.handle, o, precision, r, x)
-    assert _rel(x, O.coarsest_solve(lv, r, H.n_cgs)) <= tol
+    if precision == 0:
+        assert _rel(x, O.coarsest_solve(lv, r, H.n_cgs)) <= 1e-11
+        return
+    M = np.eye(int(np.prod(lv.space_shape()))) - lv.a * lv.spatial_dense()
+    kappa = float(np.linalg.cond(M))
+    s = lv.nt // H.n_cgs
+    tol = 4.0 * s * kappa * U32
+    assert tol < 1e-3
+    assert _rel(x, O.coarsest_solve(lv, _fp32(r), H.n_cgs)) <= tol, (kappa, s)
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-4)])
@@ -223,9 +247,16 @@ def test_coarsest_2d_long_slabs(n_cgs, precision, tol):
 
 
 # --------------------------------------------------------------------------- a5
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-3)])
-def test_precondition_cycle(case, precision, tol):
-    """x = Q_l v: restriction, inner FGMRES recursion, decoupled slabs, interpolation."""
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_precondition_cycle(case, precision):
+    """x = Q_l v: restriction, inner FGMRES recursion, decoupled slabs, interpolation.
+    FP64: 1e-10.  Mixed (FP32 cycle): the oracle runs on the FP32-rounded v, so only the
+    cycle's own FP32 arithmetic is measured.  The cycle chains, per level, about 30 FP32 stages
+    (the restriction of the shifted residual, the slab solve or the m inner iterations with
+    their Gram-Schmidt updates, the interpolation with its matvec), each returning its output
+    with about two roundoffs of relative error; over up to 4 levels that is 240 x 2^-24 =
+    1.4e-5, so the bound is 2e-5 (an error of 1e-4 in one FP32 kernel, a coefficient or a
+    shift off by that much, fails it; measured at most 4e-7)."""
     P, H, p = case
     o = _opts(P.schedule, precision=precision)
     rng = np.random.default_rng(26)
@@ -235,7 +266,10 @@ def test_precondition_cycle(case, precision, tol):
         v /= np.linalg.norm(v)
         x = np.empty_like(v)
         mk.mk_op_precond(p.handle, o, l + 1, v, x)
-        assert _rel(x, O.precondition(H, l, v)) <= tol, l
+        if precision == "fp64":
+            assert _rel(x, O.precondition(H, l, v)) <= 1e-10, l
+        else:
+            assert _rel(x, O.precondition(H, l, _fp32(v))) <= 2e-5, l
 
 
 # --------------------------------------------------------------------------- a8, a9, a10
@@ -449,15 +483,23 @@ def test_full_size_1d_large_workload(precision, bound):
         assert O.max_rel_error(um, ref) <= 1e-11
 
 
-def test_full_size_1d_at_bench_tolerance():
-    """The bench's operating point: mixed precision, relative residual 1e-8, restart 40, one
-    Gram-Schmidt pass, autotuned tiles.  The metric asks for 1e-8 max relative error against
-    the oracle; the solution must meet it (measured 2.5e-9)."""
+@pytest.fixture(scope="module")
+def large_1d():
     P = W.heat1d_large(precision="mixed")
-    s = P.schedule
     ref = O.theta_march(1, P.nx, 1, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)
-    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=s.n_cgs,
-                     tol=1e-8, restart=40, precision="mixed", orth=0, autotune=True)
+    return P, ref
+
+
+@pytest.mark.parametrize("n_cgs,restart", [(16, 40), (2, 16), (0, 16), (0, 24)])
+def test_full_size_1d_at_bench_tolerance(large_1d, n_cgs, restart):
+    """The bench's operating points: mixed precision, relative residual 1e-8, one Gram-Schmidt
+    pass, autotuned tiles, 5 levels, and the slab counts and restart lengths the schedule
+    autotuner picks among on this workload (the exact coupled coarse solve included).  The
+    metric asks for 1e-8 max relative error against the oracle."""
+    P, ref = large_1d
+    s = P.schedule
+    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=n_cgs,
+                     tol=1e-8, restart=restart, precision="mixed", orth=0, autotune=True)
     with _prob(P) as p:
         u = np.empty_like(ref)
         info = mk.mk_solve(p.handle, P.u0, u, o)
@@ -465,19 +507,59 @@ def test_full_size_1d_at_bench_tolerance():
     assert O.max_rel_error(u, ref) <= 1e-8, info.iterations
 
 
-def test_full_size_2d_workload_sampled():
-    """255 x 255, n_t = 1024, TS coarsening, mixed precision.  The oracle marches the first
-    24 steps (sampled outputs) and checks the residual of the whole GPU solution."""
+@pytest.mark.parametrize("levels_flag", [False, True])
+def test_full_size_1d_tuned_schedule(large_1d, levels_flag):
+    """The schedule the autotuner picks for the bench (5 levels as configured, and any level
+    count: the two-level method with the exact coarse solve on this workload) meets the
+    metric's 1e-8 against the oracle."""
+    P, ref = large_1d
+    s = P.schedule
+    base = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=s.n_cgs,
+                        tol=1e-8, restart=40, precision="mixed", orth=0, autotune=True)
+    with _prob(P) as p:
+        o, ti = mk.mk_tune(p.handle, P.u0, base, levels=levels_flag, max_trials=40)
+        u = np.empty_like(ref)
+        info = mk.mk_solve(p.handle, P.u0, u, o)
+    assert (o.levels == 5) or levels_flag
+    assert info.rel_residual < 1e-8
+    assert O.max_rel_error(u, ref) <= 1e-8, (o.levels, o.n_cgs, o.restart, info.iterations)
+
+
+@pytest.fixture(scope="module")
+def large_2d():
+    """The 2D workload and the oracle's full march of it (about a minute on one core)."""
     P = W.heat2d_large()
+    ref = O.theta_march(2, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, P.u0, None)
+    return P, ref
+
+
+def test_full_size_2d_workload(large_2d):
+    """255 x 255, n_t = 1024, TS coarsening, mixed precision, tol 1e-12: the whole solution
+    against the oracle's march, and its residual under the oracle's operator."""
+    P, ref = large_2d
     with _prob(P) as p:
         u = np.empty((P.nt + 1, P.ny, P.nx))
         info = mk.mk_solve(p.handle, P.u0, u, _opts(P.schedule, precision="mixed", tol=1e-12))
-    ks = 24
-    ref = O.theta_march(2, P.nx, P.ny, ks, P.tau, P.theta, P.dt, P.u0, None)
-    assert O.max_rel_error(u[:ks + 1], ref) <= 1e-8, info.iterations
+    assert O.max_rel_error(u, ref) <= 1e-8, info.iterations
     lv = O.build_levels(2, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, (), (), "one")[0]
     f = O.assemble_rhs(P.u0, None, P.nt, P.theta, P.dt)
     assert np.linalg.norm(f - lv.apply_A(u)) / np.linalg.norm(f) <= 1e-11
+
+
+@pytest.mark.parametrize("n_cgs", [16, 0])
+def test_full_size_2d_at_bench_tolerance(large_2d, n_cgs):
+    """The 2D bench operating point: relative residual 1e-9 (the error runs about 4x the
+    residual on this workload), the schedule's 16 slabs or the exact coarse solve, autotuned
+    tiles: the whole solution within the metric's 1e-8 of the oracle's march."""
+    P, ref = large_2d
+    s = P.schedule
+    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=n_cgs,
+                     tol=1e-9, restart=40, precision="mixed", orth=0, autotune=True, max_iters=3000)
+    with _prob(P) as p:
+        u = np.empty((P.nt + 1, P.ny, P.nx))
+        info = mk.mk_solve(p.handle, P.u0, u, o)
+    assert info.rel_residual < 1e-9
+    assert O.max_rel_error(u, ref) <= 1e-8, info.iterations
 
 
 def test_one_call_solve_matches_problem_solve():
