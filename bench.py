@@ -167,7 +167,9 @@ def profiled_classes(mk, torch, dev, solve):
     solve()
     torch.cuda.synchronize(dev)
     rows = []
-    for cls in range(9):
+    for cls in range(16):
+        if not lib.mk_profile_class_name(cls):
+            break
         for lvl in range(0, 13):
             ms_, by_, n_ = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
             lib.mk_profile_read(cls, lvl, ctypes.byref(ms_), ctypes.byref(by_), ctypes.byref(n_))
@@ -584,8 +586,8 @@ def main():
     ap.add_argument("--tune-trials", type=int, default=40,
                     help="trial solves of the schedule autotuner on the headline workload")
     ap.add_argument("--tune-trials-fp64", type=int, default=8)
-    ap.add_argument("--tune-trials-2d", type=int, default=6)
-    ap.add_argument("--tune-trials-batch", type=int, default=8,
+    ap.add_argument("--tune-trials-2d", type=int, default=4)
+    ap.add_argument("--tune-trials-batch", type=int, default=5,
                     help="trial solves per member of the batch")
     ap.add_argument("--no-autotune", action="store_true",
                     help="built-in tile heuristics instead of the per-hierarchy autotuner")
