@@ -112,9 +112,8 @@ typedef struct mk_solve_opts {
                             mk_op_restrict, mk_op_interp_correct and mk_create_batch take
                             MK_TRANSFER_MK only. */
     int32_t inner_kernel; /* how the inner levels 2..L run in each outer iteration:
-                            MK_INNER_AUTO (default): separate launches, or, when autotune is on
-                            and MK_INNER_COOP applies, whichever of the two the autotuner times
-                            faster on this hierarchy; MK_INNER_SEPARATE: one launch per step;
+                            MK_INNER_AUTO (default) and MK_INNER_SEPARATE: one launch per step
+                            (measured faster than the cooperative kernel in whole solves);
                             MK_INNER_COOP: the whole inner recursion (restrictions, inner FGMRES
                             iterations, coarsest solve, interpolations, Gram-Schmidt and least
                             squares) in one cooperative launch with grid-wide barriers --

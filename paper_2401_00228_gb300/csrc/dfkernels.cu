@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(DF_THREADS) k_multidot_df(int64_t len, const f
         for (int w2 = 0; w2 < DF_WARPS; ++w2) s += acc[t * DF_WARPS + w2];
         rs.partials[(int64_t)t * rs.max_blocks + blockIdx.x] = s;
     }
-    if (last_block_ticket(rs.counter)) {
+    if (last_block_ticket(rs.counter, (int)threadIdx.x < nslots)) {
         const int lane2 = threadIdx.x & 31, warp2 = threadIdx.x >> 5;
         double *res = smem_md;
         for (int t = warp2; t < nslots; t += DF_WARPS) {
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(DF_THREADS) k_update_df(int64_t len, const flo
     }
     double bs = block_sum(df_to_double(acc));
     if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
-    if (last_block_ticket(rs.counter)) {
+    if (last_block_ticket(rs.counter, threadIdx.x == 0)) {
         double tot = sum_partials(rs.partials, gridDim.x);
         update_epilogue_block(tot, ks, j, mode, second);
         if (threadIdx.x == 0) rs.counter[0] = 0u;

@@ -189,7 +189,7 @@ cudaError_t coop_set_attributes();
 void launch_inner_coop(const CoopParams *Pdev, int N2, int grid, const int *done, cudaStream_t s);
 
 // Tile depth (time steps per thread) for the tiled 1D transfer launches that follow on this
-// host thread: restriction in {1, 2, 4}, interpolation in {2, 4}; 0 = built-in heuristic.
+// host thread: restriction in {1, 2, 4, 8}, interpolation in {2, 4}; 0 = built-in heuristic.
 void set_tile_hint(int kc_restrict, int kc_interp);
 
 // Time-tiled 1D variants for nu = 2 (transfer1d.cu).  Each returns false, launching

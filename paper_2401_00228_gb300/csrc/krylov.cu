@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_multidot(int64_t len, const TW *
         for (int w2 = 0; w2 < KR_WARPS; ++w2) s += acc[t * KR_WARPS + w2];
         rs.partials[(int64_t)t * rs.max_blocks + blockIdx.x] = s;
     }
-    if (last_block_ticket(rs.counter)) {
+    if (last_block_ticket(rs.counter, (int)threadIdx.x < nslots)) {
         double *res = smem;  // reuse
         finish_slots(rs.partials, rs.max_blocks, nslots, gridDim.x, res);
         multidot_epilogue(res, ks, j, nv, second);
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_update(int64_t len, const TW *__
     }
     double bs = block_sum((double)acc);
     if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
-    if (last_block_ticket(rs.counter)) {
+    if (last_block_ticket(rs.counter, threadIdx.x == 0)) {
         double tot = sum_partials(rs.partials, gridDim.x);
         update_epilogue_block(tot, ks, j, mode, second);
         if (threadIdx.x == 0) rs.counter[0] = 0u;
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_multidot_sb(int64_t len, const T
         for (int w2 = 0; w2 < KR_WARPS; ++w2) sum += acc[t * KR_WARPS + w2];
         rs.partials[(int64_t)t * rs.max_blocks + blockIdx.x] = sum;
     }
-    if (last_block_ticket(rs.counter)) {
+    if (last_block_ticket(rs.counter, (int)threadIdx.x < nslots)) {
         double *res = acc;  // reuse
         finish_slots(rs.partials, rs.max_blocks, nslots, gridDim.x, res);
         multidot_epilogue(res, ks, j, NV, second);
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_update_sb(int64_t len, const T *
     }
     double bs = block_sum((double)acc);
     if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
-    if (last_block_ticket(rs.counter)) {
+    if (last_block_ticket(rs.counter, threadIdx.x == 0)) {
         double tot = sum_partials(rs.partials, gridDim.x);
         update_epilogue_block(tot, ks, j, mode, second);
         if (threadIdx.x == 0) rs.counter[0] = 0u;

@@ -48,11 +48,13 @@ __device__ __forceinline__ int linear_block() {
 }
 __device__ __forceinline__ int num_blocks() { return gridDim.x * gridDim.y * gridDim.z; }
 
-// Ticket: returns true in every thread of the last block to finish.
-__device__ __forceinline__ bool last_block_ticket(unsigned *counter) {
+// Ticket: returns true in every thread of the last block to finish.  `wrote`: this thread
+// stored one of the block's partials; only those threads fence (making the partial visible
+// GPU-wide before the block's ticket is taken), the others' stores need no ordering here.
+__device__ __forceinline__ bool last_block_ticket(unsigned *counter, bool wrote) {
     __shared__ bool am_last;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    __threadfence();
+    if (wrote) __threadfence();
     __syncthreads();
     if (tid == 0) {
         unsigned t = atomicAdd(counter, 1u);
@@ -114,7 +116,7 @@ __device__ __forceinline__ void block_partial_and_finish(double v, const ReduceS
     double bs = block_sum(v);
     double *part = rs.partials + (int64_t)slot * rs.max_blocks;
     if (tid == 0) part[linear_block()] = bs;
-    if (last_block_ticket(rs.counter + slot)) {
+    if (last_block_ticket(rs.counter + slot, tid == 0)) {
         double tot = sum_partials(part, num_blocks());
         if (tid == 0) {
             run_epilogue(tot, ks, epi);

@@ -412,8 +412,7 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
     H->rs.counter = H->counters.as<unsigned>();
     H->coop_ok = coop_eligible(*H, o);
     if (o.inner_kernel == MK_INNER_COOP && !H->coop_ok) return MK_ERR_INVALID;
-    // MK_INNER_COOP: the cooperative kernel; MK_INNER_AUTO: separate launches unless the
-    // autotuner measures the cooperative kernel faster (it is slower on the workloads measured)
+    // MK_INNER_COOP: the cooperative kernel; MK_INNER_AUTO: separate launches (measured faster)
     if (H->coop_ok && o.inner_kernel == MK_INNER_COOP) {
         mk_status st = coop_configure(*H, 3);
         if (st != MK_OK) return st;
@@ -854,7 +853,7 @@ static void tune_level(Hierarchy &H, int l, cudaStream_t s, cudaEvent_t e0, cuda
     Tc *dst = C.coarsest ? C.R.as<Tc>() : C.V.as<Tc>();
     const KState ksc = C.coarsest ? KState{nullptr, nullptr, 0} : C.ks;
     float best = 1e30f;
-    for (int kc : {1, 2, 4}) {
+    for (int kc : {1, 2, 4, 8}) {
         set_tile_hint(kc, 0);
         const float t = time_launch([&] {
             launch_restrict<Tv, Tc, Tc>(L.g, C.g, L.nu, L.space, L.w, op_of<Tc>(L), v, nullptr, dst,
@@ -913,17 +912,15 @@ mk_status autotune_hierarchy(Hierarchy &H, cudaStream_t s) {
     }
     // coarsest: every applicable variant of the decoupled slab solve
     Level &C = *H.lv.back();
-    // inner levels: separate launches against the cooperative kernel (1, 2 or 4 blocks per SM)
-    if (H.coop_ok && H.key.inner_kernel != MK_INNER_SEPARATE && !fp64) {
+    // inner levels in the cooperative kernel (MK_INNER_COOP only): its grid, 2 or 3 blocks
+    // per SM.  (Timing one cycle step outside a graph would favour it over the separate
+    // launches, whose per-launch host cost a captured graph does not pay; whole solves measure
+    // it slower, so MK_INNER_AUTO keeps the separate launches.)
+    if (H.use_coop && !fp64) {
         float best = 1e30f;
         int best_b = 0;
-        if (H.key.inner_kernel == MK_INNER_AUTO) {
-            H.use_coop = false;
-            best = time_launch([&] { enqueue_cycle_step(H, 0, 0, nullptr, s); }, s, e0, e1);
-        }
         for (int b : {2, 3}) {
             if (coop_configure(H, b) != MK_OK) continue;
-            H.use_coop = true;
             const float t = time_launch([&] { enqueue_cycle_step(H, 0, 0, nullptr, s); }, s, e0, e1);
             if (t < best) {
                 best = t;
@@ -933,9 +930,6 @@ mk_status autotune_hierarchy(Hierarchy &H, cudaStream_t s) {
         if (best_b > 0) {
             mk_status st = coop_configure(H, best_b);
             if (st != MK_OK) return st;
-            H.use_coop = true;
-        } else {
-            H.use_coop = false;
         }
     }
     if (C.g.dim == 1) {

@@ -497,7 +497,7 @@ bool launch_restrict_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space
     const int xb = (gf.nx + TT * PT - 1) / (TT * PT);
     const int rows = gc.nt + 1;
     const int h = t_kc_restrict;
-    const int kc = (h == 1 || h == 2 || h == 4) ? h : tiled_kc(xb, rows, true);
+    const int kc = (h == 1 || h == 2 || h == 4 || h == 8) ? h : tiled_kc(xb, rows, true);
     const int yb = (rows + kc - 1) / kc;
     if (ks_c.d && (int64_t)xb * yb > rs.max_blocks) return false;
     const dim3 grid(xb, yb);
@@ -506,9 +506,9 @@ bool launch_restrict_1d_tiled(const Geom &gf, const Geom &gc, int nu, bool space
     k_restrict_1d_t<S, K, Tin, Tout, Tc><<<grid, TT, 0, s>>>(gf, gc, a, b, mu, L, v, sigma, \
                                                              vhat, rs, slot, ks_c, done)
     if (space) {
-        if (kc == 4) MK_RT(true, 4); else if (kc == 2) MK_RT(true, 2); else MK_RT(true, 1);
+        if (kc == 8) MK_RT(true, 8); else if (kc == 4) MK_RT(true, 4); else if (kc == 2) MK_RT(true, 2); else MK_RT(true, 1);
     } else {
-        if (kc == 4) MK_RT(false, 4); else if (kc == 2) MK_RT(false, 2); else MK_RT(false, 1);
+        if (kc == 8) MK_RT(false, 8); else if (kc == 4) MK_RT(false, 4); else if (kc == 2) MK_RT(false, 2); else MK_RT(false, 1);
     }
 #undef MK_RT
     return true;
