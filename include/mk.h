@@ -123,8 +123,18 @@ typedef struct mk_solve_opts {
                             cooperative kernel holds every SM for its duration: do not run
                             other GPU work concurrently with such a solve (separate streams
                             included); batches never use it. */
+    int32_t augment;     /* k >= 0 (default 0): FGMRES with recycled corrections, the flexible
+                            form of augmented restarting.  The correction u_c - u_{c-1} of every
+                            restart cycle c is kept (ring slot (c-1) mod k, in the cycle
+                            precision); once k cycles have completed, the last k of each
+                            cycle's `restart` directions are those corrections instead of
+                            preconditioned basis vectors (the Arnoldi relation and the least
+                            squares are unchanged: FGMRES accepts any direction).  Requires
+                            k < restart and k <= 8; not in batches.  Memory: k more level-1
+                            vectors. */
 } mk_solve_opts;
 
+#define MK_MAX_AUGMENT 8
 #define MK_INNER_AUTO 0
 #define MK_INNER_SEPARATE 1
 #define MK_INNER_COOP 2
@@ -388,8 +398,8 @@ mk_status mk_op_lsq(int32_t j, const double *H, double beta, double *y, double *
      taken as MK_INNER_SEPARATE): their branches run concurrently, and a cooperative kernel
      sized to the whole GPU is not run beside other work.
      Errors: MK_ERR_INVALID (count < 1, a NULL or repeated handle, bad options, options
-     with transfer != MK_TRANSFER_MK or inner_kernel = MK_INNER_COOP), MK_ERR_NOMEM,
-     MK_ERR_CUDA.
+     with transfer != MK_TRANSFER_MK, inner_kernel = MK_INNER_COOP or augment > 0),
+     MK_ERR_NOMEM, MK_ERR_CUDA.
    mk_solve_batch: u0[i] = initial state of problem i (nx or ny x nx), u_out[i] = its
      (nt+1) x n solution; each pointer host or device as elsewhere in this ABI.  infos =
      NULL or count structs (solve_ms and kernel_launches are those of the whole batch).

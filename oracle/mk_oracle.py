@@ -514,41 +514,71 @@ class SolveInfo:
     history: List[float]
 
 
+def fgmres_cycle(H: Hierarchy, f: np.ndarray, u: np.ndarray, restart: int, extra=(),
+                 tol: float = 0.0, fnorm: float = 1.0, budget: int = 1 << 30):
+    """One restart cycle of the outer FGMRES from u (Algorithm 2 with u^0 = u): Arnoldi on
+    r = f - A u with the directions x_j = Q_1 v_j (substeps 4.1-4.5), except that the last
+    len(extra) of the `restart` slots take the given directions instead (a flexible method
+    accepts any direction: the relation A X = V H stays exact).  Stops early when the
+    least-squares residual estimate drops below tol * fnorm, on a happy breakdown, or after
+    `budget` directions.  Returns (u + X y, X y, directions used)."""
+    lv = H.levels[0]
+    r = f - lv.apply_A(u)
+    beta = np.linalg.norm(r.ravel())
+    V = [r / beta]
+    X = []
+    Hm = np.zeros((restart + 1, restart))
+    J = 0
+    first_extra = restart - len(extra)
+    y = np.zeros(0)
+    for j in range(restart):
+        x = extra[j - first_extra] if j >= first_extra else precondition(H, 0, V[j])
+        X.append(x)
+        w = _arnoldi_step(lv, V, lv.apply_A(x), Hm, j)
+        J = j + 1
+        e1 = np.zeros(J + 1)
+        e1[0] = beta
+        y = np.linalg.lstsq(Hm[:J + 1, :J], e1, rcond=None)[0]
+        est = np.linalg.norm(e1 - Hm[:J + 1, :J] @ y)
+        if Hm[j + 1, j] == 0.0 or est / fnorm < tol or J >= budget:
+            break
+        V.append(w / Hm[j + 1, j])
+    d = np.zeros_like(u)
+    for i in range(J):
+        d = d + y[i] * X[i]
+    return u + d, d, J
+
+
 def fgmres(H: Hierarchy, f: np.ndarray, tol: float, restart: int = 50, maxit: int = 1000,
-           u0: Optional[np.ndarray] = None) -> Tuple[np.ndarray, SolveInfo]:
+           u0: Optional[np.ndarray] = None, augment: int = 0) -> Tuple[np.ndarray, SolveInfo]:
     """Outer FGMRES(restart) on level 1 preconditioned by Q_1.  Convergence when
-    ||f - A u|| / ||f|| < tol (Sec. 3.3.1), checked with the true residual."""
+    ||f - A u|| / ||f|| < tol (Sec. 3.3.1), checked with the true residual.
+
+    augment = k > 0: FGMRES with recycled corrections (the flexible form of augmented
+    restarting, a recycling restart for the stiff regime of Sec. 3.1): the correction
+    d_c = u_c - u_{c-1} of every completed cycle c is kept in ring slot (c - 1) mod k, and once
+    k cycles have completed, the last k of each cycle's `restart` directions are those k
+    corrections (slot order) instead of preconditioned basis vectors, so every cycle
+    minimises the residual over its preconditioned Krylov directions plus the recent
+    corrections."""
     lv = H.levels[0]
     u = np.zeros_like(f) if u0 is None else u0.copy()
     fnorm = np.linalg.norm(f.ravel())
     hist = []
     total = 0
     restarts = 0
+    ring = [None] * max(augment, 0)
     while True:
         r = f - lv.apply_A(u)
         beta = np.linalg.norm(r.ravel())
         hist.append(beta / fnorm)
         if beta / fnorm < tol or total >= maxit:
             return u, SolveInfo(total, restarts, beta / fnorm, hist)
-        V = [r / beta]
-        X = []
-        Hm = np.zeros((restart + 1, restart))
-        J = 0
-        for j in range(restart):
-            x = precondition(H, 0, V[j])
-            X.append(x)
-            w = _arnoldi_step(lv, V, lv.apply_A(x), Hm, j)
-            J = j + 1
-            total += 1
-            e1 = np.zeros(J + 1)
-            e1[0] = beta
-            y, res, *_ = np.linalg.lstsq(Hm[:J + 1, :J], e1, rcond=None)
-            est = np.linalg.norm(e1 - Hm[:J + 1, :J] @ y)
-            if Hm[j + 1, j] == 0.0 or est / fnorm < tol or total >= maxit:
-                break
-            V.append(w / Hm[j + 1, j])
-        for i in range(J):
-            u = u + y[i] * X[i]
+        extra = tuple(ring) if augment > 0 and restarts >= augment else ()
+        u, d, J = fgmres_cycle(H, f, u, restart, extra, tol, fnorm, maxit - total)
+        total += J
+        if augment > 0:
+            ring[restarts % augment] = d
         restarts += 1
 
 

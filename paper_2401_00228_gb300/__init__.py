@@ -74,12 +74,13 @@ def make_opts(levels: int = 3, nu: Sequence[int] = (), space: Sequence[bool] = (
               m_inner: Sequence[int] = (), n_cgs: int = 16, tol: float = 1e-12, restart: int = 40,
               max_iters: int = 2000, precision: str = "fp64", mu: str | float = "lambda_max",
               use_graph: bool = True, orth: int = 1, autotune: bool = False,
-              transfer: str = "mk", inner: str = "auto") -> mk_solve_opts:
+              transfer: str = "mk", inner: str = "auto", augment: int = 0) -> mk_solve_opts:
     """Options struct from Python values (unset per-level entries keep the defaults).
     transfer: "mk" (Sec. 3.2 block transfers, Galerkin levels) or "mgrit" (the comparison
     two-level method of Eqs. (mgritY), (mgritZ) with the coarse matrix of Eq. (coarsemat)).
     inner: "auto", "separate" (one launch per step of the inner levels) or "coop" (the inner
-    recursion in one cooperative kernel)."""
+    recursion in one cooperative kernel).  augment: k recycled corrections per restart cycle
+    (0: plain FGMRES(m))."""
     o = mk_default_opts()
     o.levels = levels
     for i, v in enumerate(nu):
@@ -105,6 +106,7 @@ def make_opts(levels: int = 3, nu: Sequence[int] = (), space: Sequence[bool] = (
     o.transfer = {"mk": _lib.MK_TRANSFER_MK, "mgrit": _lib.MK_TRANSFER_MGRIT}[transfer]
     o.inner_kernel = {"auto": _lib.MK_INNER_AUTO, "separate": _lib.MK_INNER_SEPARATE,
                       "coop": _lib.MK_INNER_COOP}[inner]
+    o.augment = int(augment)
     return o
 
 

@@ -30,7 +30,7 @@ class mk_solve_opts(ctypes.Structure):
                 ("n_cgs", ctypes.c_int32), ("mu_mode", ctypes.c_int32), ("mu_value", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("orth", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("transfer", ctypes.c_int32),
-                ("inner_kernel", ctypes.c_int32)]
+                ("inner_kernel", ctypes.c_int32), ("augment", ctypes.c_int32)]
 
 MK_TRANSFER_MK = 0      # Y, Z of Eq. (blockYZ) with Galerkin coarse levels
 MK_TRANSFER_MGRIT = 1   # Eqs. (mgritY), (mgritZ) with the coarse matrix of Eq. (coarsemat)

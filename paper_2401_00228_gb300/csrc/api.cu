@@ -982,7 +982,7 @@ mk_status mk_create_batch(mk_problem *const *problems, int32_t count, const mk_s
         if (o.transfer != MK_TRANSFER_MK) return MK_ERR_INVALID;   // batches: block transfers
         // members run concurrently on graph branches: a cooperative kernel sized to the whole
         // GPU must not overlap other work, so the inner levels take separate launches here
-        if (o.inner_kernel == MK_INNER_COOP) return MK_ERR_INVALID;
+        if (o.inner_kernel == MK_INNER_COOP || o.augment > 0) return MK_ERR_INVALID;
         o.inner_kernel = MK_INNER_SEPARATE;
         std::unique_ptr<Hierarchy> H;
         CKS(build_hierarchy_new(P, o, H));

@@ -596,31 +596,52 @@ static int df_grid(int64_t len, int64_t per_block) {
 
 // u += sum_{i < jf} y_i X_i with FP32 X: y_i split into double-float once per block, each
 // term y_i X_i formed and summed in double-float on the FP32 pipe, one FP64 add per element.
+// aug (recycled corrections, may be null): the cycle's correction sum y_i X_i is also stored,
+// rounded to FP32, in ring slot flags[5] mod augk.
 __global__ void __launch_bounds__(DF_THREADS) k_combine_df(int64_t len, double *__restrict__ u,
                                                            const float *__restrict__ X,
-                                                           int64_t xstride, KState ks) {
+                                                           int64_t xstride, KState ks,
+                                                           float *__restrict__ aug, int augk) {
     __shared__ float2 y[MK_MAX_RESTART];
     const int jf = ks.flags[1];
     if (jf <= 0 || ks.flags[3]) return;
     for (int i = threadIdx.x; i < jf; i += DF_THREADS) y[i] = df_pack(df_from_double(ks.y()[i]));
     __syncthreads();
+    float *d = aug ? aug + (int64_t)(ks.flags[5] % augk) * xstride : nullptr;
     for (int64_t e = (int64_t)blockIdx.x * DF_THREADS + threadIdx.x; e < len;
          e += (int64_t)gridDim.x * DF_THREADS) {
         df acc = {0.f, 0.f};
 #pragma unroll 4
         for (int i = 0; i < jf; ++i) acc = df_add(acc, df_mul_f(df_unpack(y[i]), X[(int64_t)i * xstride + e]));
-        u[e] += df_to_double(acc);
+        const double c = df_to_double(acc);
+        u[e] += c;
+        if (d) d[e] = (float)c;
     }
 }
 
+// w (double-float pairs) from the FP64 values stored in the same 8 bytes, in place.
+__global__ void k_f64_to_df(int64_t len, void *w) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = reinterpret_cast<const double *>(w)[e];
+        reinterpret_cast<float2 *>(w)[e] = df_pack(df_from_double(v));
+    }
+}
+
+void launch_f64_to_df(int64_t len, void *w, const int *done, cudaStream_t s) {
+    (void)done;
+    k_f64_to_df<<<df_grid(len, (int64_t)DF_THREADS * 8), DF_THREADS, 0, s>>>(len, w);
+    count_launch();
+}
+
 void launch_combine_df(int64_t len, double *u, const float *X, int64_t xstride, KState ks,
-                       cudaStream_t s) {
+                       cudaStream_t s, float *aug, int augk) {
     const double alg_n = prof_alg_n() > 0 ? prof_alg_n() : (double)len;
     // one element per thread: each element is a dependent chain of jf double-float terms, so
     // independent chains (threads), not a grid-stride loop, hide its latency
     const int64_t grid = (len + DF_THREADS - 1) / DF_THREADS;
     prof_begin(s);
-    k_combine_df<<<(unsigned)grid, DF_THREADS, 0, s>>>(len, u, X, xstride, ks);
+    k_combine_df<<<(unsigned)grid, DF_THREADS, 0, s>>>(len, u, X, xstride, ks, aug, augk);
     prof_end(s, PROF_COMBINE, (double)alg_n * (16.0 + (double)ks.m * sizeof(float)));
     count_launch();
 }

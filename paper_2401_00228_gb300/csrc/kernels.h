@@ -104,9 +104,11 @@ void launch_update(int64_t len, const TW *W, TV *V, int64_t vstride, int j, bool
                    const int *done, cudaStream_t s);
 
 // u += sum_{i < jf} y_i X_i (FP64 u), jf = flags[1] (outer) -- skip when nothing to add.
+// aug (may be null): the correction sum y_i X_i also goes to ring slot flags[5] mod augk
+// (slots xstride apart).
 template <typename TX>
 void launch_combine(int64_t len, double *u, const TX *X, int64_t xstride, KState ks,
-                    cudaStream_t s);
+                    cudaStream_t s, TX *aug = nullptr, int augk = 0);
 
 // Small solve on the device: least squares of an explicit (j+1) x j Hessenberg by Givens,
 // rotating H in place; gg: j+1 doubles of scratch.
@@ -220,7 +222,9 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
                       const float2 *uniform_ab = nullptr, bool uniform_square = false);
 // u += sum_{i < jf} y_i X_i for FP32 X in double-float arithmetic (mixed level 1)
 void launch_combine_df(int64_t len, double *u, const float *X, int64_t xstride, KState ks,
-                       cudaStream_t s);
+                       cudaStream_t s, float *aug = nullptr, int augk = 0);
+// In place: the FP64 values of w become double-float pairs (same 8 bytes per element).
+void launch_f64_to_df(int64_t len, void *w, const int *done, cudaStream_t s);
 void launch_multidot_df(int64_t len, const float2 *W, const float2 *V, int64_t vstride, int j,
                         const ReduceScratch &rs, KState ks, bool second_pass, const int *done,
                         cudaStream_t s);

@@ -304,20 +304,31 @@ static int sb_grid(int64_t len) {
 // ---------------------------------------------------------------------------------------
 // combine: u += sum_{i < jf} y_i X_i
 // ---------------------------------------------------------------------------------------
+// aug (recycled corrections, may be null): the cycle's correction sum y_i X_i is also stored in
+// ring slot flags[5] mod augk.
 template <typename TX>
 __global__ void __launch_bounds__(KR_THREADS) k_combine(int64_t len, double *__restrict__ u,
                                                         const TX *__restrict__ X,
-                                                        int64_t xstride, KState ks) {
+                                                        int64_t xstride, KState ks,
+                                                        TX *__restrict__ aug, int augk) {
     __shared__ double y[MK_MAX_RESTART];
     const int jf = ks.flags[1];
     if (jf <= 0 || ks.flags[3]) return;
     for (int i = threadIdx.x; i < jf; i += KR_THREADS) y[i] = ks.y()[i];
     __syncthreads();
+    TX *d = aug ? aug + (int64_t)(ks.flags[5] % augk) * xstride : nullptr;
     for (int64_t e = (int64_t)blockIdx.x * KR_THREADS + threadIdx.x; e < len;
          e += (int64_t)gridDim.x * KR_THREADS) {
-        double acc = u[e];
-        for (int i = 0; i < jf; ++i) acc += y[i] * (double)X[(int64_t)i * xstride + e];
-        u[e] = acc;
+        if (d) {
+            double c = 0.0;
+            for (int i = 0; i < jf; ++i) c += y[i] * (double)X[(int64_t)i * xstride + e];
+            u[e] += c;
+            d[e] = (TX)c;
+        } else {
+            double acc = u[e];
+            for (int i = 0; i < jf; ++i) acc += y[i] * (double)X[(int64_t)i * xstride + e];
+            u[e] = acc;
+        }
     }
 }
 
@@ -402,11 +413,11 @@ void launch_update(int64_t len, const TW *W, TV *V, int64_t vstride, int j, bool
 
 template <typename TX>
 void launch_combine(int64_t len, double *u, const TX *X, int64_t xstride, KState ks,
-                    cudaStream_t s) {
+                    cudaStream_t s, TX *aug, int augk) {
     const double alg_n = prof_alg_n() > 0 ? prof_alg_n() : (double)len;
     int grid = krylov_grid(len, (int64_t)KR_THREADS * 8);
     prof_begin(s);
-    k_combine<TX><<<grid, KR_THREADS, 0, s>>>(len, u, X, xstride, ks);
+    k_combine<TX><<<grid, KR_THREADS, 0, s>>>(len, u, X, xstride, ks, aug, augk);
     prof_end(s, PROF_COMBINE, (double)alg_n * (16.0 + (double)ks.m * sizeof(TX)));
     count_launch();
 }
@@ -430,8 +441,8 @@ template void launch_update<float, float>(int64_t, const float *, float *, int64
                                           const ReduceScratch &, KState, int, bool, const int *,
                                           cudaStream_t);
 template void launch_combine<double>(int64_t, double *, const double *, int64_t, KState,
-                                     cudaStream_t);
+                                     cudaStream_t, double *, int);
 template void launch_combine<float>(int64_t, double *, const float *, int64_t, KState,
-                                    cudaStream_t);
+                                    cudaStream_t, float *, int);
 
 }  // namespace mk

@@ -21,7 +21,8 @@ int64_t launches_total();
 bool OptsKey::operator==(const OptsKey &o) const {
     if (levels != o.levels || n_cgs != o.n_cgs || mu_mode != o.mu_mode ||
         precision != o.precision || restart != o.restart || mu_value != o.mu_value || orth != o.orth ||
-        autotune != o.autotune || transfer != o.transfer || inner_kernel != o.inner_kernel)
+        autotune != o.autotune || transfer != o.transfer || inner_kernel != o.inner_kernel ||
+        augment != o.augment)
         return false;
     for (int i = 0; i < MK_MAX_LEVELS; ++i)
         if (nu[i] != o.nu[i] || space[i] != o.space[i] || m_inner[i] != o.m_inner[i]) return false;
@@ -40,6 +41,7 @@ static OptsKey make_key(const mk_solve_opts &o) {
     k.autotune = o.autotune ? 1 : 0;
     k.transfer = o.transfer;
     k.inner_kernel = o.inner_kernel;
+    k.augment = o.augment;
     k.mu_value = o.mu_mode == 2 ? o.mu_value : 0.0;
     for (int i = 0; i < o.levels - 1 && i < MK_MAX_LEVELS; ++i) {
         k.nu[i] = o.nu[i];
@@ -59,6 +61,7 @@ mk_status validate_opts(const Problem &P, const mk_solve_opts &o) {
     if (o.n_cgs < 0) return MK_ERR_INVALID;
     if (o.transfer != MK_TRANSFER_MK && o.transfer != MK_TRANSFER_MGRIT) return MK_ERR_INVALID;
     if (o.inner_kernel < MK_INNER_AUTO || o.inner_kernel > MK_INNER_COOP) return MK_ERR_INVALID;
+    if (o.augment < 0 || o.augment > MK_MAX_AUGMENT || o.augment >= o.restart) return MK_ERR_INVALID;
     if (o.transfer == MK_TRANSFER_MGRIT &&
         (P.dim != 1 || o.levels != 2 || o.space[0] != 0 || o.nu[0] < 2 ||
          P.nt % o.nu[0] != 0 || P.nt / o.nu[0] > 65535))
@@ -364,6 +367,10 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
             lv->m = o.restart;
             MKCK(lv->V.alloc(sizeof(double) * len * (lv->m + 1)));
             MKCK(lv->X.alloc(cs * len * lv->m));
+            if (o.augment > 0) {
+                MKCK(H->aug.alloc(cs * len * o.augment));
+                H->aug_k = o.augment;
+            }
             MKCK(lv->W.alloc(sizeof(double) * len));
             st = alloc_kstate(*lv, lv->m);
             if (st != MK_OK) return st;
@@ -601,18 +608,36 @@ void enqueue_cycle_step(Hierarchy &H, int l, int j, const int *done, cudaStream_
 
 // One restart cycle of the outer FGMRES (Algorithm 2), ending with the true residual of
 // the updated iterate, which also starts the next cycle.
-static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s) {
+// With aug (recycled corrections in use): the last H.aug_k slots take x_j = the stored
+// correction of an earlier cycle and w = A x_j (FP64, then double-float pairs in the mixed
+// solve) instead of x_j = Q_1 v_j; the Gram-Schmidt and least squares are the same.
+static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s, bool aug = false) {
     Level &L = *H.lv[0];
     const int *done = L.ks.flags;
     const int64_t len = L.g.len;
     const bool fp64 = H.precision == 0;
+    const size_t xs = fp64 ? sizeof(double) : sizeof(float);
     double *V = L.V.as<double>();
     double *W = L.W.as<double>();
     float2 *Vd = L.V.as<float2>();
     float2 *Wd = L.W.as<float2>();
     for (int j = 0; j < L.m; ++j) {
         t_outer_j = j;
-        enqueue_cycle_step(H, 0, j, done, s);
+        const int q = j - (L.m - H.aug_k);
+        if (aug && q >= 0) {
+            set_ctx(L, 0);
+            char *xj = L.X.as<char>() + (size_t)j * L.stride * xs;
+            const char *dq = H.aug.as<char>() + (size_t)q * L.stride * xs;
+            cudaMemcpyAsync(xj, dq, (size_t)len * xs, cudaMemcpyDeviceToDevice, s);
+            if (fp64) {
+                launch_apply<double, double, double>(L.g, L.w, L.op64, reinterpret_cast<double *>(xj), W, s);
+            } else {
+                launch_apply<float, double, double>(L.g, L.w, L.op64, reinterpret_cast<float *>(xj), W, s);
+                launch_f64_to_df(len, W, done, s);
+            }
+        } else {
+            enqueue_cycle_step(H, 0, j, done, s);
+        }
         set_ctx(L, 0);
         const int orth = H.key.orth;
         const int mode = orth == 0 ? UPD_GIVENS : (orth == 2 ? UPD_GIVENS | UPD_REORTH_ALWAYS : UPD_OUTER);
@@ -638,11 +663,13 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s) {
     t_outer_j = -1;
     set_ctx(L, 0);
     if (fp64) {
-        launch_combine<double>(len, H.u.as<double>(), L.X.as<double>(), L.stride, L.ks, s);
+        launch_combine<double>(len, H.u.as<double>(), L.X.as<double>(), L.stride, L.ks, s,
+                               H.aug_k ? H.aug.as<double>() : nullptr, H.aug_k);
         launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), V, H.rs, 0, L.ks,
                         EPI_OUTER_START, s);
     } else {
-        launch_combine_df(len, H.u.as<double>(), L.X.as<float>(), L.stride, L.ks, s);
+        launch_combine_df(len, H.u.as<double>(), L.X.as<float>(), L.stride, L.ks, s,
+                          H.aug_k ? H.aug.as<float>() : nullptr, H.aug_k);
         launch_residual_df(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), Vd, H.rs, 0, L.ks,
                            EPI_OUTER_START, s);
     }
@@ -652,24 +679,31 @@ void release_pairs(std::vector<ProfPair> &pairs);
 
 Hierarchy::~Hierarchy() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (graph_aug) cudaGraphExecDestroy(graph_aug);
     release_pairs(graph_pairs);
+    release_pairs(graph_aug_pairs);
 }
 
-static mk_status capture_cycle(Problem &P, Hierarchy &H) {
-    if (H.graph) {
-        cudaGraphExecDestroy(H.graph);
-        H.graph = nullptr;
+// One restart cycle captured into a graph: the plain cycle, or (aug) the cycle whose last
+// aug_k slots use the recycled corrections.
+static mk_status capture_cycle(Problem &P, Hierarchy &H, bool aug = false) {
+    cudaGraphExec_t &exec = aug ? H.graph_aug : H.graph;
+    std::vector<ProfPair> &pairs = aug ? H.graph_aug_pairs : H.graph_pairs;
+    int64_t &kernels = aug ? H.graph_aug_kernels : H.graph_kernels;
+    if (exec) {
+        cudaGraphExecDestroy(exec);
+        exec = nullptr;
     }
-    release_pairs(H.graph_pairs);
-    H.graph_kernels = 0;
-    H.graph_profiled = prof_enabled();
+    release_pairs(pairs);
+    kernels = 0;
+    (aug ? H.graph_aug_profiled : H.graph_profiled) = prof_enabled();
     cudaStream_t cs;
     MKCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph;
     MKCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    set_capture_counter(&H.graph_kernels);
-    prof_set_sink(&H.graph_pairs);
-    enqueue_outer_cycle(P, H, cs);
+    set_capture_counter(&kernels);
+    prof_set_sink(&pairs);
+    enqueue_outer_cycle(P, H, cs, aug);
     prof_set_sink(nullptr);
     set_capture_counter(nullptr);
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
@@ -678,12 +712,12 @@ static mk_status capture_cycle(Problem &P, Hierarchy &H) {
         set_cuda_error(ce);
         return MK_ERR_CUDA;
     }
-    ce = cudaGraphInstantiate(&H.graph, graph, 0);
+    ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     cudaStreamDestroy(cs);
     if (ce != cudaSuccess) {
         set_cuda_error(ce);
-        H.graph = nullptr;
+        exec = nullptr;
         return MK_ERR_CUDA;
     }
     return MK_OK;
@@ -737,12 +771,23 @@ mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const doub
     int iters_before = 0;
     std::vector<ProfPair> cycle_pairs;
     for (;;) {
+        // recycled corrections: the cycle index selects the ring slot its correction goes to;
+        // once aug_k cycles have completed, the cycle uses them
+        const bool aug = H.aug_k > 0 && cycles >= H.aug_k;
+        if (H.aug_k > 0) {
+            H.cycle_host = cycles;
+            MKCK(cudaMemcpyAsync(L.ks.flags + 5, &H.cycle_host, sizeof(int), cudaMemcpyHostToDevice, s));
+        }
+        if (o.use_graph && aug && (!H.graph_aug || H.graph_aug_profiled != prof_enabled())) {
+            mk_status st = capture_cycle(P, H, true);
+            if (st != MK_OK) return st;
+        }
         if (o.use_graph) {
-            MKCK(cudaGraphLaunch(H.graph, s));
-            add_launches(H.graph_kernels);
+            MKCK(cudaGraphLaunch(aug ? H.graph_aug : H.graph, s));
+            add_launches(aug ? H.graph_aug_kernels : H.graph_kernels);
         } else {
             prof_set_sink(&cycle_pairs);
-            enqueue_outer_cycle(P, H, s);
+            enqueue_outer_cycle(P, H, s, aug);
             prof_set_sink(nullptr);
         }
         ++cycles;
@@ -753,7 +798,7 @@ mk_status run_solve(Problem &P, Hierarchy &H, const mk_solve_opts &o, const doub
         const int worked = hflags[4] - iters_before;
         iters_before = hflags[4];
         if (prof_enabled()) {
-            if (o.use_graph) prof_accumulate(H.graph_pairs, worked);
+            if (o.use_graph) prof_accumulate(aug ? H.graph_aug_pairs : H.graph_pairs, worked);
             else {
                 prof_accumulate(cycle_pairs, worked);
                 release_pairs(cycle_pairs);

@@ -31,7 +31,7 @@ struct DevMem {
 };
 
 struct OptsKey {
-    int levels, n_cgs, mu_mode, precision, restart, orth, autotune, transfer, inner_kernel;
+    int levels, n_cgs, mu_mode, precision, restart, orth, autotune, transfer, inner_kernel, augment;
     int nu[MK_MAX_LEVELS], space[MK_MAX_LEVELS], m_inner[MK_MAX_LEVELS];
     double mu_value;
     bool operator==(const OptsKey &o) const;
@@ -93,6 +93,15 @@ struct Hierarchy {
     bool graph_profiled = false;        // captured with kernel-class timing events
     int64_t graph_kernels = 0;          // kernels in one replay of the graph
     std::vector<ProfPair> graph_pairs;  // timing events inside the graph
+    // recycled corrections (mk_solve_opts.augment = aug_k > 0): ring of aug_k level-1 vectors
+    // in the X precision, and the restart cycle whose last aug_k slots use them
+    int aug_k = 0;
+    DevMem aug;
+    cudaGraphExec_t graph_aug = nullptr;
+    bool graph_aug_profiled = false;
+    int64_t graph_aug_kernels = 0;
+    std::vector<ProfPair> graph_aug_pairs;
+    int cycle_host = 0;                 // source of the cycle index's host-to-device copy
     double tol_host = 0.0;              // source of the tolerance's host-to-device copy
     ~Hierarchy();
 };

@@ -518,3 +518,60 @@ def test_adjoint_gradients_vs_central_differences(dim, theta):
     assert abs(fd - np.sum(gg * dg)) <= 1e-6 * max(1.0, abs(fd))
     fd = (fwd(u0, g, tau + eps) - fwd(u0, g, tau - eps)) / (2 * eps)
     assert abs(fd - gtau) <= 1e-6 * max(1.0, abs(fd))
+
+
+# ---------------------------------------------------------------------------------------
+# FGMRES with recycled corrections (augment > 0): the restart cycle with given directions.
+# ---------------------------------------------------------------------------------------
+def _tiny_hierarchy():
+    H = O.make_hierarchy(1, 15, 1, 16, 1.0, 1.0, 0.02, (2, 2), (False, False), (1,), 2)
+    rng = np.random.default_rng(91)
+    f = rng.standard_normal(H.levels[0].shape())
+    return H, f, rng
+
+
+def test_cycle_with_given_directions_is_least_squares():
+    """A cycle whose every slot is a given direction returns the minimiser of ||f - A u|| over
+    u0 + span(directions): brute force by dense least squares on A applied to them."""
+    H, f, rng = _tiny_hierarchy()
+    lv = H.levels[0]
+    u0 = rng.standard_normal(f.shape)
+    E = [rng.standard_normal(f.shape) for _ in range(3)]
+    u1, d, J = O.fgmres_cycle(H, f, u0, 3, tuple(E))
+    assert J == 3
+    AE = np.stack([lv.apply_A(e).ravel() for e in E], axis=1)
+    r0 = (f - lv.apply_A(u0)).ravel()
+    c = np.linalg.lstsq(AE, r0, rcond=None)[0]
+    ref = u0 + sum(ci * ei for ci, ei in zip(c, E))
+    assert np.max(np.abs(u1 - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.allclose(d, u1 - u0, rtol=0, atol=1e-14 * np.max(np.abs(u1)))
+
+
+def test_cycle_with_recycled_slots_never_does_worse():
+    """m - k preconditioned directions plus k recycled ones span a superset of the plain
+    (m - k)-step cycle from the same iterate (the same Arnoldi vectors come first), so the
+    residual can only be smaller."""
+    H, f, rng = _tiny_hierarchy()
+    lv = H.levels[0]
+    u0 = rng.standard_normal(f.shape) * 0.1
+    extra = tuple(rng.standard_normal(f.shape) for _ in range(2))
+    ua, _, _ = O.fgmres_cycle(H, f, u0, 5, extra)
+    up, _, _ = O.fgmres_cycle(H, f, u0, 3, ())
+    ra = np.linalg.norm(f - lv.apply_A(ua))
+    rp = np.linalg.norm(f - lv.apply_A(up))
+    assert ra <= rp * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("augment", [0, 1, 2])
+def test_fgmres_with_recycled_corrections_solves_the_system(augment):
+    """Outer FGMRES(6) with 0-2 recycled corrections reaches the unique solution of
+    Eq. (finesys) (the sequential march); augment = 0 is plain FGMRES."""
+    P = W.heat1d_small()
+    s = P.schedule
+    H = O.make_hierarchy(1, P.nx, 1, P.nt, P.tau, P.theta, P.dt, s.nu, s.space, s.m_inner, s.n_cgs)
+    f = O.assemble_rhs(P.u0, P.g, P.nt, P.theta, P.dt)
+    u, info = O.fgmres(H, f, 1e-11, restart=6, augment=augment, maxit=400)
+    ref = O.theta_march(1, P.nx, 1, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)
+    assert info.rel_residual < 1e-11
+    assert O.max_rel_error(u, ref) <= 1e-9
+    assert info.restarts > augment   # the recycled slots were in use
