@@ -136,7 +136,7 @@ __device__ __noinline__ double restrict_phase(const CoopLevel &F, const Geom &gc
     const int nf = F.g.nx, ng = (nf + 3) / 4;
     const int64_t items = (int64_t)(gc.nt + 1) * ng;
     const float a = F.a, b = F.b, mu = F.mu;
-    double acc = 0.0;
+    float acc = 0.f;   // per-thread sum in FP32 (FP64 only across threads)
     for (int64_t t = (int64_t)blockIdx.x * CT + threadIdx.x; t < items; t += (int64_t)gridDim.x * CT) {
         const int K = (int)(t / ng);
         const int i0 = 4 * (int)(t - (int64_t)K * ng);
@@ -169,11 +169,11 @@ __device__ __noinline__ double restrict_phase(const CoopLevel &F, const Geom &gc
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             if (i0 + p >= nf) o[p] = 0.f;
-            acc += (double)o[p] * (double)o[p];
+            acc += o[p] * o[p];
         }
         st4f(out + gc.guard + (int64_t)K * gc.plane + i0, o);
     }
-    return acc;
+    return (double)acc;
 }
 
 // ---- 4.4-4.5 and step 5: x = sigma v - Z vt, w = A x --------------------------------------

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu_rt, T
     const int nu = NU > 0 ? NU : nu_rt;
     int I, J, chunk;
     point_index<DIM>(I, J, chunk);
-    double acc2 = 0.0;
+    Tc acc2 = (Tc)0;   // per-thread sum in the arithmetic type (FP64 only across threads)
     const bool active = I < gc.nx && J < gc.ny;
     if (active) {
         const Tc scale = sigma ? (Tc)(*sigma) : (Tc)1;
@@ -309,10 +309,10 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu_rt, T
             }
             Tc outv = scale * (sum * inv_count);
             vhat[gc.at(K, J, I)] = (Tout)outv;
-            acc2 += (double)outv * (double)outv;
+            acc2 += outv * outv;
         }
     }
-    if (ks.d) block_partial_and_finish(acc2, rs, slot, ks, EPI_BETA);
+    if (ks.d) block_partial_and_finish((double)acc2, rs, slot, ks, EPI_BETA);
 }
 
 // 1D specialisation of K3: one thread per coarse column; each fine value is loaded once and
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(256) k_restrict_1d(Geom gf, Geom gc, int nu, T
             l1 = (Tc)0;
         }
     };
-    double acc2 = 0.0;
+    Tc acc2 = (Tc)0;   // per-thread sum in the arithmetic type (FP64 only across threads)
     const int K0 = blockIdx.y * kc;
     const int K1 = min(K0 + kc, gc.nt + 1);
     Tc pr0 = 0, pr1 = 0, Lp0 = 0, Lp1 = 0;
@@ -397,10 +397,10 @@ __global__ void __launch_bounds__(256) k_restrict_1d(Geom gf, Geom gc, int nu, T
         if (active) {
             Tc outv = scale * (sum * inv_count);
             vhat[gc.at(K, 0, I)] = (Tout)outv;
-            acc2 += (double)outv * (double)outv;
+            acc2 += outv * outv;
         }
     }
-    if (ks.d) block_partial_and_finish(acc2, rs, slot, ks, EPI_BETA);
+    if (ks.d) block_partial_and_finish((double)acc2, rs, slot, ks, EPI_BETA);
 }
 
 template <typename Tin, typename Tout, typename Tc>

@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(TT) k_restrict_1d_t(Geom gf, Geom gc, Tc a, Tc
     };
     const Tc scale = sigma ? (Tc)(*sigma) : (Tc)1;
     const int nK = gc.nt + 1 - K0;
-    double acc2 = 0.0;
+    // the norm of vhat for the next level's beta: summed per thread in the arithmetic type
+    // (FP64 per element would run at the FP64 rate, 1/64 of FP32 here), in FP64 across threads
+    Tc acc2 = (Tc)0;
     Tc lp[PT];
     lap(0, lp);
 #pragma unroll
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(TT) k_restrict_1d_t(Geom gf, Geom gc, Tc a, Tc
                                       : (((t1[2 * P] + t1[2 * P + 1]) + t2[2 * P]) + t2[2 * P + 1]);
                     const Tc inv = (2 * I + 1 < nf) ? (Tc)0.5 : (Tc)1;
                     o[P] = (I < gc.nx) ? scale * (sum * inv) : (Tc)0;
-                    acc2 += (double)o[P] * (double)o[P];
+                    acc2 += o[P] * o[P];
                 }
                 st2(vhat + gc.guard + (int64_t)K * gc.plane + i0 / 2, o);
             } else {
@@ -192,13 +194,13 @@ __global__ void __launch_bounds__(TT) k_restrict_1d_t(Geom gf, Geom gc, Tc a, Tc
                 for (int p = 0; p < PT; ++p) {
                     Tc sum = (K == 0) ? t1[p] : t1[p] + t2[p];
                     o[p] = (i0 + p < nf) ? scale * sum : (Tc)0;
-                    acc2 += (double)o[p] * (double)o[p];
+                    acc2 += o[p] * o[p];
                 }
                 st4(vhat + gc.guard + (int64_t)K * gc.plane + i0, o);
             }
         }
     }
-    if (ks.d) block_partial_and_finish(acc2, rs, slot, ks, EPI_BETA);
+    if (ks.d) block_partial_and_finish((double)acc2, rs, slot, ks, EPI_BETA);
 }
 
 // ---------------------------------------------------------------------------------------
