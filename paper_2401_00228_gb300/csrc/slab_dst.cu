@@ -12,7 +12,7 @@
 // run at once instead of s sequential tridiagonal solves per slab.  This is the fast form of
 // the diagonalisation the 2D coarsest solve uses.
 //
-// DST-I through a complex FFT of length N2 = 2(n+1): the odd extension
+// DST-I through a complex FFT of length N2 = 2(n+1), two rows per transform: the odd extension
 //     y_0 = 0, y_m = v_{m-1} (1 <= m <= n), y_{n+1} = 0, y_{N2-m} = -v_{m-1}
 // has Y_m = -2i sum_j v_j sin(pi m (j+1)/(n+1)), so DST(v)_j = -Im(Y_{j+1}) / 2.  The FFT is
 // the shared-memory Stockham FFT of dst_fft.cuh.
@@ -31,7 +31,9 @@ namespace {
 using namespace dstfft;
 
 // rh[k][j] = DST(r_k)_j for every row k = k0..nt (k0 = 0 when the coupling to x_0 is kept).
-// Grid: one block per row.
+// Two rows per FFT: the odd extension of a real row has a purely imaginary transform
+// (Y = -2i S), so with row k in the real and row k+1 in the imaginary part of the input,
+// Y = -2i S_k + 2 S_{k+1}: S_k = -Im(Y)/2 and S_{k+1} = Re(Y)/2.  Grid: one block per pair.
 __global__ void __launch_bounds__(DST_THREADS) k_dst_forward(Geom g, const float *__restrict__ r,
                                                               float *__restrict__ rh, int ldd,
                                                               const float2 *__restrict__ tw,
@@ -41,19 +43,30 @@ __global__ void __launch_bounds__(DST_THREADS) k_dst_forward(Geom g, const float
     if (done && *done) return;
     extern __shared__ float2 sm_dst[];
     float2 *a = sm_dst;
-    const int k = blockIdx.x + k0;
+    const int k = k0 + 2 * blockIdx.x;
+    const bool two = k + 1 <= g.nt;
     const int n = g.nx, N = n + 1;
     const float *row = r + g.guard + (int64_t)k * g.plane;
+    const float *row2 = row + g.plane;
     for (int m = threadIdx.x; m < N2; m += DST_THREADS) {
-        float v = 0.f;
-        if (m > 0 && m < N) v = row[m - 1];
-        else if (m > N) v = -row[N2 - m - 1];
-        a[pad(m)] = make_float2(v, 0.f);
+        float v = 0.f, w = 0.f;
+        if (m > 0 && m < N) {
+            v = row[m - 1];
+            if (two) w = row2[m - 1];
+        } else if (m > N) {
+            v = -row[N2 - m - 1];
+            if (two) w = -row2[N2 - m - 1];
+        }
+        a[pad(m)] = make_float2(v, w);
     }
     __syncthreads();
     fft_smem(a, N2, logN2, tw);
     float *out = rh + (int64_t)k * ldd;
-    for (int j = threadIdx.x; j < n; j += DST_THREADS) out[j] = -0.5f * a[pad(j + 1)].y;
+    for (int j = threadIdx.x; j < n; j += DST_THREADS) {
+        const float2 y = a[pad(j + 1)];
+        out[j] = -0.5f * y.y;
+        if (two) out[ldd + j] = 0.5f * y.x;
+    }
 }
 
 // In place on rh: xh_k = alpha_j xh_{k-1} + beta_j rh_k over each slab, xh = 0 before its
@@ -90,7 +103,8 @@ __global__ void __launch_bounds__(REC_THREADS) k_dst_recurrence(int n, float *__
     }
 }
 
-// x_k = 2/(n+1) DST(xh_k), k = 1..nt; block 0 copies x_0 = r_0.
+// x_k = 2/(n+1) DST(xh_k), k = 1..nt, two rows per FFT as in k_dst_forward; block 0 also
+// copies x_0 = r_0.
 __global__ void __launch_bounds__(DST_THREADS) k_dst_inverse(Geom g, const float *__restrict__ r,
                                                               const float *__restrict__ xh, int ldd,
                                                               const float2 *__restrict__ tw,
@@ -100,25 +114,35 @@ __global__ void __launch_bounds__(DST_THREADS) k_dst_inverse(Geom g, const float
     if (done && *done) return;
     extern __shared__ float2 sm_dst[];
     float2 *a = sm_dst;
-    const int k = blockIdx.x;
     const int n = g.nx, N = n + 1;
-    float *xrow = x + g.guard + (int64_t)k * g.plane;
-    if (k == 0) {
+    if (blockIdx.x == 0) {
         const float *r0 = r + g.guard;
-        for (int i = threadIdx.x; i < n; i += DST_THREADS) xrow[i] = r0[i];
-        return;
+        float *x0 = x + g.guard;
+        for (int i = threadIdx.x; i < n; i += DST_THREADS) x0[i] = r0[i];
     }
+    const int k = 1 + 2 * blockIdx.x;
+    const bool two = k + 1 <= g.nt;
     const float *in = xh + (int64_t)k * ldd;
     for (int m = threadIdx.x; m < N2; m += DST_THREADS) {
-        float v = 0.f;
-        if (m > 0 && m < N) v = in[m - 1];
-        else if (m > N) v = -in[N2 - m - 1];
-        a[pad(m)] = make_float2(v, 0.f);
+        float v = 0.f, w = 0.f;
+        if (m > 0 && m < N) {
+            v = in[m - 1];
+            if (two) w = in[ldd + m - 1];
+        } else if (m > N) {
+            v = -in[N2 - m - 1];
+            if (two) w = -in[ldd + N2 - m - 1];
+        }
+        a[pad(m)] = make_float2(v, w);
     }
     __syncthreads();
     fft_smem(a, N2, logN2, tw);
-    const float sc = -1.f / (float)N;
-    for (int i = threadIdx.x; i < n; i += DST_THREADS) xrow[i] = sc * a[pad(i + 1)].y;
+    const float sc = 1.f / (float)N;
+    float *xrow = x + g.guard + (int64_t)k * g.plane;
+    for (int i = threadIdx.x; i < n; i += DST_THREADS) {
+        const float2 y = a[pad(i + 1)];
+        xrow[i] = -sc * y.y;
+        if (two) xrow[g.plane + i] = sc * y.x;
+    }
 }
 
 }  // namespace
@@ -148,13 +172,13 @@ void launch_slab_1d_dst(const Geom &g, const float *tab, const float2 *tw, int N
     const int k0 = coupled ? 0 : 1;   // row 0 is transformed only when its coupling is kept
     const size_t shm = dst_smem_bytes(N2);
     prof_begin(s);
-    k_dst_forward<<<g.nt + 1 - k0, DST_THREADS, shm, s>>>(g, r, rh, ldd, tw, N2, logN2, k0, done);
+    k_dst_forward<<<(g.nt + 2 - k0) / 2, DST_THREADS, shm, s>>>(g, r, rh, ldd, tw, N2, logN2, k0, done);
     if (!coupled && steps <= DST_SHORT_SLAB)
         k_dst_recurrence<<<dim3((g.nx + REC_THREADS - 1) / REC_THREADS, n_cgs), REC_THREADS, 0, s>>>(
             g.nx, rh, ldd, tab, tab + g.nx, steps, done);
     else
         launch_mode_scan<float>(g.nx, rh, ldd, ModeTable<float>{tab, tab + g.nx}, n_cgs, g.nt, done, s);
-    k_dst_inverse<<<g.nt + 1, DST_THREADS, shm, s>>>(g, r, rh, ldd, tw, N2, logN2, x, done);
+    k_dst_inverse<<<(g.nt + 1) / 2, DST_THREADS, shm, s>>>(g, r, rh, ldd, tw, N2, logN2, x, done);
     prof_end(s, PROF_SLAB, 2.0 * sizeof(float) * (double)g.interior());
     count_launch(3);
 }
