@@ -149,11 +149,12 @@ def run_reference(args, world, rank):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) over algorithmic bytes of the
-# level-1 Arnoldi kernels, from one ncu capture of the launches j = 19 and j = 20 of the first
-# restart cycle of this workload: multidot read 1410.1 MB + wrote 3.1 MB against 1408.1 MB
-# algorithmic (j = 19) and 1477.4 MB against 1475.1 MB (j = 20).  The ratio scales the
-# average algorithmic bytes of a launch to its DRAM traffic.
-DRAM_TRAFFIC_RATIO = {"multidot@level1": 1.0026, "update@level1": 0.9979}
+# level-1 Gram-Schmidt kernels (their current code), from one ncu capture of the launches
+# j = 5 and j = 6 of the first restart cycle of this workload at restart 12 with the exact
+# coarse solve: multidot read 470.1 + wrote 3.0 MB against 469.4 MB algorithmic (j = 5) and
+# 537.3 MB against 536.4 MB (j = 6); update 528.4 MB against 536.4 MB and 593.8 MB against
+# 603.5 MB.  The ratio scales the average algorithmic bytes of a launch to its DRAM traffic.
+DRAM_TRAFFIC_RATIO = {"multidot@level1": 1.005, "update@level1": 0.984}
 
 
 def profiled_classes(mk, torch, dev, solve):
@@ -578,6 +579,9 @@ def main():
                     help="relative residual target of the 2D solve: its error is ~4x its residual "
                          "(1e-9 gives 4.2e-9 against the GPU march, 3e-9 gives 1.7e-8)")
     ap.add_argument("--restart", type=int, default=40)
+    ap.add_argument("--n-cgs", type=int, default=None,
+                    help="coarsest slabs of the headline's base schedule (default: the workload's 16; "
+                         "0 = the exact coupled coarse solve)")
     ap.add_argument("--orth", type=int, default=0, help="Gram-Schmidt passes: 0 one, 1 conditional, 2 two")
     ap.add_argument("--no-aux", action="store_true", help="skip the secondary paths")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-member batch path")
@@ -625,8 +629,9 @@ def main():
 
     def opts(precision):
         return mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner,
-                            n_cgs=s.n_cgs, tol=args.tol, restart=args.restart, precision=precision,
-                            orth=args.orth, autotune=not args.no_autotune)
+                            n_cgs=s.n_cgs if args.n_cgs is None else args.n_cgs, tol=args.tol,
+                            restart=args.restart, precision=precision, orth=args.orth,
+                            autotune=not args.no_autotune)
 
     base_mixed, base_fp64 = opts("mixed"), opts("fp64")
     g_dev = torch.from_numpy(P.g).to(dev)
