@@ -190,6 +190,10 @@ cudaError_t coop_set_attributes();
 // Pdev: the parameters in device memory; N2: the coarsest level's FFT length.
 void launch_inner_coop(const CoopParams *Pdev, int N2, int grid, const int *done, cudaStream_t s);
 
+// Blocks per SM of the small-basis Gram-Schmidt launches that follow on this host thread
+// (0: the default 4).
+void set_krylov_hint(int blocks_per_sm);
+
 // Tile depth (time steps per thread) for the tiled 1D transfer launches that follow on this
 // host thread: restriction in {1, 2, 4, 8}, interpolation in {2, 4}; 0 = built-in heuristic.
 void set_tile_hint(int kc_restrict, int kc_interp);

@@ -292,10 +292,16 @@ __global__ void __launch_bounds__(KR_THREADS) k_update_sb(int64_t len, const T *
     }
 }
 
-// one resident wave: these kernels hold up to 4 blocks of 256 threads per SM
+// blocks per SM of the small-basis kernels for the launches that follow on this host thread
+// (0: 4, one resident wave; the autotuner may pick fewer, fatter blocks for L2-resident
+// vectors, where each block's reduction tail and ticket cost more than the sweep)
+thread_local int t_sb_bpsm = 0;
+
+void set_krylov_hint(int blocks_per_sm) { t_sb_bpsm = blocks_per_sm; }
+
 static int sb_grid(int64_t len) {
     int64_t g = (len + KR_THREADS * SB_EPT - 1) / (KR_THREADS * SB_EPT);
-    const int64_t cap = (int64_t)g_num_sms * 4;
+    const int64_t cap = (int64_t)g_num_sms * (t_sb_bpsm > 0 ? t_sb_bpsm : 4);
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (int)g;

@@ -479,6 +479,7 @@ static thread_local int t_outer_j = -1;
 static void set_ctx(const Level &L, int level) {
     prof_set_context(level + 1, t_outer_j, (double)L.g.interior());
     set_tile_hint(L.kc_r, L.kc_i);
+    set_krylov_hint(L.kr_bpsm);
 }
 
 // x_j = sigma_j V_j - Z vt and w = A x_j (K4).  Level 1 of the mixed solve keeps V and w as
@@ -939,12 +940,40 @@ static void tune_interp(Hierarchy &H, int l, cudaStream_t s, cudaEvent_t e0, cud
     set_tile_hint(0, 0);
 }
 
+// Blocks per SM of an inner level's small-basis Gram-Schmidt (dot products and update of
+// the second basis vector, the common case), on the level's own buffers.
+template <typename Tc>
+static void tune_krylov(Hierarchy &H, int l, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    Level &L = *H.lv[l];
+    const int j = L.m >= 2 ? 1 : 0;
+    float best = 1e30f;
+    for (int b : {1, 2, 4}) {
+        set_krylov_hint(b);
+        const float t = time_launch([&] {
+            launch_multidot<Tc, Tc>(L.g.len, L.W.as<Tc>(), L.V.as<Tc>(), L.stride, j, H.rs, L.ks,
+                                    false, nullptr, s);
+            if (j + 1 < L.m)
+                launch_update<Tc, Tc>(L.g.len, L.W.as<Tc>(), L.V.as<Tc>(), L.stride, j, true,
+                                      H.rs, L.ks, UPD_INNER, false, nullptr, s);
+        }, s, e0, e1);
+        if (t < best) {
+            best = t;
+            L.kr_bpsm = b;
+        }
+    }
+    set_krylov_hint(0);
+}
+
 mk_status autotune_hierarchy(Hierarchy &H, cudaStream_t s) {
     cudaEvent_t e0, e1;
     MKCK(cudaEventCreate(&e0));
     MKCK(cudaEventCreate(&e1));
     const int L = (int)H.lv.size();
     const bool fp64 = H.precision == 0;
+    for (int l = 1; l + 1 < L; ++l) {
+        if (fp64) tune_krylov<double>(H, l, s, e0, e1);
+        else tune_krylov<float>(H, l, s, e0, e1);
+    }
     for (int l = 0; l + 1 < L; ++l) {
         if (fp64) {
             tune_level<double, double>(H, l, s, e0, e1);

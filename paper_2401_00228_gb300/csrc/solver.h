@@ -68,6 +68,7 @@ struct Level {
     // autotuned choices (0 = heuristic): tile depth of the restriction from / interpolation
     // on this level, and the coarsest solver (1 sine transform, 2 partitioned, 3 PCR)
     int kc_r = 0, kc_i = 0, coarse_kind = 0, coarse_kind_best = 0;
+    int kr_bpsm = 0;   // blocks per SM of this level's small-basis Gram-Schmidt (0: default)
     DevMem Sx, Sxi, lamx, Sy, Syi, lamy;
     DevMem fdmbuf;     // 2D coarsest: transformed rows, (nt+1) nx ny in the cycle precision
 };
