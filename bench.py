@@ -772,6 +772,17 @@ def main():
         peak, peak_kind = _peaks()
         line["roofline"] = roofline_of(rows, peak, peak_kind)
         line["kernel_classes"] = class_table(rows)
+        # device time per outer iteration by level (event-bracketed launches of the profiled
+        # solve; its iteration count is that of the level-1 launches)
+        iters_prof = max((r[2] for r in rows if r[4] == 1 and r[3] == "multidot"), default=0)
+        if iters_prof:
+            per_level = {}
+            for r in rows:
+                per_level[r[4]] = per_level.get(r[4], 0.0) + r[0]
+            line["ms_per_outer_iteration_by_level"] = {
+                f"level{lv}": round(ms / iters_prof, 4) for lv, ms in sorted(per_level.items())}
+            line["inner_levels_ms_per_outer_iteration"] = round(
+                sum(ms for lv, ms in per_level.items() if lv >= 2) / iters_prof, 4)
 
         # ---------------- e2e through host buffers ----------------
         g_h = torch.from_numpy(P.g).pin_memory()
