@@ -283,15 +283,15 @@ mk_status mk_problem_shape(const mk_problem *p, int32_t *dim, int32_t *nx, int32
 
 /* mk_tune -- schedule autotuner for one problem: picks the knobs the method leaves free by
    timing complete solves of this problem (its source as set, initial state u0, host or
-   device) to base->tol.  Starting from *base (NULL: defaults), one pass of coordinate
-   descent over
-     - with MK_TUNE_LEVELS in flags: the level count 2 .. base->levels (base's nu and space,
-       inner counts 2 and 1 above the coarsest, the exact coarse solve where it is parallel);
+   device) to base->tol.  Starting from *base (NULL: defaults): with MK_TUNE_LEVELS in flags
+   the level count 2 .. base->levels (base's nu and space, inner counts 2 and 1 above the
+   coarsest, the exact coarse solve where it is parallel), then up to two passes (the second
+   only if the first improved) of coordinate descent over
+     - each inner iteration count m_inner (Sec. 4.1) +1 and -1, deepest level first;
      - n_cgs (Sec. 3.3.2) in {base, 16, 8, 4, 2, 1, 0} (0 is left out for the FP64 path in 1D,
        whose coupled coarse march is sequential);
      - restart (Algorithm 2) in {8, 12, 16, 24, 32, 40, 64} (with MK_TUNE_RESTART_CAP only
        those up to base->restart: the level-1 basis grows with it);
-     - each inner iteration count m_inner (Sec. 4.1) +1 and -1;
    keeping at each step the fastest candidate that converges within base->max_iters (others,
    and candidates the library rejects, are skipped).  At most max_trials solves (0: no limit).
    *best receives the chosen options (tile autotuning on); info (may be NULL) the number of

@@ -225,8 +225,8 @@ def mk_solve_rhs(p: int, f, u_out, opts: Optional[mk_solve_opts] = None, stream=
 def mk_tune(p: int, u0, base: Optional[mk_solve_opts] = None, levels: bool = False,
             max_trials: int = 0, restart_cap: bool = False, stream=None):
     """Schedule autotuner: (best options, mk_tune_info) from timed solves of this problem
-    (n_cgs, restart -- at most base.restart when `restart_cap` --, inner iteration counts; the
-    level count too when `levels`)."""
+    (inner iteration counts, n_cgs, restart -- at most base.restart when `restart_cap` --, in
+    up to two coordinate-descent passes; the level count too when `levels`)."""
     best = mk_solve_opts()
     info = mk_tune_info()
     s = _stream(stream) or _current_stream_for(u0)

@@ -7,9 +7,9 @@
 // Built on the public entry points only (mk_solve, mk_problem_shape): a trial is a solve to
 // the base tolerance; a candidate that does not converge within base->max_iters, or that
 // the library rejects (MK_ERR_INVALID: a slab count that does not divide the coarsest
-// level, too few steps for another level), is skipped.  The search is one pass of
-// coordinate descent: level count (optional), then N_CGS, then restart, then each inner
-// iteration count.  A candidate whose first solve is within 30% of the best so far is
+// level, too few steps for another level), is skipped.  The search: the level count
+// (optional), then up to two passes of coordinate descent over the inner iteration counts
+// (deepest level first), N_CGS and the restart length.  A candidate whose first solve is within 30% of the best so far is
 // solved once more and keeps the faster time (the first solve of new options also builds
 // their hierarchy, autotunes its tiles and captures its graph, all inside solve_ms).
 #include <algorithm>
@@ -114,34 +114,41 @@ extern "C" mk_status mk_tune(mk_problem *p, const double *u0, const mk_solve_opt
             T.trial(o);
         }
     }
-    {   // N_CGS
-        const mk_solve_opts c = T.best;
-        for (int v : ncgs_values(c)) {
-            if (v == c.n_cgs) continue;
-            mk_solve_opts o = c;
-            o.n_cgs = v;
-            T.trial(o);
+    // coordinate descent: inner counts (deepest intermediate level first, +1 then -1), then
+    // N_CGS, then the restart length; a second pass when the first improved anything (the
+    // knobs interact: a coupled coarse solve pays off only once the level above it iterates
+    // enough), within the trial budget
+    for (int pass = 0; pass < 2; ++pass) {
+        const double start_ms = T.best_ms;
+        for (int l = T.best.levels - 3; l >= 0; --l) {
+            for (int d : {+1, -1}) {
+                const mk_solve_opts c = T.best;
+                mk_solve_opts o = c;
+                o.m_inner[l] = c.m_inner[l] + d;
+                if (o.m_inner[l] < 1 || o.m_inner[l] > mk::MK_MAX_INNER) continue;
+                T.trial(o);
+            }
         }
-    }
-    {   // restart length
-        const mk_solve_opts c = T.best;
-        for (int r : {8, 12, 16, 24, 32, 40, 64}) {
-            if (r == c.restart || r > mk::MK_MAX_RESTART) continue;
-            if ((flags & MK_TUNE_RESTART_CAP) && r > b.restart) continue;
-            mk_solve_opts o = c;
-            o.restart = r;
-            T.trial(o);
-        }
-    }
-    // inner iteration counts, one level at a time (+1, then -1)
-    for (int l = 0; l + 2 < T.best.levels; ++l) {
-        for (int d : {+1, -1}) {
+        {
             const mk_solve_opts c = T.best;
-            mk_solve_opts o = c;
-            o.m_inner[l] = c.m_inner[l] + d;
-            if (o.m_inner[l] < 1 || o.m_inner[l] > mk::MK_MAX_INNER) continue;
-            T.trial(o);
+            for (int v : ncgs_values(c)) {
+                if (v == c.n_cgs) continue;
+                mk_solve_opts o = T.best;
+                o.n_cgs = v;
+                T.trial(o);
+            }
         }
+        {
+            const mk_solve_opts c = T.best;
+            for (int r : {8, 12, 16, 24, 32, 40, 64}) {
+                if (r == c.restart || r > mk::MK_MAX_RESTART) continue;
+                if ((flags & MK_TUNE_RESTART_CAP) && r > b.restart) continue;
+                mk_solve_opts o = T.best;
+                o.restart = r;
+                T.trial(o);
+            }
+        }
+        if (!(T.best_ms < start_ms)) break;
     }
     cudaStreamSynchronize((cudaStream_t)stream);
     cudaFree(u);

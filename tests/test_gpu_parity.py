@@ -546,15 +546,19 @@ def test_full_size_2d_workload(large_2d):
     assert np.linalg.norm(f - lv.apply_A(u)) / np.linalg.norm(f) <= 1e-11
 
 
-@pytest.mark.parametrize("n_cgs", [16, 0])
-def test_full_size_2d_at_bench_tolerance(large_2d, n_cgs):
-    """The 2D bench operating point: relative residual 1e-9 (the error runs about 4x the
-    residual on this workload), the schedule's 16 slabs or the exact coarse solve, autotuned
-    tiles: the whole solution within the metric's 1e-8 of the oracle's march."""
+@pytest.mark.parametrize("m_inner,n_cgs,restart", [((2, 1), 16, 40), ((2, 1), 0, 40),
+                                                    ((2, 2), 0, 12), ((2, 2), 0, 16)])
+def test_full_size_2d_at_bench_tolerance(large_2d, m_inner, n_cgs, restart):
+    """The 2D bench operating points: relative residual 1e-9 (the error runs about 4x the
+    residual on this workload), the schedule's inner counts and 16 slabs, the exact coarse
+    solve, and the points the schedule autotuner picks (two inner iterations on both
+    intermediate levels with the exact coarse solve), autotuned tiles: the whole solution
+    within the metric's 1e-8 of the oracle's march."""
     P, ref = large_2d
     s = P.schedule
-    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=n_cgs,
-                     tol=1e-9, restart=40, precision="mixed", orth=0, autotune=True, max_iters=3000)
+    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=m_inner, n_cgs=n_cgs,
+                     tol=1e-9, restart=restart, precision="mixed", orth=0, autotune=True,
+                     max_iters=3000)
     with _prob(P) as p:
         u = np.empty((P.nt + 1, P.ny, P.nx))
         info = mk.mk_solve(p.handle, P.u0, u, o)
