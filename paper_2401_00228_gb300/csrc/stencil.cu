@@ -315,6 +315,135 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu_rt, T
     if (ks.d) block_partial_and_finish((double)acc2, rs, slot, ks, EPI_BETA);
 }
 
+// 2D specialisation of K3 for 2 x 2 agglomeration and nu = 2 (every coarsening of the 2D
+// workloads): a thread owns the aggregate (I, J), i.e. fine points (2I, 2I+1) x (2J, 2J+1),
+// and walks its chunk of coarse steps.  Each fine step it loads its 2 x 2 values and the two
+// points of the rows 2J-1 and 2J+2 as four vector loads (the pair 2I, 2I+1 is 8- or 16-byte
+// aligned: 2I is even and rows start at multiples of 8 elements); the x neighbours 2I-1 and
+// 2I+2 come from the adjacent lanes by warp shuffles, and the two edge lanes of a warp load
+// theirs.  Every lane runs the loop (lanes past the grid carry zeros and store nothing).
+// Points outside the fine grid (the singleton edge of an odd size) are masked.
+template <typename Tc>
+__device__ __forceinline__ void ld_pair(const float2 *p, Tc &a, Tc &b) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);   // double-float pairs: hi parts
+    a = (Tc)q.x;
+    b = (Tc)q.z;
+}
+template <typename Tc>
+__device__ __forceinline__ void ld_pair(const float *p, Tc &a, Tc &b) {
+    const float2 q = *reinterpret_cast<const float2 *>(p);
+    a = (Tc)q.x;
+    b = (Tc)q.y;
+}
+template <typename Tc>
+__device__ __forceinline__ void ld_pair(const double *p, Tc &a, Tc &b) {
+    const double2 q = *reinterpret_cast<const double2 *>(p);
+    a = (Tc)q.x;
+    b = (Tc)q.y;
+}
+
+template <typename Tin, typename Tout, typename Tc>
+__global__ void __launch_bounds__(256) k_restrict_2d_ts(Geom gf, Geom gc, Tc a, Tc b, Tc mu,
+                                                        SpaceOp<Tc> L, const Tin *__restrict__ v,
+                                                        const double *__restrict__ sigma,
+                                                        Tout *__restrict__ vhat, int kc,
+                                                        ReduceScratch rs, int slot, KState ks,
+                                                        const int *__restrict__ done) {
+    if (done && *done) return;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;   // blocks are 32 x 8: a warp is one row of 32 I's
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int chunk = blockIdx.z;
+    const bool active = I < gc.nx && J < gc.ny;
+    const int i0 = 2 * I, i1 = 2 * I + 1, j0 = 2 * J, j1 = 2 * J + 1;
+    const bool in00 = active, in01 = active && i1 < gf.nx;              // (j0, i0), (j0, i1)
+    const bool in10 = active && j1 < gf.ny, in11 = in10 && i1 < gf.nx;  // (j1, i0), (j1, i1)
+    const Tc *cx = L.x, *cy = L.y;
+    const int nxf = gf.nx, nyf = gf.ny;
+    // coefficients of the thread's columns and rows (0 where masked)
+    const Tc xl0 = in00 ? cx[i0] : (Tc)0, xd0 = in00 ? cx[nxf + i0] : (Tc)0, xu0 = in00 ? cx[2 * nxf + i0] : (Tc)0;
+    const Tc xl1 = in01 ? cx[i1] : (Tc)0, xd1 = in01 ? cx[nxf + i1] : (Tc)0, xu1 = in01 ? cx[2 * nxf + i1] : (Tc)0;
+    const Tc yl0 = in00 ? cy[j0] : (Tc)0, yd0 = in00 ? cy[nyf + j0] : (Tc)0, yu0 = in00 ? cy[2 * nyf + j0] : (Tc)0;
+    const Tc yl1 = in10 ? cy[j1] : (Tc)0, yd1 = in10 ? cy[nyf + j1] : (Tc)0, yu1 = in10 ? cy[2 * nyf + j1] : (Tc)0;
+    const int npts = (int)in00 + (int)in01 + (int)in10 + (int)in11;
+    const Tc inv_count = npts > 0 ? (Tc)1 / (Tc)npts : (Tc)0;
+    const Tc scale = sigma ? (Tc)(*sigma) : (Tc)1;
+    // values and Laplacians of the four points at fine step kf
+    auto step = [&](int kf, Tc (&c)[4], Tc (&l)[4]) {
+        const int64_t r0 = gf.at(kf, j0, 0);
+        Tc u0a = 0, u0b = 0, u1a = 0, u1b = 0, dna = 0, dnb = 0, upa = 0, upb = 0;
+        if (active) {
+            ld_pair<Tc>(v + r0 + i0, u0a, u0b);                 // row j0
+            ld_pair<Tc>(v + r0 + gf.ldx + i0, u1a, u1b);        // row j1 (the zero row at ny)
+            ld_pair<Tc>(v + r0 - gf.ldx + i0, dna, dnb);        // row j0 - 1 (zero below j = 0)
+            ld_pair<Tc>(v + r0 + 2 * gf.ldx + i0, upa, upb);    // row j1 + 1
+        }
+        // x neighbours: 2I - 1 is the left lane's second column, 2I + 2 the right lane's first
+        Tc l0 = __shfl_up_sync(FULL, u0b, 1), l1 = __shfl_up_sync(FULL, u1b, 1);
+        Tc r0v = __shfl_down_sync(FULL, u0a, 1), r1v = __shfl_down_sync(FULL, u1a, 1);
+        if (lane == 0) {
+            l0 = active ? ldv<Tc>(v, r0 + i0 - 1) : (Tc)0;
+            l1 = active ? ldv<Tc>(v, r0 + gf.ldx + i0 - 1) : (Tc)0;
+        }
+        if (lane == 31) {
+            r0v = active ? ldv<Tc>(v, r0 + i1 + 1) : (Tc)0;
+            r1v = active ? ldv<Tc>(v, r0 + gf.ldx + i1 + 1) : (Tc)0;
+        }
+        c[0] = u0a; c[1] = u0b; c[2] = u1a; c[3] = u1b;
+        // the order of lap_at: x part, then the y part added
+        l[0] = (xd0 * u0a + xl0 * l0 + xu0 * u0b) + (yd0 * u0a + yl0 * dna + yu0 * u1a);
+        l[1] = (xd1 * u0b + xl1 * u0a + xu1 * r0v) + (yd0 * u0b + yl0 * dnb + yu0 * u1b);
+        l[2] = (xd0 * u1a + xl0 * l1 + xu0 * u1b) + (yd1 * u1a + yl1 * u0a + yu1 * upa);
+        l[3] = (xd1 * u1b + xl1 * u1a + xu1 * r1v) + (yd1 * u1b + yl1 * u0b + yu1 * upb);
+    };
+    const bool m[4] = {in00, in01, in10, in11};
+    Tc prev[4] = {0, 0, 0, 0}, Lprev[4] = {0, 0, 0, 0};
+    const int K0 = chunk * kc;
+    const int K1 = min(K0 + kc, gc.nt + 1);
+    if (K0 > 0) step(2 * (K0 - 1), prev, Lprev);
+    Tc acc2 = (Tc)0;   // per-thread sum in the arithmetic type (FP64 only across threads)
+    for (int K = K0; K < K1; ++K) {
+        Tc sum = 0;
+        if (K == 0) {
+            Tc c[4], l[4];
+            step(0, c, l);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (m[q]) sum += c[q] - mu * c[q];
+                prev[q] = c[q];
+                Lprev[q] = l[q];
+            }
+        } else {
+            Tc c1[4], l1[4], c2[4], l2[4];
+            step(2 * K - 1, c1, l1);
+            step(2 * K, c2, l2);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (m[q]) {
+                    const Tc av1 = (c1[q] - a * l1[q]) - (prev[q] + b * Lprev[q]);
+                    sum += av1 - mu * c1[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (m[q]) {
+                    const Tc av2 = (c2[q] - a * l2[q]) - (c1[q] + b * l1[q]);
+                    sum += av2 - mu * c2[q];
+                }
+                prev[q] = c2[q];
+                Lprev[q] = l2[q];
+            }
+        }
+        if (active) {
+            const Tc outv = scale * (sum * inv_count);
+            vhat[gc.at(K, J, I)] = (Tout)outv;
+            acc2 += outv * outv;
+        }
+    }
+    if (ks.d) block_partial_and_finish((double)acc2, rs, slot, ks, EPI_BETA);
+}
+
 // 1D specialisation of K3: one thread per coarse column; each fine value is loaded once and
 // its spatial neighbours come from the adjacent lanes (warp shuffles; the two edge lanes of
 // a warp load their outer neighbour).  With agglomeration a thread owns the fine pair
@@ -440,6 +569,10 @@ void launch_restrict(const Geom &gf, const Geom &gc, int nu, bool space, const W
         // 1D, nu = 2: time-tiled kernel (transfer1d.cu)
     } else if (gf.dim == 1) {
         if (space) MK_RESTRICT1(true); else MK_RESTRICT1(false);
+    } else if (space && nu == 2) {
+        // 2 x 2 agglomeration with nu = 2: aggregate-per-thread kernel with vector loads
+        k_restrict_2d_ts<Tin, Tout, Tc><<<l.grid, l.block, 0, s>>>(gf, gc, a, b, mu, L, v, sigma,
+                                                                    vhat, kc, rs, slot, ks_c, done);
     } else {
         if (space) MK_RESTRICT(2, true); else MK_RESTRICT(2, false);
     }
