@@ -84,6 +84,39 @@ __device__ __forceinline__ df lap5_df(float l, float r, float d, float u, float 
     return fast_two_sum(t.hi, t.lo + s.lo);
 }
 
+// (l + r) + (d + u) - 4 c of five floats as an unnormalised pair (hi, lo): the leading sums
+// by TwoSum, their four rounding errors added in FP32 (error of order 2^-47 of the largest
+// operand; the pair is renormalised by whatever consumes it)
+__device__ __forceinline__ df lap5_pair(float l, float r, float d, float u, float c) {
+    const df a = two_sum(l, r), b = two_sum(d, u);
+    const df s = two_sum(a.hi, b.hi);
+    const df t = two_sum(s.hi, -4.f * c);
+    return {t.hi, ((a.lo + b.lo) + s.lo) + t.lo};
+}
+
+// a x + b y of double-float operands (x, y possibly unnormalised), renormalised once by its
+// consumer: the leading products exact (TwoProduct), their sum by TwoSum, the cross terms
+// a.hi x.lo + a.lo x.hi (and for b, y) and the errors in FP32; the lo*lo terms are dropped
+// (relative 2^-48)
+__device__ __forceinline__ df df_dot2(df a, df x, df b, df y) {
+    const df p = two_prod(a.hi, x.hi), q = two_prod(b.hi, y.hi);
+    const df s = two_sum(p.hi, q.hi);
+    const float lo = fmaf(a.hi, x.lo, fmaf(a.lo, x.hi, p.lo)) + fmaf(b.hi, y.lo, fmaf(b.lo, y.hi, q.lo));
+    return {s.hi, s.lo + lo};
+}
+__device__ __forceinline__ df df_dot1(df a, df x) {
+    const df p = two_prod(a.hi, x.hi);
+    return {p.hi, fmaf(a.hi, x.lo, fmaf(a.lo, x.hi, p.lo))};
+}
+
+// (c - p) - D for floats c, p and a double-float D (possibly unnormalised): c - p exact by
+// TwoSum, one TwoSum with D.hi, the low parts in FP32, one renormalisation
+__device__ __forceinline__ df df_diff_sub(float c, float p, df D) {
+    const df d = two_sum(c, -p);
+    const df e = two_sum(d.hi, -D.hi);
+    return fast_two_sum(e.hi, (d.lo - D.lo) + e.lo);
+}
+
 __host__ __device__ __forceinline__ float2 df_pack(df x) { return make_float2(x.hi, x.lo); }
 __host__ __device__ __forceinline__ df df_unpack(float2 v) { return {v.x, v.y}; }
 

@@ -382,6 +382,184 @@ __global__ void __launch_bounds__(256) k_interp_df_1d(Geom gf, Geom gc, int nu,
     }
 }
 
+// 2D K4 in double-float with 2 x 2 aggregates and a uniform fine operator, walked in time.
+// A thread owns the aggregate (I, J): the fine points (2I, 2I+1) x (2J, 2J+1), which share
+// one coarse value (Z vt)_{K(k)}.  Per fine step it forms x at those four points and at the
+// two points of each adjacent row (2J-1 and 2J+2, from the aggregates J-1 and J+1); the
+// columns 2I-1 and 2I+2 come from the neighbouring lanes by warp shuffles (the first and
+// last lane form them itself).  The five-point sums S(x_{k-1}) stay in registers from the
+// previous step, so x and w are written once per point and v is read once per point from
+// HBM (the adjacent rows are the neighbouring threads' rows, served by the caches).  The
+// global loads of step k+1 are issued before step k is computed.
+//   w_0 = x_0,  w_k = (x_k - x_{k-1}) - [a c S(x_k) + b c S(x_{k-1})]    (SQ: cx = cy = c)
+//   w_k = (x_k - x_{k-1}) - [a cx Sx(x_k) + b cx Sx(x_{k-1})] - [a cy Sy(x_k) + b cy Sy(x_{k-1})]
+// in double-float (lap5_pair / lap3_exact, df_dot2, df_diff_sub); u = [a cx, b cx, a cy, b cy].
+// MC: number of coarse directions combined, vt = sum_m y_m Xc_m (0: Xc itself).
+// Row starts are multiples of eight elements and i0 is even, so the paired accesses are
+// 16-byte (v, w) and 8-byte (x) aligned; a row is read only where it is interior.
+__device__ __forceinline__ float4 ld_df_pair(const float2 *p) {
+    return *reinterpret_cast<const float4 *>(p);
+}
+
+template <bool SQ, bool HAS_B, int MC>
+__global__ void __launch_bounds__(256, 2) k_interp_df_2d_ts(Geom gf, Geom gc, int nu,
+                                                            const float2 *__restrict__ u,
+                                                            const float2 *__restrict__ v,
+                                                            const double *__restrict__ sigma,
+                                                            const float *__restrict__ Xc,
+                                                            int64_t xc_stride,
+                                                            const double *__restrict__ yc,
+                                                            float *__restrict__ x,
+                                                            float2 *__restrict__ w, int kc,
+                                                            const int *__restrict__ done) {
+    if (done && *done) return;   // the same flag for every thread of the block
+    constexpr int NZ = MC > 0 ? MC : 1;
+    __shared__ float s_w[NZ + 1];
+    const int t = threadIdx.x + 32 * threadIdx.y;
+    if (t == 0) s_w[0] = sigma ? (float)(*sigma) : 1.f;
+    else if (MC > 0 && t <= MC) s_w[t] = (float)yc[t - 1];
+    __syncthreads();
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x;
+    const int I = blockIdx.x * 32 + lane;
+    const int J = blockIdx.y * 8 + threadIdx.y;
+    const int nx = gf.nx, ny = gf.ny;
+    const int64_t ldx = gf.ldx, cld = gc.ldx;
+    const int i0 = 2 * I, j0 = 2 * J;
+    if (j0 >= ny) return;   // the whole warp shares J
+    const float sig = s_w[0];
+    float ym[NZ];
+#pragma unroll
+    for (int m = 0; m < NZ; ++m) ym[m] = MC > 0 ? s_w[1 + m] : 1.f;
+    const bool c0 = i0 < nx, c1 = i0 + 1 < nx, r1 = j0 + 1 < ny;
+    const bool hd = c0 && j0 > 0, hu = c0 && j0 + 2 < ny;
+    const bool cl = lane == 0 && i0 > 0 && i0 - 1 < nx, cr = lane == 31 && i0 + 2 < nx;
+    const int64_t o0 = (int64_t)j0 * ldx + i0;   // fine offset of (2J, 2I) in a plane
+    const int64_t oc = (int64_t)J * cld + I;      // coarse offset of (J, I)
+    const int64_t oe = o0 + (cl ? -1 : 2);        // outside column of the first / last lane
+    const int64_t oce = oc + (cl ? -1 : 1);
+    const df ua = df_unpack(u[0]), ub = df_unpack(u[1]);
+    const df uay = df_unpack(u[2]), uby = df_unpack(u[3]);
+    // raw loads of one step
+    const float4 Z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 A0 = Z4, A1 = Z4, QD = Z4, QU = Z4;
+    float ZO[NZ], ZD[NZ], ZU[NZ], ZE[NZ], VE0 = 0.f, VE1 = 0.f;
+    auto load = [&](int k, int K) {
+        const float2 *vk = v + gf.guard + (int64_t)k * gf.plane;
+        const float *zk = Xc + gc.guard + (int64_t)K * gc.plane;
+        A0 = c0 ? ld_df_pair(vk + o0) : Z4;
+        A1 = (c0 && r1) ? ld_df_pair(vk + o0 + ldx) : Z4;
+        QD = hd ? ld_df_pair(vk + o0 - ldx) : Z4;
+        QU = hu ? ld_df_pair(vk + o0 + 2 * ldx) : Z4;
+#pragma unroll
+        for (int m = 0; m < NZ; ++m) {
+            const float *zm = zk + (int64_t)m * xc_stride;
+            ZO[m] = c0 ? zm[oc] : 0.f;
+            ZD[m] = hd ? zm[oc - cld] : 0.f;
+            ZU[m] = hu ? zm[oc + cld] : 0.f;
+            ZE[m] = (cl || cr) ? zm[oce] : 0.f;
+        }
+        VE0 = (cl || cr) ? vk[oe].x : 0.f;
+        VE1 = ((cl || cr) && r1) ? vk[oe + ldx].x : 0.f;
+    };
+    // (Z vt) from the raw coarse values
+    auto comb = [&](const float (&zr)[NZ]) -> float {
+        if (MC == 0) return zr[0];
+        float z = ym[0] * zr[0];
+#pragma unroll
+        for (int m = 1; m < NZ; ++m) z = fmaf(ym[m], zr[m], z);
+        return z;
+    };
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(k0 + kc, gf.nt + 1);
+    const int kstart = k0 > 0 ? k0 - 1 : 0;
+    // coarse block of fine step k: 0 for k = 0, (k-1)/nu + 1 otherwise (tracked incrementally)
+    int K = (kstart == 0) ? 0 : (kstart - 1) / nu + 1;
+    int ph = (kstart == 0) ? nu - 1 : (kstart - 1) % nu;
+    float p00 = 0.f, p01 = 0.f, p10 = 0.f, p11 = 0.f;   // x_{k-1}
+    // S(x_{k-1}) (SQ), or Sx and Sy
+    df s00 = {0.f, 0.f}, s01 = s00, s10 = s00, s11 = s00;
+    df y00 = s00, y01 = s00, y10 = s00, y11 = s00;
+    load(kstart, K);
+    for (int k = kstart; k < k1; ++k) {
+        const float4 a0 = A0, a1 = A1, qd = QD, qu = QU;
+        const float zo = comb(ZO), zd = comb(ZD), zu = comb(ZU), ze = comb(ZE);
+        const float ve0 = VE0, ve1 = VE1;
+        if (k + 1 < k1) {
+            if (ph == nu - 1) {
+                ++K;
+                ph = 0;
+            } else {
+                ++ph;
+            }
+            load(k + 1, K);
+        }
+        const float x00 = c0 ? sig * a0.x - zo : 0.f;
+        const float x01 = c1 ? sig * a0.z - zo : 0.f;
+        const float x10 = (c0 && r1) ? sig * a1.x - zo : 0.f;
+        const float x11 = (c1 && r1) ? sig * a1.z - zo : 0.f;
+        const float d0 = hd ? sig * qd.x - zd : 0.f, d1 = (hd && c1) ? sig * qd.z - zd : 0.f;
+        const float e0 = hu ? sig * qu.x - zu : 0.f, e1 = (hu && c1) ? sig * qu.z - zu : 0.f;
+        float l0 = __shfl_up_sync(FULL, x01, 1), l1 = __shfl_up_sync(FULL, x11, 1);
+        float q0 = __shfl_down_sync(FULL, x00, 1), q1 = __shfl_down_sync(FULL, x10, 1);
+        const float xe0 = (cl || cr) ? sig * ve0 - ze : 0.f;
+        const float xe1 = ((cl || cr) && r1) ? sig * ve1 - ze : 0.f;
+        if (lane == 0) {
+            l0 = xe0;
+            l1 = xe1;
+        }
+        if (lane == 31) {
+            q0 = xe0;
+            q1 = xe1;
+        }
+        // stencil (left, right, down, up, centre) at the four points
+        df S00, S01, S10, S11, Y00, Y01, Y10, Y11;
+        if (SQ) {
+            S00 = lap5_pair(l0, x01, d0, x10, x00);
+            S01 = lap5_pair(x00, q0, d1, x11, x01);
+            S10 = lap5_pair(l1, x11, x00, e0, x10);
+            S11 = lap5_pair(x10, q1, x01, e1, x11);
+        } else {
+            S00 = lap3_exact(l0, x00, x01); Y00 = lap3_exact(d0, x00, x10);
+            S01 = lap3_exact(x00, x01, q0); Y01 = lap3_exact(d1, x01, x11);
+            S10 = lap3_exact(l1, x10, x11); Y10 = lap3_exact(x00, x10, e0);
+            S11 = lap3_exact(x10, x11, q1); Y11 = lap3_exact(x01, x11, e1);
+        }
+        if (k >= k0 && c0) {
+            auto wk = [&](float c, float p, df S, df Sp, df Y, df Yp) -> df {
+                if (k == 0) return df_from_float(c);
+                df D;
+                if (SQ) {
+                    D = HAS_B ? df_dot2(ua, S, ub, Sp) : df_dot1(ua, S);
+                } else {
+                    const df dx = HAS_B ? df_dot2(ua, S, ub, Sp) : df_dot1(ua, S);
+                    const df dy = HAS_B ? df_dot2(uay, Y, uby, Yp) : df_dot1(uay, Y);
+                    D = df_add(fast_two_sum(dx.hi, dx.lo), fast_two_sum(dy.hi, dy.lo));
+                }
+                return df_diff_sub(c, p, D);
+            };
+            const int64_t f0 = gf.guard + (int64_t)k * gf.plane + o0;
+            const df w00 = wk(x00, p00, S00, s00, Y00, y00);
+            const df w01 = c1 ? wk(x01, p01, S01, s01, Y01, y01) : df{0.f, 0.f};
+            *reinterpret_cast<float2 *>(x + f0) = make_float2(x00, x01);
+            *reinterpret_cast<float4 *>(w + f0) = make_float4(w00.hi, w00.lo, w01.hi, w01.lo);
+            if (r1) {
+                const df w10 = wk(x10, p10, S10, s10, Y10, y10);
+                const df w11 = c1 ? wk(x11, p11, S11, s11, Y11, y11) : df{0.f, 0.f};
+                *reinterpret_cast<float2 *>(x + f0 + ldx) = make_float2(x10, x11);
+                *reinterpret_cast<float4 *>(w + f0 + ldx) = make_float4(w10.hi, w10.lo, w11.hi, w11.lo);
+            }
+        }
+        p00 = x00; p01 = x01; p10 = x10; p11 = x11;
+        if (HAS_B) {
+            s00 = S00; s01 = S01; s10 = S10; s11 = S11;
+            if (!SQ) {
+                y00 = Y00; y01 = Y01; y10 = Y10; y11 = Y11;
+            }
+        }
+    }
+}
+
 void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const float2 *ca,
                       const float2 *cb, bool has_b, const float2 *v, const double *sigma,
                       const float *Xc, int mc, int64_t xc_stride, const double *yc, float *x,
@@ -410,6 +588,37 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
         // 1D, nu = 2: time-tiled kernel (transfer1d.cu)
     } else if (gf.dim == 1) {
         if (space) MK_IDF1(true); else MK_IDF1(false);
+    } else if (space && uniform_ab && (!yc || (mc >= 1 && mc <= 4))) {
+        // 2 x 2 agglomeration, uniform operator: aggregate-per-thread kernel walked in time;
+        // chunks for one full wave of 2048 threads per SM, at least eight fine steps each
+        // (the step before a chunk is formed again), at most 65535 chunks
+        const int ncx = (gf.nx + 1) / 2, ncy = (gf.ny + 1) / 2;
+        const int nsteps = gf.nt + 1;
+        const int64_t want = (int64_t)g_num_sms * 2048;
+        int64_t kt = ((int64_t)ncx * ncy * nsteps) / (want > 0 ? want : 1);
+        if (kt < 8) kt = 8;
+        if (kt > nsteps) kt = nsteps;
+        while ((nsteps + kt - 1) / kt > 65535) ++kt;
+        const int kct = (int)kt;
+        const dim3 grid((ncx + 31) / 32, (ncy + 7) / 8, (nsteps + kct - 1) / kct), blk(32, 8, 1);
+#define MK_IDF2M(SQ, HB, M)                                                                     \
+    k_interp_df_2d_ts<SQ, HB, M><<<grid, blk, 0, s>>>(gf, gc, nu, uniform_ab, v, sigma, Xc,      \
+                                                      xc_stride, yc, x, wout, kct, done)
+#define MK_IDF2(SQ, HB)                                                                         \
+    do {                                                                                        \
+        if (!yc) MK_IDF2M(SQ, HB, 0);                                                           \
+        else if (mc == 1) MK_IDF2M(SQ, HB, 1);                                                  \
+        else if (mc == 2) MK_IDF2M(SQ, HB, 2);                                                  \
+        else if (mc == 3) MK_IDF2M(SQ, HB, 3);                                                  \
+        else MK_IDF2M(SQ, HB, 4);                                                               \
+    } while (0)
+        if (uniform_square) {
+            if (hb) MK_IDF2(true, true); else MK_IDF2(true, false);
+        } else {
+            if (hb) MK_IDF2(false, true); else MK_IDF2(false, false);
+        }
+#undef MK_IDF2
+#undef MK_IDF2M
     } else {
         // 2D: x once per point, then w = A x in double-float from the stored x
         const dim3 g2 = grid_2d_points(gf), g4 = grid_2d_points4(gf), b2(32, 8, 1);
