@@ -359,6 +359,20 @@ mk_status mk_op_interp_correct(mk_problem *p, const mk_solve_opts *opts, int32_t
                                int32_t precision, const double *v, const double *vt,
                                double *x, double *w, void *stream);
 
+/* The same step with the full argument set of the solve: x = sigma v - Z vt with
+   vt = sum_{m < nvt} y_m vt_m (the scaled basis vector and the inner FGMRES combination of
+   the coarser level, substeps 4.4-4.5 of Algorithm 2), and w = A_l x.  vt: nvt consecutive
+   level-(l+1) arrays; y: nvt host doubles, or NULL with nvt = 1 (vt used as it is).
+   precision 0: FP64; 1: FP32; 2: the level-1 path of the mixed solve -- v rounded to a
+   double-float pair (hi, lo) and vt to FP32, x formed in FP32 from the leading part of v,
+   w = A_1 x evaluated in double-float arithmetic and returned as hi + lo (level 1 only,
+   opts->precision 1).  Errors as above; MK_ERR_INVALID also for nvt outside 1..8, y NULL
+   with nvt > 1, or precision 2 with level != 1 or opts->precision != 1. */
+mk_status mk_op_interp_combine(mk_problem *p, const mk_solve_opts *opts, int32_t level,
+                               int32_t precision, const double *v, double sigma,
+                               const double *vt, int32_t nvt, const double *y, double *x,
+                               double *w, void *stream);
+
 /* x = Atilde_L^{-1} r on the coarsest level (decoupled slabs, Eq. (Qhtilde); n_cgs = 0: the
    exact coarse matrix; with MK_TRANSFER_MGRIT the theta-scheme of Eq. (coarsemat)). */
 mk_status mk_op_coarsest(mk_problem *p, const mk_solve_opts *opts, int32_t precision,

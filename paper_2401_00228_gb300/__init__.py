@@ -19,7 +19,7 @@ from ._lib import (MK_MAX_LEVELS, MKError, mk_level_desc, mk_solve_info, mk_solv
 
 __all__ = ["mk_default_opts", "mk_create_problem", "mk_set_source", "mk_destroy", "mk_solve",
            "mk_solve_rhs", "mk_march", "mk_tune", "mk_trim", "mk_schedule_alternate", "mk_adjoint", "mk_level_info", "mk_op_rhs", "mk_op_apply",
-           "mk_op_residual", "mk_op_residual_noalloc", "mk_problem_shape", "mk_op_restrict", "mk_op_interp_correct", "mk_op_coarsest",
+           "mk_op_residual", "mk_op_residual_noalloc", "mk_problem_shape", "mk_op_restrict", "mk_op_interp_correct", "mk_op_interp_combine", "mk_op_coarsest",
            "mk_op_precond", "mk_op_orthogonalize", "mk_op_lsq", "mk_kernel_launch_count",
            "mk_create_batch", "mk_solve_batch", "mk_destroy_batch", "Batch",
            "make_opts", "Problem", "HeatSolve", "MKError", "lib", "solve"]
@@ -327,6 +327,19 @@ def mk_op_interp_correct(p: int, opts, level: int, precision: int, v, vt, x, w, 
     _lib.check(lib().mk_op_interp_correct(p, ctypes.byref(opts) if opts else None, level, precision,
                                           _ptr(v), _ptr(vt), _ptr(x), _ptr(w), _stream(stream)),
                "mk_op_interp_correct")
+
+
+def mk_op_interp_combine(p: int, opts, level: int, precision: int, v, sigma: float, vt, nvt: int,
+                         y, x, w, stream=None) -> None:
+    """x = sigma v - Z (sum_m y_m vt_m), w = A x; vt holds nvt consecutive coarse arrays, y the
+    nvt weights (a host sequence, or None with nvt = 1).  precision 2: the level-1 double-float
+    path of the mixed solve."""
+    yh = None if y is None else np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+    if yh is not None and yh.size != nvt:
+        raise ValueError("y must hold nvt weights")
+    _lib.check(lib().mk_op_interp_combine(p, ctypes.byref(opts) if opts else None, level, precision,
+                                          _ptr(v), float(sigma), _ptr(vt), nvt, _ptr(yh), _ptr(x),
+                                          _ptr(w), _stream(stream)), "mk_op_interp_combine")
 
 
 def mk_op_coarsest(p: int, opts, precision: int, r, x, stream=None) -> None:

@@ -102,6 +102,8 @@ SIGNATURES = {
     "mk_op_residual_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "mk_op_restrict": (ctypes.c_int, [_P, ctypes.POINTER(mk_solve_opts), _I, _I, _P, _P, _P]),
     "mk_op_interp_correct": (ctypes.c_int, [_P, ctypes.POINTER(mk_solve_opts), _I, _I, _P, _P, _P, _P, _P]),
+    "mk_op_interp_combine": (ctypes.c_int, [_P, ctypes.POINTER(mk_solve_opts), _I, _I, _P, _D, _P, _I,
+                                            _P, _P, _P, _P]),
     "mk_op_coarsest": (ctypes.c_int, [_P, ctypes.POINTER(mk_solve_opts), _I, _P, _P, _P]),
     "mk_op_precond": (ctypes.c_int, [_P, ctypes.POINTER(mk_solve_opts), _I, _P, _P, _P]),
     "mk_op_orthogonalize": (ctypes.c_int, [_P, _I, _P, _P, _P, _P]),

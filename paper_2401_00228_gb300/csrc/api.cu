@@ -735,6 +735,85 @@ mk_status mk_op_interp_correct(mk_problem *p, const mk_solve_opts *opts, int32_t
 
 }  // extern "C"
 
+// x = sigma v - Z sum_m y_m vt_m and w = A x with the types of the solve: T throughout, or
+// (DF) level 1 of the mixed solve (v and w double-float pairs, x and vt FP32)
+template <typename T, bool DF>
+static mk_status op_interp_comb_t(Hierarchy &H, int l, const double *dv, double sigma,
+                                  const double *dvt, int nvt, const double *y, double *dx,
+                                  double *dw, cudaStream_t s) {
+    using Tv = typename std::conditional<DF, float2, T>::type;
+    Level &L = *H.lv[l];
+    Level &C = *H.lv[l + 1];
+    DevMem vp, cp, xp, wp, sg, yd;
+    CK(vp.alloc(sizeof(Tv) * L.g.len));
+    CK(cp.alloc(sizeof(T) * C.g.len * nvt));
+    CK(xp.alloc(sizeof(T) * L.g.len));
+    CK(wp.alloc(sizeof(Tv) * L.g.len));
+    CK(sg.alloc(sizeof(double)));
+    CK(cudaMemcpyAsync(sg.p, &sigma, sizeof(double), cudaMemcpyHostToDevice, s));
+    if (y) {
+        CK(yd.alloc(sizeof(double) * nvt));
+        CK(cudaMemcpyAsync(yd.p, y, sizeof(double) * nvt, cudaMemcpyHostToDevice, s));
+    }
+    const double *ydev = y ? yd.as<double>() : nullptr;
+    launch_pack<double, Tv>(L.g, dv, vp.as<Tv>(), s);
+    for (int m = 0; m < nvt; ++m)
+        launch_pack<double, T>(C.g, dvt + (size_t)m * level_n(C), cp.as<T>() + (int64_t)m * C.g.len, s);
+    if constexpr (DF) {
+        const int64_t nc = 3 * (int64_t)L.g.nx + (L.g.dim == 2 ? 3 * (int64_t)L.g.ny : 0);
+        const float2 *ca = L.cdf.as<float2>();
+        launch_interp_df(L.g, C.g, L.nu, L.space, ca, ca + nc, L.w.b != 0.0, vp.as<float2>(),
+                         sg.as<double>(), cp.as<float>(), nvt, C.g.len, ydev, xp.as<float>(),
+                         wp.as<float2>(), nullptr, s, L.cuni.p ? L.cuni.as<float2>() : nullptr,
+                         L.cuni_square);
+    } else {
+        launch_interp<T, T, T, T, T>(L.g, C.g, L.nu, L.space, L.w, op_of<T>(L), vp.as<T>(),
+                                     sg.as<double>(), cp.as<T>(), nvt, C.g.len, ydev, xp.as<T>(),
+                                     wp.as<T>(), nullptr, s);
+    }
+    launch_unpack<T, double>(L.g, xp.as<T>(), dx, s);
+    launch_unpack<Tv, double>(L.g, wp.as<Tv>(), dw, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return MK_OK;
+}
+
+extern "C" {
+
+mk_status mk_op_interp_combine(mk_problem *p, const mk_solve_opts *opts, int32_t level,
+                               int32_t precision, const double *v, double sigma,
+                               const double *vt, int32_t nvt, const double *y, double *x,
+                               double *w, void *stream) {
+    if (!v || !vt || !x || !w || precision < 0 || precision > 2) return MK_ERR_INVALID;
+    if (nvt < 1 || nvt > MK_MAX_INNER || (!y && nvt != 1)) return MK_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Hierarchy *H = nullptr;
+    mk_solve_opts o;
+    CKS(get_level(p, opts, level, H, o));
+    if (o.transfer != MK_TRANSFER_MK) return MK_ERR_INVALID;
+    if (level >= (int)H->lv.size()) return MK_ERR_INVALID;
+    if (precision == 2 && (level != 1 || o.precision != 1)) return MK_ERR_INVALID;
+    Level &L = *H->lv[level - 1];
+    Level &C = *H->lv[level];
+    DevMem t1, t2;
+    const double *dv = nullptr, *dvt = nullptr;
+    CKS(stage_in(v, level_n(L), t1, dv, s));
+    CKS(stage_in(vt, level_n(C) * (size_t)nvt, t2, dvt, s));
+    OutStage ox, ow;
+    CKS(stage_out(x, level_n(L), ox));
+    CKS(stage_out(w, level_n(L), ow));
+    if (precision == 0)
+        CKS((op_interp_comb_t<double, false>(*H, level - 1, dv, sigma, dvt, nvt, y, ox.dev, ow.dev, s)));
+    else if (precision == 1)
+        CKS((op_interp_comb_t<float, false>(*H, level - 1, dv, sigma, dvt, nvt, y, ox.dev, ow.dev, s)));
+    else
+        CKS((op_interp_comb_t<float, true>(*H, level - 1, dv, sigma, dvt, nvt, y, ox.dev, ow.dev, s)));
+    CKS(finish_out(ox, s));
+    return finish_out(ow, s);
+}
+
+}  // extern "C"
+
 template <typename T>
 static mk_status op_coarsest_t(Hierarchy &H, const double *dr, double *dx, cudaStream_t s) {
     Level &C = *H.lv.back();

@@ -86,36 +86,6 @@ void launch_residual_df(const Geom &g, const Weights &w, SpaceOp<double> L, cons
 //   (FP32) combined with yc on the fly.  The spatial operator enters as per-index
 //   double-float coefficients a*L and b*L: aL = [lo|di|up] (x) then (y).
 // ---------------------------------------------------------------------------------------
-template <int DIM, bool SPACE>
-struct XEvalDF {
-    const float2 *v;
-    float sigma;
-    const float *Xc;
-    int mc;
-    int64_t xc_stride;
-    float y[MK_MAX_INNER];
-    Geom gf, gc;
-    int nu;
-
-    __device__ __forceinline__ float operator()(int k, int j, int i) const {
-        if (i < 0 || i >= gf.nx || j < 0 || j >= gf.ny) return 0.f;
-        int K = (k == 0) ? 0 : (k - 1) / nu + 1;
-        int I = SPACE ? (i >> 1) : i;
-        int J = (SPACE && DIM == 2) ? (j >> 1) : j;
-        int64_t cidx = gc.at(K, J, I);
-        float zt;
-        if (mc == 0) {
-            zt = Xc[cidx];
-        } else {
-            zt = 0.f;
-#pragma unroll
-            for (int m = 0; m < MK_MAX_INNER; ++m)
-                if (m < mc) zt += y[m] * Xc[cidx + m * xc_stride];
-        }
-        return sigma * v[gf.at(k, j, i)].x - zt;
-    }
-};
-
 template <int DIM>
 __device__ __forceinline__ df lap_df(const float2 *__restrict__ cx, const float2 *__restrict__ cy,
                                      int nx, int ny, int i, int j, float c, float l, float r,
@@ -227,73 +197,6 @@ __global__ void __launch_bounds__(256) k_apply_df_2d_sq(Geom g, const float2 *__
     w[idx] = df_pack(r);
 }
 
-template <int DIM, bool SPACE>
-__global__ void __launch_bounds__(256) k_interp_df(Geom gf, Geom gc, int nu,
-                                                   const float2 *__restrict__ ca,
-                                                   const float2 *__restrict__ cb, int has_b,
-                                                   const float2 *__restrict__ v,
-                                                   const double *__restrict__ sigma,
-                                                   const float *__restrict__ Xc, int mc,
-                                                   int64_t xc_stride,
-                                                   const double *__restrict__ yc,
-                                                   float *__restrict__ xout,
-                                                   float2 *__restrict__ wout, int kc,
-                                                   const int *__restrict__ done) {
-    if (done && *done) return;
-    int i, j, chunk;
-    point_index<DIM>(i, j, chunk);
-    if (i >= gf.nx || j >= gf.ny) return;
-    XEvalDF<DIM, SPACE> X;
-    X.v = v;
-    X.sigma = sigma ? (float)(*sigma) : 1.f;
-    X.Xc = Xc;
-    X.mc = yc ? mc : 0;
-    X.xc_stride = xc_stride;
-    for (int m = 0; m < MK_MAX_INNER; ++m) X.y[m] = (yc && m < mc) ? (float)yc[m] : 0.f;
-    X.gf = gf;
-    X.gc = gc;
-    X.nu = nu;
-    // coefficient rows: a*L in ca, b*L in cb; x block first (3 nx), then y (3 ny)
-    const float2 *cax = ca, *cay = ca + 3 * gf.nx;
-    const float2 *cbx = cb, *cby = cb + 3 * gf.nx;
-    int k0 = chunk * kc;
-    int k1 = min(k0 + kc, gf.nt + 1);
-    float prev = 0.f;
-    df bLprev = {0.f, 0.f};
-    auto eval = [&](int k, float &c, df &aL, df &bL) {
-        c = X(k, j, i);
-        float l = X(k, j, i - 1), r = X(k, j, i + 1);
-        float d = 0.f, u = 0.f;
-        if (DIM == 2) {
-            d = X(k, j - 1, i);
-            u = X(k, j + 1, i);
-        }
-        aL = lap_df<DIM>(cax, cay, gf.nx, gf.ny, i, j, c, l, r, d, u);
-        bL = has_b ? lap_df<DIM>(cbx, cby, gf.nx, gf.ny, i, j, c, l, r, d, u) : df{0.f, 0.f};
-    };
-    if (k0 > 0) {
-        df aL;
-        eval(k0 - 1, prev, aL, bLprev);
-    }
-    for (int k = k0; k < k1; ++k) {
-        float c;
-        df aL, bL;
-        eval(k, c, aL, bL);
-        df w;
-        if (k == 0) {
-            w = df_from_float(c);
-        } else {
-            // (x_k - a L x_k) - (x_{k-1} + b L x_{k-1})
-            w = df_sub(df_sub(df_from_sum(c, -prev), aL), bLprev);
-        }
-        int64_t idx = gf.at(k, j, i);
-        xout[idx] = c;
-        wout[idx] = df_pack(w);
-        prev = c;
-        bLprev = bL;
-    }
-}
-
 // 1D specialisation: x once per point, neighbours from the adjacent lanes, the point's
 // double-float coefficients held in registers, row pointers and the coarse block index
 // advanced once per step, the coarse combination specialised on its size MC (see the FP32
@@ -334,16 +237,16 @@ __global__ void __launch_bounds__(256) k_interp_df_1d(Geom gf, Geom gc, int nu,
         if (MC == 0) {
             zt = zp[0];
         } else if (MC == 1) {
-            zt = y[0] * zp[0];
+            zt = mul_rn(y[0], zp[0]);
         } else if (MC == 2) {
-            zt = y[0] * zp[0] + y[NY > 1 ? 1 : 0] * zp[xc_stride];
+            zt = fma_rn(y[NY > 1 ? 1 : 0], zp[xc_stride], mul_rn(y[0], zp[0]));
         } else {
             zt = 0.f;
 #pragma unroll
             for (int m = 0; m < NY; ++m)
-                if (m < mc) zt += y[m] * zp[m * xc_stride];
+                if (m < mc) zt = fma_rn(y[m], zp[m * xc_stride], zt);
         }
-        return sig * vr[ii].x - zt;
+        return fma_rn(sig, vr[ii].x, -zt);
     };
     const int k0 = blockIdx.y * kc;
     const int k1 = min(k0 + kc, gf.nt + 1);
@@ -465,9 +368,9 @@ __global__ void __launch_bounds__(256, 2) k_interp_df_2d_ts(Geom gf, Geom gc, in
     // (Z vt) from the raw coarse values
     auto comb = [&](const float (&zr)[NZ]) -> float {
         if (MC == 0) return zr[0];
-        float z = ym[0] * zr[0];
+        float z = mul_rn(ym[0], zr[0]);
 #pragma unroll
-        for (int m = 1; m < NZ; ++m) z = fmaf(ym[m], zr[m], z);
+        for (int m = 1; m < NZ; ++m) z = fma_rn(ym[m], zr[m], z);
         return z;
     };
     const int k0 = blockIdx.z * kc;
@@ -494,16 +397,16 @@ __global__ void __launch_bounds__(256, 2) k_interp_df_2d_ts(Geom gf, Geom gc, in
             }
             load(k + 1, K);
         }
-        const float x00 = c0 ? sig * a0.x - zo : 0.f;
-        const float x01 = c1 ? sig * a0.z - zo : 0.f;
-        const float x10 = (c0 && r1) ? sig * a1.x - zo : 0.f;
-        const float x11 = (c1 && r1) ? sig * a1.z - zo : 0.f;
-        const float d0 = hd ? sig * qd.x - zd : 0.f, d1 = (hd && c1) ? sig * qd.z - zd : 0.f;
-        const float e0 = hu ? sig * qu.x - zu : 0.f, e1 = (hu && c1) ? sig * qu.z - zu : 0.f;
+        const float x00 = c0 ? fma_rn(sig, a0.x, -zo) : 0.f;
+        const float x01 = c1 ? fma_rn(sig, a0.z, -zo) : 0.f;
+        const float x10 = (c0 && r1) ? fma_rn(sig, a1.x, -zo) : 0.f;
+        const float x11 = (c1 && r1) ? fma_rn(sig, a1.z, -zo) : 0.f;
+        const float d0 = hd ? fma_rn(sig, qd.x, -zd) : 0.f, d1 = (hd && c1) ? fma_rn(sig, qd.z, -zd) : 0.f;
+        const float e0 = hu ? fma_rn(sig, qu.x, -zu) : 0.f, e1 = (hu && c1) ? fma_rn(sig, qu.z, -zu) : 0.f;
         float l0 = __shfl_up_sync(FULL, x01, 1), l1 = __shfl_up_sync(FULL, x11, 1);
         float q0 = __shfl_down_sync(FULL, x00, 1), q1 = __shfl_down_sync(FULL, x10, 1);
-        const float xe0 = (cl || cr) ? sig * ve0 - ze : 0.f;
-        const float xe1 = ((cl || cr) && r1) ? sig * ve1 - ze : 0.f;
+        const float xe0 = (cl || cr) ? fma_rn(sig, ve0, -ze) : 0.f;
+        const float xe1 = ((cl || cr) && r1) ? fma_rn(sig, ve1, -ze) : 0.f;
         if (lane == 0) {
             l0 = xe0;
             l1 = xe1;
@@ -569,9 +472,6 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
     int nch = (gf.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(gf.dim, gf.nx, gf.ny, nch);
     const int hb = has_b ? 1 : 0;
-#define MK_IDF(D, S)                                                                          \
-    k_interp_df<D, S><<<l.grid, l.block, 0, s>>>(gf, gc, nu, ca, cb, hb, v, sigma, Xc, mc,    \
-                                                 xc_stride, yc, x, wout, kc, done)
 #define MK_IDF1M(S, M)                                                                        \
     k_interp_df_1d<S, M><<<l.grid, l.block, 0, s>>>(gf, gc, nu, ca, cb, hb, v, sigma, Xc, mc, \
                                                     xc_stride, yc, x, wout, kc, done)
@@ -637,7 +537,6 @@ void launch_interp_df(const Geom &gf, const Geom &gc, int nu, bool space, const 
         else k_apply_df_2d<<<g2, b2, 0, s>>>(gf, ca, cb, hb, x, wout, done);
         count_launch();
     }
-#undef MK_IDF
 #undef MK_IDF1
 #undef MK_IDF1M
     prof_end(s, PROF_INTERP, (double)gf.interior() * (8.0 + 4.0 + 8.0) + (double)mc * gc.interior() * 4.0);

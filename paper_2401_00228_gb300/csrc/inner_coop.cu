@@ -25,6 +25,7 @@
 
 #include "kernels.h"
 #include "reduce.cuh"
+#include "rounding.cuh"
 #include "dst_fft.cuh"
 #include "scan.cuh"
 #include "krylov_epilogue.cuh"
@@ -190,9 +191,9 @@ __device__ __forceinline__ void zrow(const Geom &gc, const float *Xc, int mc, in
         float t[4], tl, tr;
         row4(gc, Xc + (int64_t)m * xcs, K, i0, t, tl, tr);
 #pragma unroll
-        for (int p = 0; p < 4; ++p) z[p] = (m == 0) ? ym * t[p] : z[p] + ym * t[p];
-        zl = (m == 0) ? ym * tl : zl + ym * tl;
-        zr = (m == 0) ? ym * tr : zr + ym * tr;
+        for (int p = 0; p < 4; ++p) z[p] = (m == 0) ? mul_rn(ym, t[p]) : fma_rn(ym, t[p], z[p]);
+        zl = (m == 0) ? mul_rn(ym, tl) : fma_rn(ym, tl, zl);
+        zr = (m == 0) ? mul_rn(ym, tr) : fma_rn(ym, tr, zr);
     }
 }
 
@@ -203,9 +204,9 @@ __device__ __forceinline__ void xfrom(const Geom &gf, const float *v, float sig,
     float c[4], l, r;
     row4(gf, v, k, i0, c, l, r);
 #pragma unroll
-    for (int p = 0; p < 4; ++p) x[p] = (i0 + p < nf) ? sig * c[p] - z[p] : 0.f;
-    xl = (i0 > 0) ? sig * l - zl : 0.f;
-    xr = (i0 + 4 < nf) ? sig * r - zr : 0.f;
+    for (int p = 0; p < 4; ++p) x[p] = (i0 + p < nf) ? fma_rn(sig, c[p], -z[p]) : 0.f;
+    xl = (i0 > 0) ? fma_rn(sig, l, -zl) : 0.f;
+    xr = (i0 + 4 < nf) ? fma_rn(sig, r, -zr) : 0.f;
 }
 
 __device__ __noinline__ void interp_phase(const CoopLevel &F, const Geom &gc, const float *v, float sig,

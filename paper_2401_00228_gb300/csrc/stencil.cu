@@ -613,9 +613,9 @@ struct XEval {
             zt = (Tx)0;
 #pragma unroll
             for (int m = 0; m < MK_MAX_INNER; ++m)
-                if (m < mc) zt += y[m] * (Tx)Xc[cidx + m * xc_stride];
+                if (m < mc) zt = fma_rn(y[m], (Tx)Xc[cidx + m * xc_stride], zt);
         }
-        return sigma * (Tx)v[gf.at(k, j, i)] - zt;
+        return fma_rn(sigma, (Tx)v[gf.at(k, j, i)], -zt);
     }
 };
 
@@ -707,16 +707,16 @@ __global__ void __launch_bounds__(256) k_interp_1d(Geom gf, Geom gc, int nu, Tc 
         if (MC == 0) {
             zt = (Tx)zp[0];
         } else if (MC == 1) {
-            zt = y[0] * (Tx)zp[0];
+            zt = mul_rn(y[0], (Tx)zp[0]);
         } else if (MC == 2) {
-            zt = y[0] * (Tx)zp[0] + y[NY > 1 ? 1 : 0] * (Tx)zp[xc_stride];
+            zt = fma_rn(y[NY > 1 ? 1 : 0], (Tx)zp[xc_stride], mul_rn(y[0], (Tx)zp[0]));
         } else {
             zt = (Tx)0;
 #pragma unroll
             for (int m = 0; m < NY; ++m)
-                if (m < mc) zt += y[m] * (Tx)zp[m * xc_stride];
+                if (m < mc) zt = fma_rn(y[m], (Tx)zp[m * xc_stride], zt);
         }
-        return sig * ldv<Tx>(vr, ii) - zt;
+        return fma_rn(sig, ldv<Tx>(vr, ii), -zt);
     };
     const int k0 = blockIdx.y * kc;
     const int k1 = min(k0 + kc, gf.nt + 1);

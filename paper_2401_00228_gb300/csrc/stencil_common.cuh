@@ -2,6 +2,7 @@
 #pragma once
 
 #include "kernels.h"
+#include "rounding.cuh"
 
 namespace mk {
 
@@ -183,10 +184,10 @@ __global__ void __launch_bounds__(256) k_interp_x2d(Geom gf, Geom gc, int nu,
             if (!yc) {
                 zt = (Tx)crow[I];
             } else {
-                for (int m = 0; m < nm; ++m) zt += s_w[1 + m] * (Tx)crow[I + m * xc_stride];
+                for (int m = 0; m < nm; ++m) zt = fma_rn(s_w[1 + m], (Tx)crow[I + m * xc_stride], zt);
             }
         }
-        out[p] = (i < gf.nx) ? sig * vin[p] - zt : (Tx)0;
+        out[p] = (i < gf.nx) ? fma_rn(sig, vin[p], -zt) : (Tx)0;
     }
     x2d_store4<Tx>(x + idx, out);
 }

@@ -246,9 +246,9 @@ struct CoarseRows {
                 if constexpr (PC == 4) ld4(cm + I0, t);
                 else ld2(cm + I0, t);
 #pragma unroll
-                for (int p = 0; p < PC; ++p) z[rc][p] = (m == 0) ? ym * t[p] : z[rc][p] + ym * t[p];
-                if (wl) zl[rc] = (m == 0) ? ym * ld1<Tx>(cm + Il) : zl[rc] + ym * ld1<Tx>(cm + Il);
-                if (wr) zr[rc] = (m == 0) ? ym * ld1<Tx>(cm + Ir) : zr[rc] + ym * ld1<Tx>(cm + Ir);
+                for (int p = 0; p < PC; ++p) z[rc][p] = (m == 0) ? mul_rn(ym, t[p]) : fma_rn(ym, t[p], z[rc][p]);
+                if (wl) zl[rc] = (m == 0) ? mul_rn(ym, ld1<Tx>(cm + Il)) : fma_rn(ym, ld1<Tx>(cm + Il), zl[rc]);
+                if (wr) zr[rc] = (m == 0) ? mul_rn(ym, ld1<Tx>(cm + Ir)) : fma_rn(ym, ld1<Tx>(cm + Ir), zr[rc]);
             }
         }
     }
@@ -310,10 +310,10 @@ __global__ void __launch_bounds__(TT) k_interp_1d_t(Geom gf, Geom gc, Tc a, Tc b
         Tx x[PT];
 #pragma unroll
         for (int p = 0; p < PT; ++p)
-            x[p] = (ok && i0 + p < nf) ? sig * vv[r][p] - cr.z[r / 2][SPACE ? p / 2 : p] : (Tx)0;
+            x[p] = (ok && i0 + p < nf) ? fma_rn(sig, vv[r][p], -cr.z[r / 2][SPACE ? p / 2 : p]) : (Tx)0;
         Tx xl = __shfl_up_sync(FULL, x[PT - 1], 1), xr = __shfl_down_sync(FULL, x[0], 1);
-        if (lane == 0) xl = (ok && i0 > 0) ? sig * vl[r] - cr.zl[r / 2] : (Tx)0;
-        if (lane == 31) xr = (ok && i0 + PT < nf) ? sig * vr[r] - cr.zr[r / 2] : (Tx)0;
+        if (lane == 0) xl = (ok && i0 > 0) ? fma_rn(sig, vl[r], -cr.zl[r / 2]) : (Tx)0;
+        if (lane == 31) xr = (ok && i0 + PT < nf) ? fma_rn(sig, vr[r], -cr.zr[r / 2]) : (Tx)0;
         Tc xc[PT], lx[PT];
 #pragma unroll
         for (int p = 0; p < PT; ++p) xc[p] = (Tc)x[p];
@@ -420,10 +420,10 @@ __global__ void __launch_bounds__(TT) k_interp_df_1d_t(Geom gf, Geom gc,
         float x[PT];
 #pragma unroll
         for (int p = 0; p < PT; ++p)
-            x[p] = (ok && i0 + p < nf) ? sig * vv[r][p] - cr.z[r / 2][SPACE ? p / 2 : p] : 0.f;
+            x[p] = (ok && i0 + p < nf) ? fma_rn(sig, vv[r][p], -cr.z[r / 2][SPACE ? p / 2 : p]) : 0.f;
         float xl = __shfl_up_sync(FULL, x[PT - 1], 1), xr = __shfl_down_sync(FULL, x[0], 1);
-        if (lane == 0) xl = (ok && i0 > 0) ? sig * vl[r] - cr.zl[r / 2] : 0.f;
-        if (lane == 31) xr = (ok && i0 + PT < nf) ? sig * vr[r] - cr.zr[r / 2] : 0.f;
+        if (lane == 0) xl = (ok && i0 > 0) ? fma_rn(sig, vl[r], -cr.zl[r / 2]) : 0.f;
+        if (lane == 31) xr = (ok && i0 + PT < nf) ? fma_rn(sig, vr[r], -cr.zr[r / 2]) : 0.f;
         df aL[PT], bL[PT];
 #pragma unroll
         for (int p = 0; p < PT; ++p) {
