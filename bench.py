@@ -590,7 +590,7 @@ def main():
     ap.add_argument("--tune-trials", type=int, default=48,
                     help="trial solves of the schedule autotuner on the headline workload")
     ap.add_argument("--tune-trials-fp64", type=int, default=8)
-    ap.add_argument("--tune-trials-2d", type=int, default=28)
+    ap.add_argument("--tune-trials-2d", type=int, default=56)
     ap.add_argument("--tune-trials-batch", type=int, default=6,
                     help="trial solves per member of the batch")
     ap.add_argument("--no-autotune", action="store_true",

@@ -293,7 +293,10 @@ mk_status mk_problem_shape(const mk_problem *p, int32_t *dim, int32_t *nx, int32
      - restart (Algorithm 2) in {8, 12, 16, 24, 32, 40, 64} (with MK_TUNE_RESTART_CAP only
        those up to base->restart: the level-1 basis grows with it);
    keeping at each step the fastest candidate that converges within base->max_iters (others,
-   and candidates the library rejects, are skipped).  At most max_trials solves (0: no limit).
+   and candidates the library rejects, are skipped).  Each candidate first runs one restart
+   cycle (max_iters 1), which builds its hierarchy, tunes its tiles and captures its graph, so
+   that the timed solves that follow measure the iterations alone.  At most max_trials timed
+   solves (0: no limit; the one-cycle runs are not counted).
    *best receives the chosen options (tile autotuning on); info (may be NULL) the number of
    solves, the best solve's time and iterations and the wall time of the tuning.  Allocates
    one solution buffer for the trials and frees it, and frees the workspace of the last trial
@@ -303,7 +306,7 @@ mk_status mk_problem_shape(const mk_problem *p, int32_t *dim, int32_t *nx, int32
 #define MK_TUNE_LEVELS 1
 #define MK_TUNE_RESTART_CAP 2   /* restart candidates only up to base->restart (bounds memory) */
 typedef struct mk_tune_info {
-    int32_t trials;           /* solves run */
+    int32_t trials;           /* timed solves run */
     int32_t best_iterations;  /* outer iterations of the chosen options */
     double best_ms;           /* device time of the chosen options' solve */
     double tune_ms;           /* wall time of the whole tuning */

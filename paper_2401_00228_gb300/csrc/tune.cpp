@@ -9,9 +9,11 @@
 // the library rejects (MK_ERR_INVALID: a slab count that does not divide the coarsest
 // level, too few steps for another level), is skipped.  The search: the level count
 // (optional), then up to two passes of coordinate descent over the inner iteration counts
-// (deepest level first), N_CGS and the restart length.  A candidate whose first solve is within 30% of the best so far is
-// solved once more and keeps the faster time (the first solve of new options also builds
-// their hierarchy, autotunes its tiles and captures its graph, all inside solve_ms).
+// (deepest level first), N_CGS and the restart length.  Each candidate first runs one
+// restart cycle (max_iters 1): the first solve of new options builds their hierarchy,
+// autotunes its tiles and captures its graph, all of which would otherwise fall inside
+// solve_ms.  The timed solve follows; one within 30% of the best so far is solved once more
+// and keeps the faster time.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -40,6 +42,16 @@ struct Tuner {
     double trial(const mk_solve_opts &o) {
         if (hard != MK_OK || (max_trials > 0 && trials >= max_trials)) return -1.0;
         mk_solve_info info;
+        {
+            mk_solve_opts w = o;
+            w.max_iters = 1;
+            const mk_status sw = mk_solve(p, u0, &w, u, &info, stream);
+            if (sw == MK_ERR_INVALID || sw == MK_ERR_NONFINITE) return -1.0;
+            if (sw != MK_OK && sw != MK_ERR_NOT_CONVERGED) {
+                hard = sw;
+                return -1.0;
+            }
+        }
         ++trials;
         mk_status st = mk_solve(p, u0, &o, u, &info, stream);
         if (st == MK_ERR_INVALID || st == MK_ERR_NOT_CONVERGED || st == MK_ERR_NONFINITE) return -1.0;

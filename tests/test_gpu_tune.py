@@ -30,8 +30,10 @@ def test_tune_picks_converging_options(levels_flag):
         i2 = mk.mk_solve(p.handle, P.u0, u, best)
     assert i2.rel_residual < 1e-9
     assert O.max_rel_error(u, ref) <= 1e-8
-    # the re-solve rebuilds the hierarchy and re-times its tiles: rounding-level differences
-    assert abs(info.best_iterations - i2.iterations) <= 2
+    # the re-solve rebuilds the hierarchy and re-times its tiles; a different tile choice sums
+    # in another order, and FGMRES at this tolerance moves by a few iterations with the
+    # rounding (5% of the count, at least 2)
+    assert abs(info.best_iterations - i2.iterations) <= max(2, 0.05 * i2.iterations)
     # the starting point is a candidate, so the pick is not slower than it (same device, up
     # to timing noise; its first solve also built the hierarchy)
     assert info.best_ms <= 1.5 * b_info.solve_ms
