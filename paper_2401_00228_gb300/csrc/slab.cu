@@ -392,9 +392,11 @@ constexpr int FDM_THREADS = 256;
 constexpr int FDM_SHORT_SLAB = 32;   // longer slabs (and the coupled march) take the blocked scan
 
 template <typename T>
-__device__ __forceinline__ void fdm_product(const T *__restrict__ Mleft, const T *__restrict__ Mright_t,
+__device__ __forceinline__ void fdm_product(const T *__restrict__ Mleft, const T *__restrict__ MrT,
                                             T *__restrict__ A, T *__restrict__ B, int nx, int ny) {
-    // B = Mleft A (ny x ny times ny x nx), then A = B Mright_t^T (Mright_t is nx x nx, row-major)
+    // B = Mleft A (ny x ny times ny x nx), then A = B Mright^T with MrT[q][i] = Mright^T[q][i]
+    // = Mright[i][q] (Mright nx x nx, kept transposed so that lanes of consecutive i read
+    // consecutive words: no bank conflicts)
     const int nxy = nx * ny;
     for (int e = threadIdx.x; e < nxy; e += FDM_THREADS) {
         const int j = e / nx, i = e - j * nx;
@@ -406,7 +408,7 @@ __device__ __forceinline__ void fdm_product(const T *__restrict__ Mleft, const T
     for (int e = threadIdx.x; e < nxy; e += FDM_THREADS) {
         const int j = e / nx, i = e - j * nx;
         T acc = 0;
-        for (int q = 0; q < nx; ++q) acc += B[j * nx + q] * Mright_t[i * nx + q];
+        for (int q = 0; q < nx; ++q) acc += B[j * nx + q] * MrT[q * nx + i];
         A[e] = acc;
     }
     __syncthreads();
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(FDM_THREADS) k_fdm_forward(Geom g, const T *__
     T *A = Syi + ny * ny;
     T *B = A + nxy;
     const int k = k0 + blockIdx.x;
-    for (int e = threadIdx.x; e < nx * nx; e += FDM_THREADS) Sxi[e] = Sxi_g[e];
+    for (int e = threadIdx.x; e < nx * nx; e += FDM_THREADS) Sxi[e] = Sxi_g[(e % nx) * nx + e / nx];
     for (int e = threadIdx.x; e < ny * ny; e += FDM_THREADS) Syi[e] = Syi_g[e];
     for (int e = threadIdx.x; e < nxy; e += FDM_THREADS) {
         const int j = e / nx, i = e - j * nx;
@@ -486,7 +488,7 @@ __global__ void __launch_bounds__(FDM_THREADS) k_fdm_inverse(Geom g, const T *__
     T *Sy = Sx + nx * nx;
     T *A = Sy + ny * ny;
     T *B = A + nxy;
-    for (int e = threadIdx.x; e < nx * nx; e += FDM_THREADS) Sx[e] = Sx_g[e];
+    for (int e = threadIdx.x; e < nx * nx; e += FDM_THREADS) Sx[e] = Sx_g[(e % nx) * nx + e / nx];
     for (int e = threadIdx.x; e < ny * ny; e += FDM_THREADS) Sy[e] = Sy_g[e];
     const T *in = xh + (int64_t)k * nxy;
     for (int e = threadIdx.x; e < nxy; e += FDM_THREADS) A[e] = in[e];
@@ -625,8 +627,10 @@ __global__ void __launch_bounds__(1024) k_slab_2d(Geom g, T a, T b, SpaceOp<T> L
     const T *ylo = L.y, *ydi = L.y + ny, *yup = L.y + 2 * ny;
 
     for (int e = tid; e < nx * nx; e += NT) {
-        Sx[e] = Sx_g[e];
-        Sxi[e] = Sxi_g[e];
+        // transposed ([q][i] = S[i][q]): the products below read consecutive words across lanes
+        const int et = (e % nx) * nx + e / nx;
+        Sx[e] = Sx_g[et];
+        Sxi[e] = Sxi_g[et];
     }
     for (int e = tid; e < ny * ny; e += NT) {
         Sy[e] = Sy_g[e];
@@ -676,7 +680,7 @@ __global__ void __launch_bounds__(1024) k_slab_2d(Geom g, T a, T b, SpaceOp<T> L
         for (int e = tid; e < nxy; e += NT) {
             int j = e / nx, i = e - j * nx;
             T acc = 0;
-            for (int q = 0; q < nx; ++q) acc += B[j * nx + q] * Sxi[i * nx + q];
+            for (int q = 0; q < nx; ++q) acc += B[j * nx + q] * Sxi[q * nx + i];
             A[e] = acc / ((T)1 - a * (lamy[j] + lamx[i]));
         }
         __syncthreads();
@@ -692,7 +696,7 @@ __global__ void __launch_bounds__(1024) k_slab_2d(Geom g, T a, T b, SpaceOp<T> L
         for (int e = tid; e < nxy; e += NT) {
             int j = e / nx, i = e - j * nx;
             T acc = 0;
-            for (int q = 0; q < nx; ++q) acc += B[j * nx + q] * Sx[i * nx + q];
+            for (int q = 0; q < nx; ++q) acc += B[j * nx + q] * Sx[q * nx + i];
             x[g.at(k, j, i)] = acc;
             xp[(j + 1) * fx + i + 1] = acc;
         }
