@@ -88,7 +88,12 @@ typedef struct mk_solve_opts {
     double mu_value;
     int32_t precision;   /* 0: FP64 throughout.  1: mixed -- MK cycle, transfers, inner levels and
                             coarsest slabs in FP32; level-1 residual, Arnoldi, least squares and the
-                            true-residual check in FP64. */
+                            true-residual check in FP64 (the level-1 basis as double-float pairs).
+                            2: mixed with an FP32 level-1 basis -- as 1, but the level-1 Arnoldi
+                            vectors are FP32 (dot products summed in FP32 within a tile, in FP64
+                            across tiles): half the level-1 basis traffic and memory.  The true
+                            residual of every restart stays FP64, so each restart cycle refines
+                            the FP64 iterate and the tolerance is met in FP64 as in mode 1. */
     int32_t use_graph;   /* 1: capture each restart cycle in a CUDA graph (default 1) */
     int32_t orth;        /* level-1 Arnoldi: 0 = one classical Gram-Schmidt pass; 1 = a second
                             pass when the norm drops below 1/sqrt(2) of its value (default);

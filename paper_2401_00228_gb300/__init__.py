@@ -80,7 +80,8 @@ def make_opts(levels: int = 3, nu: Sequence[int] = (), space: Sequence[bool] = (
     two-level method of Eqs. (mgritY), (mgritZ) with the coarse matrix of Eq. (coarsemat)).
     inner: "auto", "separate" (one launch per step of the inner levels) or "coop" (the inner
     recursion in one cooperative kernel).  augment: k recycled corrections per restart cycle
-    (0: plain FGMRES(m))."""
+    (0: plain FGMRES(m)).  precision: "fp64", "mixed" (FP32 cycle, double-float level-1 basis)
+    or "mixed32" (FP32 cycle and FP32 level-1 basis; FP64 true residual at every restart)."""
     o = mk_default_opts()
     o.levels = levels
     for i, v in enumerate(nu):
@@ -93,7 +94,7 @@ def make_opts(levels: int = 3, nu: Sequence[int] = (), space: Sequence[bool] = (
     o.tol = tol
     o.restart = restart
     o.max_iters = max_iters
-    o.precision = {"fp64": 0, "mixed": 1}[precision]
+    o.precision = {"fp64": 0, "mixed": 1, "mixed32": 2}[precision]
     if mu == "lambda_max":
         o.mu_mode = 0
     elif mu == "one":

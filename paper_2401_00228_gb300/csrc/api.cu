@@ -932,7 +932,7 @@ mk_status mk_op_precond(mk_problem *p, const mk_solve_opts *opts, int32_t level,
     // v -> basis slot 0 of level l with sigma_0 = 1; flags cleared (not done)
     const bool l0 = level == 1;
     if (H->precision == 0) launch_pack<double, double>(L.g, dv, L.V.as<double>(), s);
-    else if (l0) launch_pack<double, float2>(L.g, dv, L.V.as<float2>(), s);   // double-float basis
+    else if (l0 && H->precision == 1) launch_pack<double, float2>(L.g, dv, L.V.as<float2>(), s);   // double-float basis
     else launch_pack<double, float>(L.g, dv, L.V.as<float>(), s);
     double one = 1.0;
     CK(cudaMemcpyAsync(L.ks.sigma(), &one, sizeof(double), cudaMemcpyHostToDevice, s));

@@ -30,13 +30,17 @@ __device__ __forceinline__ df warp_sum_df(df v) {
 }
 
 // ---------------------------------------------------------------------------------------
-// K2: r = f - A u in FP64; r stored as a double-float pair (the basis vector V_0)
+// K2: r = f - A u in FP64; r stored as a double-float pair (the basis vector V_0 of the mixed
+// solve) or rounded to FP32 (the FP32 level-1 basis)
 // ---------------------------------------------------------------------------------------
-template <int DIM>
+__device__ __forceinline__ void store_r(float2 *r, int64_t idx, double v) { r[idx] = df_pack(df_from_double(v)); }
+__device__ __forceinline__ void store_r(float *r, int64_t idx, double v) { r[idx] = (float)v; }
+
+template <int DIM, typename Tr>
 __global__ void __launch_bounds__(256) k_residual_df(Geom g, double a, double b, SpaceOp<double> L,
                                                      const double *__restrict__ f,
                                                      const double *__restrict__ u,
-                                                     float2 *__restrict__ r, int kc,
+                                                     Tr *__restrict__ r, int kc,
                                                      ReduceScratch rs, int slot, KState ks, int epi) {
     int i, j, chunk;
     point_index<DIM>(i, j, chunk);
@@ -56,7 +60,7 @@ __global__ void __launch_bounds__(256) k_residual_df(Geom g, double a, double b,
             double Lc = lap_at<DIM, double>(u, idx, i, j, g, L.x, L.y);
             double Au = (k == 0) ? cur : (cur - a * Lc) - (prev + b * Lprev);
             double rv = f[idx] - Au;
-            r[idx] = df_pack(df_from_double(rv));
+            store_r(r, idx, rv);
             acc += rv * rv;
             prev = cur;
             Lprev = Lc;
@@ -65,19 +69,32 @@ __global__ void __launch_bounds__(256) k_residual_df(Geom g, double a, double b,
     block_partial_and_finish(acc, rs, slot, ks, epi);
 }
 
-void launch_residual_df(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
-                        const double *u, float2 *r, const ReduceScratch &rs, int slot, KState ks,
-                        int epi, cudaStream_t s) {
+template <typename Tr>
+static void launch_residual_t(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
+                              const double *u, Tr *r, const ReduceScratch &rs, int slot, KState ks,
+                              int epi, cudaStream_t s) {
     int kc = cap_kc(choose_kc(g.npts(), g.nt + 1), g.nt + 1, g.dim, g.nx, g.ny);
     int nch = (g.nt + 1 + kc - 1) / kc;
     Launch2 l = point_launch(g.dim, g.nx, g.ny, nch);
     prof_begin(s);
     if (g.dim == 1)
-        k_residual_df<1><<<l.grid, l.block, 0, s>>>(g, w.a, w.b, L, f, u, r, kc, rs, slot, ks, epi);
+        k_residual_df<1, Tr><<<l.grid, l.block, 0, s>>>(g, w.a, w.b, L, f, u, r, kc, rs, slot, ks, epi);
     else
-        k_residual_df<2><<<l.grid, l.block, 0, s>>>(g, w.a, w.b, L, f, u, r, kc, rs, slot, ks, epi);
-    prof_end(s, PROF_RESIDUAL, (double)g.interior() * 24.0);
+        k_residual_df<2, Tr><<<l.grid, l.block, 0, s>>>(g, w.a, w.b, L, f, u, r, kc, rs, slot, ks, epi);
+    prof_end(s, PROF_RESIDUAL, (double)g.interior() * (16.0 + sizeof(Tr)));
     count_launch();
+}
+
+void launch_residual_df(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
+                        const double *u, float2 *r, const ReduceScratch &rs, int slot, KState ks,
+                        int epi, cudaStream_t s) {
+    launch_residual_t<float2>(g, w, L, f, u, r, rs, slot, ks, epi, s);
+}
+
+void launch_residual_f32(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
+                         const double *u, float *r, const ReduceScratch &rs, int slot, KState ks,
+                         int epi, cudaStream_t s) {
+    launch_residual_t<float>(g, w, L, f, u, r, rs, slot, ks, epi, s);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -119,6 +119,10 @@ void launch_lsq(int j, double *H, double beta, double *gg, double *y, double *re
 void launch_residual_df(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
                         const double *u, float2 *r, const ReduceScratch &rs, int slot, KState ks,
                         int epi, cudaStream_t s);
+// the same with r rounded to FP32 (the FP32 level-1 basis)
+void launch_residual_f32(const Geom &g, const Weights &w, SpaceOp<double> L, const double *f,
+                        const double *u, float *r, const ReduceScratch &rs, int slot, KState ks,
+                        int epi, cudaStream_t s);
 // 2D coarsest slabs in the eigenbasis of Lx (+) Ly, all time rows at once (slab.cu): forward
 // transform of every row, per-mode recurrence over each slab, inverse transform.  rh: scratch of
 // (nt+1) nx ny values.  Three launches.

@@ -163,6 +163,135 @@ __global__ void __launch_bounds__(KR_THREADS) k_update(int64_t len, const TW *__
 }
 
 // ---------------------------------------------------------------------------------------
+// FP32 vectors with more than MK_MAX_INNER basis vectors (level 1 with the FP32 basis).
+// multidot: a tile is 16 consecutive elements per thread in four float4 loads (coalesced
+// across the block), two basis vectors per sweep with the W tile re-read from L1; sums in
+// FP32 per thread and warp, in FP64 across tiles and warps.  update: four consecutive
+// elements per thread and step (float4), the basis loop unrolled so that its loads overlap.
+// Vector lengths and strides are whole numbers of 4096-element tiles.
+// ---------------------------------------------------------------------------------------
+constexpr int F4_Q = 4;                            // float4 loads per thread per tile
+constexpr int F4_TILE = KR_THREADS * 4 * F4_Q;     // elements per block tile (4096)
+
+__global__ void __launch_bounds__(KR_THREADS) k_multidot_f4(int64_t len, const float *__restrict__ W,
+                                                            const float *__restrict__ V,
+                                                            int64_t vstride, int j,
+                                                            ReduceScratch rs, KState ks, int second,
+                                                            const int *__restrict__ done,
+                                                            int close_mode) {
+    if (done && *done) return;
+    if (second && !ks.flags[2]) return;
+    extern __shared__ double smem[];
+    const int nv = j + 1;
+    const int nslots = second ? nv : nv + 1;
+    double *acc = smem;                      // [nslots][KR_WARPS]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < nslots * KR_WARPS; t += KR_THREADS) acc[t] = 0.0;
+    __syncthreads();
+    const float4 *src = reinterpret_cast<const float4 *>(second ? V + (int64_t)(j + 1) * vstride : W);
+    const float4 *V4 = reinterpret_cast<const float4 *>(V);
+    const int64_t n4 = len / 4, vs4 = vstride / 4;
+    constexpr int T4 = F4_TILE / 4;          // float4 per block tile
+    for (int64_t base = (int64_t)blockIdx.x * T4 + threadIdx.x; base < n4;
+         base += (int64_t)gridDim.x * T4) {
+        if (!second) {
+            float sw = 0.f;
+#pragma unroll
+            for (int q = 0; q < F4_Q; ++q) {
+                const float4 w = src[base + q * KR_THREADS];
+                sw = fmaf(w.x, w.x, sw);
+                sw = fmaf(w.y, w.y, sw);
+                sw = fmaf(w.z, w.z, sw);
+                sw = fmaf(w.w, w.w, sw);
+            }
+            sw = warp_sum_t(sw);
+            if (lane == 0) acc[nv * KR_WARPS + warp] += (double)sw;
+        }
+        for (int i = 0; i < nv; i += 2) {
+            const bool pair = i + 1 < nv;
+            const float4 *va = V4 + (int64_t)i * vs4;
+            const float4 *vb = pair ? va + vs4 : va;
+            float sa = 0.f, sb = 0.f;
+#pragma unroll
+            for (int q = 0; q < F4_Q; ++q) {
+                const int64_t e = base + q * KR_THREADS;
+                const float4 w = src[e], x = va[e], y = vb[e];
+                sa = fmaf(w.x, x.x, sa);
+                sa = fmaf(w.y, x.y, sa);
+                sa = fmaf(w.z, x.z, sa);
+                sa = fmaf(w.w, x.w, sa);
+                sb = fmaf(w.x, y.x, sb);
+                sb = fmaf(w.y, y.y, sb);
+                sb = fmaf(w.z, y.z, sb);
+                sb = fmaf(w.w, y.w, sb);
+            }
+            sa = warp_sum_t(sa);
+            sb = warp_sum_t(sb);
+            if (lane == 0) {
+                acc[i * KR_WARPS + warp] += (double)sa;
+                if (pair) acc[(i + 1) * KR_WARPS + warp] += (double)sb;
+            }
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nslots; t += KR_THREADS) {
+        double sum = 0.0;
+        for (int w2 = 0; w2 < KR_WARPS; ++w2) sum += acc[t * KR_WARPS + w2];
+        rs.partials[(int64_t)t * rs.max_blocks + blockIdx.x] = sum;
+    }
+    if (last_block_ticket(rs.counter, (int)threadIdx.x < nslots)) {
+        double *res = smem;  // reuse
+        finish_slots(rs.partials, rs.max_blocks, nslots, gridDim.x, res);
+        multidot_epilogue(res, ks, j, nv, second);
+        if (close_mode && !second) close_iteration(res, ks, j, nv, close_mode);
+        if (threadIdx.x == 0) rs.counter[0] = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(KR_THREADS) k_update_f4(int64_t len, const float *__restrict__ W,
+                                                          float *__restrict__ V, int64_t vstride,
+                                                          int j, int write_next, ReduceScratch rs,
+                                                          KState ks, int mode, int second,
+                                                          const int *__restrict__ done) {
+    if (done && *done) return;
+    if (second && !ks.flags[2]) return;
+    __shared__ float c[MK_MAX_RESTART + 1];
+    const int nv = j + 1;
+    for (int i = threadIdx.x; i < nv; i += KR_THREADS) c[i] = (float)(ks.tmp()[i] * ks.sigma()[i]);
+    __syncthreads();
+    float4 *out = reinterpret_cast<float4 *>(V + (int64_t)(j + 1) * vstride);
+    const float4 *W4 = reinterpret_cast<const float4 *>(W);
+    const float4 *V4 = reinterpret_cast<const float4 *>(V);
+    const int64_t n4 = len / 4, vs4 = vstride / 4;
+    float acc = 0.f;
+    for (int64_t e = (int64_t)blockIdx.x * KR_THREADS + threadIdx.x; e < n4;
+         e += (int64_t)gridDim.x * KR_THREADS) {
+        float4 val = second ? out[e] : W4[e];
+#pragma unroll 4
+        for (int i = 0; i < nv; ++i) {
+            const float4 v = V4[(int64_t)i * vs4 + e];
+            const float ci = c[i];
+            val.x = fmaf(-ci, v.x, val.x);
+            val.y = fmaf(-ci, v.y, val.y);
+            val.z = fmaf(-ci, v.z, val.z);
+            val.w = fmaf(-ci, v.w, val.w);
+        }
+        if (write_next) out[e] = val;
+        acc = fmaf(val.x, val.x, acc);
+        acc = fmaf(val.y, val.y, acc);
+        acc = fmaf(val.z, val.z, acc);
+        acc = fmaf(val.w, val.w, acc);
+    }
+    double bs = block_sum((double)acc);
+    if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
+    if (last_block_ticket(rs.counter, threadIdx.x == 0)) {
+        double tot = sum_partials(rs.partials, gridDim.x);
+        update_epilogue_block(tot, ks, j, mode, second);
+        if (threadIdx.x == 0) rs.counter[0] = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Short-basis variants (j + 1 = NV <= MK_MAX_INNER vectors: every inner level, and the
 // first iterations of level 1 in FP64).  Each thread takes 8 consecutive elements per step
 // with 16-byte loads, and the vector count is a compile-time constant, so all NV + 1 loads
@@ -380,6 +509,15 @@ void launch_multidot(int64_t len, const TW *W, const TV *V, int64_t vstride, int
             return;
         }
     }
+    if constexpr (std::is_same<TW, float>::value && std::is_same<TV, float>::value) {
+        if (len % F4_TILE == 0 && vstride % F4_TILE == 0) {
+            k_multidot_f4<<<grid, KR_THREADS, shm, s>>>(len, W, V, vstride, j, rs, ks,
+                                                       second_pass ? 1 : 0, done, close_mode);
+            prof_end(s, PROF_MULTIDOT, (double)(j + 2) * alg_n * sizeof(TV));
+            count_launch();
+            return;
+        }
+    }
     k_multidot<TW, TV><<<grid, KR_THREADS, shm, s>>>(len, W, V, vstride, j, rs, ks,
                                                       second_pass ? 1 : 0, done, close_mode);
     prof_end(s, PROF_MULTIDOT, (double)(j + 2) * alg_n * sizeof(TV));
@@ -406,6 +544,15 @@ void launch_update(int64_t len, const TW *W, TV *V, int64_t vstride, int j, bool
                 MK_UP(1) MK_UP(2) MK_UP(3) MK_UP(4) MK_UP(5) MK_UP(6) MK_UP(7) MK_UP(8)
 #undef MK_UP
             }
+            prof_end(s, PROF_UPDATE, (double)(j + 2 + (write_next ? 1 : 0)) * alg_n * sizeof(TV));
+            count_launch();
+            return;
+        }
+    }
+    if constexpr (std::is_same<TW, float>::value && std::is_same<TV, float>::value) {
+        if (len % F4_TILE == 0 && vstride % F4_TILE == 0) {
+            k_update_f4<<<grid, KR_THREADS, 0, s>>>(len, W, V, vstride, j, write_next ? 1 : 0, rs,
+                                                    ks, mode, second_pass ? 1 : 0, done);
             prof_end(s, PROF_UPDATE, (double)(j + 2 + (write_next ? 1 : 0)) * alg_n * sizeof(TV));
             count_launch();
             return;

@@ -55,7 +55,7 @@ mk_status validate_opts(const Problem &P, const mk_solve_opts &o) {
     if (!(o.tol > 0.0) || o.restart < 1 || o.restart > MK_MAX_RESTART || o.max_iters < 1)
         return MK_ERR_INVALID;
     if (o.levels < 2 || o.levels > MK_MAX_LEVELS) return MK_ERR_INVALID;
-    if (o.precision != 0 && o.precision != 1) return MK_ERR_INVALID;
+    if (o.precision < 0 || o.precision > 2) return MK_ERR_INVALID;
     if (o.mu_mode < 0 || o.mu_mode > 2) return MK_ERR_INVALID;
     if (o.orth < 0 || o.orth > 2) return MK_ERR_INVALID;
     if (o.n_cgs < 0) return MK_ERR_INVALID;
@@ -342,7 +342,7 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
         else if (o.mu_mode == 1) lv->w.mu = 1.0;
         else lv->w.mu = o.mu_value;
         mk_status st = upload_coefs(*lv, P.dim);
-        if (st == MK_OK && l == 0 && !fp64) {
+        if (st == MK_OK && l == 0 && o.precision == 1) {
             // double-float a*L and b*L rows for the level-1 matvec of the mixed solve
             std::vector<double> c = coef_concat(lv->Lx, P.dim == 2 ? &lv->Ly : nullptr);
             std::vector<float2> t;
@@ -365,13 +365,15 @@ mk_status build_hierarchy_new(Problem &P, const mk_solve_opts &o, std::unique_pt
         const size_t len = (size_t)lv->g.len;
         if (l == 0) {
             lv->m = o.restart;
-            MKCK(lv->V.alloc(sizeof(double) * len * (lv->m + 1)));
+            // level-1 basis: FP64 or double-float pairs (8 bytes), FP32 with precision 2
+            const size_t vs = o.precision == 2 ? sizeof(float) : sizeof(double);
+            MKCK(lv->V.alloc(vs * len * (lv->m + 1)));
             MKCK(lv->X.alloc(cs * len * lv->m));
             if (o.augment > 0) {
                 MKCK(H->aug.alloc(cs * len * o.augment));
                 H->aug_k = o.augment;
             }
-            MKCK(lv->W.alloc(sizeof(double) * len));
+            MKCK(lv->W.alloc(vs * len));
             st = alloc_kstate(*lv, lv->m);
             if (st != MK_OK) return st;
         } else if (l < L - 1) {
@@ -600,7 +602,7 @@ static void enqueue_inner_solve(Hierarchy &H, int l, const int *done, cudaStream
 void enqueue_cycle_step(Hierarchy &H, int l, int j, const int *done, cudaStream_t s) {
     if (H.precision == 0) {
         cycle_step_t<double, double, double, double, double>(H, l, j, done, s);
-    } else if (l == 0) {
+    } else if (l == 0 && H.precision == 1) {
         cycle_step_t<float, float2, float, float2, double>(H, l, j, done, s);
     } else {
         cycle_step_t<float, float, float, float, float>(H, l, j, done, s);
@@ -617,11 +619,14 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s, bool a
     const int *done = L.ks.flags;
     const int64_t len = L.g.len;
     const bool fp64 = H.precision == 0;
+    const bool sp = H.precision == 2;   // FP32 level-1 basis
     const size_t xs = fp64 ? sizeof(double) : sizeof(float);
     double *V = L.V.as<double>();
     double *W = L.W.as<double>();
     float2 *Vd = L.V.as<float2>();
     float2 *Wd = L.W.as<float2>();
+    float *Vf = L.V.as<float>();
+    float *Wf = L.W.as<float>();
     for (int j = 0; j < L.m; ++j) {
         t_outer_j = j;
         const int q = j - (L.m - H.aug_k);
@@ -632,6 +637,8 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s, bool a
             cudaMemcpyAsync(xj, dq, (size_t)len * xs, cudaMemcpyDeviceToDevice, s);
             if (fp64) {
                 launch_apply<double, double, double>(L.g, L.w, L.op64, reinterpret_cast<double *>(xj), W, s);
+            } else if (sp) {
+                launch_apply<float, float, float>(L.g, L.w, L.op32, reinterpret_cast<float *>(xj), Wf, s);
             } else {
                 launch_apply<float, double, double>(L.g, L.w, L.op64, reinterpret_cast<float *>(xj), W, s);
                 launch_f64_to_df(len, W, done, s);
@@ -646,6 +653,10 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s, bool a
             launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, false, done, s);
             launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, mode, false, done,
                                           s);
+        } else if (sp) {
+            launch_multidot<float, float>(len, Wf, Vf, L.stride, j, H.rs, L.ks, false, done, s);
+            launch_update<float, float>(len, Wf, Vf, L.stride, j, true, H.rs, L.ks, mode, false, done,
+                                        s);
         } else {
             launch_multidot_df(len, Wd, Vd, L.stride, j, H.rs, L.ks, false, done, s);
             launch_update_df(len, Wd, Vd, L.stride, j, H.rs, L.ks, mode, false, done, s);
@@ -655,6 +666,10 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s, bool a
                 launch_multidot<double, double>(len, W, V, L.stride, j, H.rs, L.ks, true, done, s);
                 launch_update<double, double>(len, W, V, L.stride, j, true, H.rs, L.ks, UPD_GIVENS,
                                               true, done, s);
+            } else if (sp) {
+                launch_multidot<float, float>(len, Wf, Vf, L.stride, j, H.rs, L.ks, true, done, s);
+                launch_update<float, float>(len, Wf, Vf, L.stride, j, true, H.rs, L.ks, UPD_GIVENS,
+                                            true, done, s);
             } else {
                 launch_multidot_df(len, Wd, Vd, L.stride, j, H.rs, L.ks, true, done, s);
                 launch_update_df(len, Wd, Vd, L.stride, j, H.rs, L.ks, UPD_GIVENS, true, done, s);
@@ -671,8 +686,12 @@ static void enqueue_outer_cycle(Problem &P, Hierarchy &H, cudaStream_t s, bool a
     } else {
         launch_combine_df(len, H.u.as<double>(), L.X.as<float>(), L.stride, L.ks, s,
                           H.aug_k ? H.aug.as<float>() : nullptr, H.aug_k);
-        launch_residual_df(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), Vd, H.rs, 0, L.ks,
-                           EPI_OUTER_START, s);
+        if (sp)
+            launch_residual_f32(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), Vf, H.rs, 0,
+                                L.ks, EPI_OUTER_START, s);
+        else
+            launch_residual_df(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), Vd, H.rs, 0,
+                               L.ks, EPI_OUTER_START, s);
     }
 }
 
@@ -739,6 +758,9 @@ mk_status solve_prepare(Hierarchy &H, const mk_solve_opts &o, cudaStream_t s) {
     if (H.precision == 0)
         launch_residual(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<double>(),
                         H.rs, 0, L.ks, EPI_OUTER_INIT, s);
+    else if (H.precision == 2)
+        launch_residual_f32(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<float>(),
+                            H.rs, 0, L.ks, EPI_OUTER_INIT, s);
     else
         launch_residual_df(L.g, L.w, L.op64, H.f.as<double>(), H.u.as<double>(), L.V.as<float2>(),
                            H.rs, 0, L.ks, EPI_OUTER_INIT, s);
@@ -979,7 +1001,7 @@ mk_status autotune_hierarchy(Hierarchy &H, cudaStream_t s) {
             tune_level<double, double>(H, l, s, e0, e1);
             tune_interp<double>(H, l, s, e0, e1);
         } else {
-            if (l == 0) tune_level<float, float2>(H, l, s, e0, e1);
+            if (l == 0 && H.precision == 1) tune_level<float, float2>(H, l, s, e0, e1);
             else tune_level<float, float>(H, l, s, e0, e1);
             tune_interp<float>(H, l, s, e0, e1);
         }

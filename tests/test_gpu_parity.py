@@ -339,7 +339,7 @@ def test_residual_thin_2d_grid():
 
 
 # --------------------------------------------------------------------------- end to end
-@pytest.mark.parametrize("precision,bound", [("fp64", 1e-10), ("mixed", 1e-8)])
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-10), ("mixed", 1e-8), ("mixed32", 1e-8)])
 def test_solve_small(case, precision, bound):
     P, H, p = case
     o = _opts(P.schedule, precision=precision)
@@ -358,15 +358,16 @@ def test_march_small(case):
     assert O.max_rel_error(u, ref) <= 1e-12
 
 
-def test_solve_is_deterministic_and_graph_independent(case):
+@pytest.mark.parametrize("precision", ["mixed", "mixed32"])
+def test_solve_is_deterministic_and_graph_independent(case, precision):
     P, H, p = case
     u1 = np.empty((P.nt + 1,) + P.space_shape())
     u2 = np.empty_like(u1)
     u3 = np.empty_like(u1)
-    o = _opts(P.schedule, precision="mixed")
+    o = _opts(P.schedule, precision=precision)
     mk.mk_solve(p.handle, P.u0, u1, o)
     mk.mk_solve(p.handle, P.u0, u2, o)
-    o2 = _opts(P.schedule, precision="mixed")
+    o2 = _opts(P.schedule, precision=precision)
     o2.use_graph = 0
     o2.restart = o.restart
     mk.mk_solve(p.handle, P.u0, u3, o2)
@@ -468,7 +469,7 @@ def test_full_size_1d_small_workload_fp64():
         assert O.max_rel_error(u, ref) <= 1e-10, info.iterations
 
 
-@pytest.mark.parametrize("precision,bound", [("fp64", 1e-10), ("mixed", 1e-8)])
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-10), ("mixed", 1e-8), ("mixed32", 1e-8)])
 def test_full_size_1d_large_workload(precision, bound):
     """n = 1023, n_t = 8192, theta = 1, 5 levels: the launch configuration the bench times."""
     P = W.heat1d_large(precision=precision)
