@@ -2,14 +2,15 @@
 
 Workload: 1D heat equation, n = 1023 interior points, theta = 1, n_t = 8192, T = 1, tau = 1,
 seeded u_0 (8 smooth modes) and a 4-mode space-time source; 5 time levels (nu = 2), mixed
-precision (FP32 cycle, FP64 outer).  The schedule knobs the method leaves free (the number
+precision (FP32 cycle and FP32 level-1 basis by default; FP64 true residual at every restart
+and FP64 iterate).  The schedule knobs the method leaves free (the number
 of decoupled coarsest slabs, the restart length, the inner iteration counts) are picked by
 the library's autotuner (mk_tune) before the timed region; the line's config records them.
 One step = one complete solve A_h u = f_h to the tolerance, inputs resident in HBM, L2
 flushed (256 MB write) between steps.
 
-Printed: one JSON line (rank 0).  Beside the headline (mixed MK) it reports the FP64 MK, the
-base schedule, the fastest schedule at any level count and the GPU sequential theta-march on
+Printed: one JSON line (rank 0).  Beside the headline (mixed MK) it reports the other mixed
+mode (double-float level-1 basis) on the same schedule, the FP64 MK, the base schedule, the fastest schedule at any level count and the GPU sequential theta-march on
 the same problem, the error of each against the CPU oracle, a kernel-class roofline from CUDA
 events, the oracle's own time on the host cores and an end-to-end figure through host
 buffers; then the 2D workload (with its own roofline, e2e and error against the oracle's full
@@ -154,7 +155,9 @@ def run_reference(args, world, rank):
 # coarse solve: multidot read 470.1 + wrote 3.0 MB against 469.4 MB algorithmic (j = 5) and
 # 537.3 MB against 536.4 MB (j = 6); update 528.4 MB against 536.4 MB and 593.8 MB against
 # 603.5 MB.  The ratio scales the average algorithmic bytes of a launch to its DRAM traffic.
-DRAM_TRAFFIC_RATIO = {"multidot@level1": 1.005, "update@level1": 0.984}
+# DRAM bytes / algorithmic bytes that ncu measured per launch of the level-1 Gram-Schmidt
+# kernels, by precision mode (profiles/: the double-float and FP32-basis captures)
+DRAM_TRAFFIC_RATIO = {("multidot@level1", "mixed"): 1.005, ("update@level1", "mixed"): 0.984}
 
 
 def profiled_classes(mk, torch, dev, solve):
@@ -279,13 +282,13 @@ def _ev_time(torch, fn, steps, flush=None):
     return statistics.mean(ts), r
 
 
-def roofline_of(rows, peak, peak_kind):
+def roofline_of(rows, peak, peak_kind, precision="mixed"):
     """Roofline object of the dominant kernel class of a profiled solve (no DRAM counters
     taken for it: traffic null unless a ratio was measured)."""
     top = rows[0]
     ach = top[1] / (top[0] * 1e-3) / 1e9
     kname = f"{top[3]}@level{top[4]}"
-    ratio = DRAM_TRAFFIC_RATIO.get(kname)
+    ratio = DRAM_TRAFFIC_RATIO.get((kname, precision))
     return {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "peak_kind": peak_kind,
             "traffic": (ratio * top[1] / top[2]) if ratio else None,
@@ -303,7 +306,7 @@ def bench_2d(mk, torch, dev, args, flush, steps=2):
     P = W.heat2d_large()
     s = P.schedule
     base = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=s.n_cgs,
-                        tol=args.tol_2d, restart=args.restart, precision="mixed", orth=args.orth,
+                        tol=args.tol_2d, restart=args.restart, precision=args.precision, orth=args.orth,
                         autotune=not args.no_autotune, max_iters=3000)
     u0 = torch.from_numpy(P.u0).to(dev)
     u = torch.empty((P.nt + 1,) + P.space_shape(), dtype=torch.float64, device=dev)
@@ -325,7 +328,8 @@ def bench_2d(mk, torch, dev, args, flush, steps=2):
         out["max_rel_diff_vs_march"] = float(((um - u).abs().max() / um.abs().max()).item())
         rows = profiled_classes(mk, torch, dev, lambda: mk.mk_solve(p.handle, u0, u, o))
         peak, peak_kind = _peaks()
-        out["roofline"] = roofline_of(rows, peak, peak_kind)
+        out["roofline"] = roofline_of(rows, peak, peak_kind, args.precision)
+        out["precision"] = args.precision
         out["kernel_classes"] = class_table(rows)
         # end to end through the public API with host buffers (u_0 in, u out)
         u0_h = torch.from_numpy(P.u0).pin_memory()
@@ -507,9 +511,9 @@ def bench_batch(mk, torch, dev, args, count_1d=48, count_2d=16, max_iters=3000):
     ol, trials = [], 0
     for P, p, x in zip(ms, probs, u0):
         if args.no_tune:
-            ol.append(base(P, "mixed"))
+            ol.append(base(P, args.precision))
             continue
-        o, ti = mk.mk_tune(p.handle, x, base(P, "mixed"), levels=(P.dim == 1),
+        o, ti = mk.mk_tune(p.handle, x, base(P, args.precision), levels=(P.dim == 1),
                            max_trials=args.tune_trials_batch, restart_cap=True)
         ol.append(o)
         trials += int(ti.trials)
@@ -579,6 +583,10 @@ def main():
                     help="relative residual target of the 2D solve: its error is ~4x its residual "
                          "(1e-9 gives 4.2e-9 against the GPU march, 3e-9 gives 1.7e-8)")
     ap.add_argument("--restart", type=int, default=40)
+    ap.add_argument("--precision", choices=("mixed32", "mixed"), default="mixed32",
+                    help="mixed mode of the headline and the 2D workload: FP32 level-1 basis "
+                         "(mixed32) or double-float level-1 basis (mixed); the other mode runs "
+                         "on the headline's schedule as a secondary path")
     ap.add_argument("--n-cgs", type=int, default=None,
                     help="coarsest slabs of the headline's base schedule (default: the workload's 16; "
                          "0 = the exact coupled coarse solve)")
@@ -633,7 +641,8 @@ def main():
                             restart=args.restart, precision=precision, orth=args.orth,
                             autotune=not args.no_autotune)
 
-    base_mixed, base_fp64 = opts("mixed"), opts("fp64")
+    base_mixed, base_fp64 = opts(args.precision), opts("fp64")
+    other_prec = "mixed" if args.precision == "mixed32" else "mixed32"
     g_dev = torch.from_numpy(P.g).to(dev)
     u0_dev = torch.from_numpy(P.u0).to(dev)
     u_dev = torch.empty((P.nt + 1, P.nx), dtype=torch.float64, device=dev)
@@ -696,7 +705,7 @@ def main():
     u_mixed = u_dev.cpu().numpy().copy()
 
     cfg = {"workload": WORKLOAD, "nx": P.nx, "nt": P.nt, "theta": P.theta, "levels": s.levels,
-           "nu": list(s.nu), "precision": "mixed", "tol": args.tol, "orth": args.orth,
+           "nu": list(s.nu), "precision": args.precision, "tol": args.tol, "orth": args.orth,
            "autotune": not args.no_autotune, "parallelism": f"replicas x{world}",
            "l2": "flushed between steps (256 MB write)"}
     cfg.update(sched(o_mixed))
@@ -705,7 +714,10 @@ def main():
     line = {"metric": METRIC, "value": ms_mixed / 1e3, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 cycle + f64 outer", "data": "synthetic", "config": cfg,
+            "dtype": ("f32 cycle and level-1 basis, f64 residual and iterate"
+                      if args.precision == "mixed32" else
+                      "f32 cycle, double-float level-1 basis, f64 residual and iterate"),
+            "data": "synthetic", "config": cfg,
             "gpu_launches": int(launches),
             "iterations": int(inf_mixed[-1].iterations)}
     if clk:
@@ -722,6 +734,15 @@ def main():
         u_fp64 = u_dev.cpu().numpy().copy()
         t_def, inf_def, _ = timed(base_mixed, 2, 1)
         u_def = u_dev.cpu().numpy().copy()
+        # the other mixed mode on the headline's schedule
+        o_other = mk.make_opts(levels=o_mixed.levels, nu=list(o_mixed.nu)[:o_mixed.levels - 1],
+                               space=[bool(x) for x in list(o_mixed.space)[:o_mixed.levels - 1]],
+                               m_inner=list(o_mixed.m_inner)[:max(o_mixed.levels - 2, 0)],
+                               n_cgs=o_mixed.n_cgs, tol=args.tol, restart=o_mixed.restart,
+                               precision=other_prec, orth=args.orth, autotune=not args.no_autotune)
+        t_oth, inf_oth, _ = timed(o_other, 3, 1)
+        u_oth = u_dev.cpu().numpy().copy()
+        mk.mk_trim(prob.handle)
         tm = []
         for i in range(4):
             flush.fill_(1.0)
@@ -770,7 +791,7 @@ def main():
         # ---------------- roofline: kernel-class timing of one profiled solve ----------------
         rows = profiled_classes(mk, torch, dev, lambda: mk.mk_solve(prob.handle, u0_dev, u_dev, o_mixed))
         peak, peak_kind = _peaks()
-        line["roofline"] = roofline_of(rows, peak, peak_kind)
+        line["roofline"] = roofline_of(rows, peak, peak_kind, args.precision)
         line["kernel_classes"] = class_table(rows)
         # device time per outer iteration by level (event-bracketed launches of the profiled
         # solve; its iteration count is that of the level-1 launches)
@@ -816,6 +837,9 @@ def main():
             "mk_mixed": {"s": ms_mixed / 1e3, "iterations": int(inf_mixed[-1].iterations),
                          "rel_residual": inf_mixed[-1].rel_residual, "schedule": sched(o_mixed),
                          "max_rel_err": O.max_rel_error(u_mixed, ref)},
+            "mk_" + other_prec + "_same_schedule": {
+                "s": statistics.mean(t_oth) / 1e3, "iterations": int(inf_oth[-1].iterations),
+                "schedule": sched(o_other), "max_rel_err": O.max_rel_error(u_oth, ref)},
             "mk_mixed_default_schedule": {"s": statistics.mean(t_def) / 1e3,
                                           "iterations": int(inf_def[-1].iterations),
                                           "schedule": sched(base_mixed),

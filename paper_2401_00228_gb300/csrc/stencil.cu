@@ -12,6 +12,8 @@
 // coalesced along i (the contiguous direction of the padded layout).
 #include "kernels.h"
 #include "reduce.cuh"
+#include <type_traits>
+
 #include "stencil_common.cuh"
 
 namespace mk {
@@ -755,6 +757,179 @@ __global__ void __launch_bounds__(256) k_interp_1d(Geom gf, Geom gc, int nu, Tc 
     }
 }
 
+// 2D K4 with 2 x 2 aggregates in one arithmetic type T (FP32), walked in time.  A
+// thread owns the aggregate (I, J): the fine points (2I, 2I+1) x (2J, 2J+1), which share one
+// coarse value (Z vt)_{K(k)}.  Per fine step it forms x at those four points and at the two
+// points of each adjacent row (2J-1, 2J+2: the aggregates J-1 and J+1); the columns 2I-1 and
+// 2I+2 come from the neighbouring lanes by warp shuffles (the first and last lane form them
+// itself).  x_{k-1} and L x_{k-1} stay in registers from the previous step, so x and w are
+// written once per point and v read once per point from HBM (the adjacent rows are the
+// neighbouring threads' rows, served by the caches); the global loads of step k+1 are issued
+// before step k is computed.  The arithmetic is that of k_apply_2d (lap_at's order:
+// x part, then the y part added; w_k = (x_k - a L x_k) - (x_{k-1} + b L x_{k-1})).  MC: the
+// number of coarse directions combined (0: Xc itself).  Row starts are multiples of eight
+// elements and i0 is even, so the paired accesses are 8-byte aligned; a row is read only
+// where it is interior.
+template <typename T>
+__device__ __forceinline__ void ld_pair_t(const T *p, T &a, T &b);
+template <>
+__device__ __forceinline__ void ld_pair_t<float>(const float *p, float &a, float &b) {
+    const float2 q = *reinterpret_cast<const float2 *>(p);
+    a = q.x;
+    b = q.y;
+}
+template <>
+__device__ __forceinline__ void ld_pair_t<double>(const double *p, double &a, double &b) {
+    const double2 q = *reinterpret_cast<const double2 *>(p);
+    a = q.x;
+    b = q.y;
+}
+template <typename T>
+__device__ __forceinline__ void st_pair_t(T *p, T a, T b);
+template <>
+__device__ __forceinline__ void st_pair_t<float>(float *p, float a, float b) {
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+}
+template <>
+__device__ __forceinline__ void st_pair_t<double>(double *p, double a, double b) {
+    *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+}
+
+template <typename T, int MC>
+__global__ void __launch_bounds__(256, 2) k_interp_2d_ts(Geom gf, Geom gc, int nu, T a, T b,
+                                                         SpaceOp<T> L, const T *__restrict__ v,
+                                                         const double *__restrict__ sigma,
+                                                         const T *__restrict__ Xc,
+                                                         int64_t xc_stride,
+                                                         const double *__restrict__ yc,
+                                                         T *__restrict__ x, T *__restrict__ w,
+                                                         int kc, const int *__restrict__ done) {
+    if (done && *done) return;   // the same flag for every thread of the block
+    constexpr int NZ = MC > 0 ? MC : 1;
+    __shared__ T s_w[NZ + 1];
+    const int t = threadIdx.x + 32 * threadIdx.y;
+    if (t == 0) s_w[0] = sigma ? (T)(*sigma) : (T)1;
+    else if (MC > 0 && t <= MC) s_w[t] = (T)yc[t - 1];
+    __syncthreads();
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x;
+    const int I = blockIdx.x * 32 + lane;
+    const int J = blockIdx.y * 8 + threadIdx.y;
+    const int nx = gf.nx, ny = gf.ny;
+    const int64_t ldx = gf.ldx, cld = gc.ldx;
+    const int i0 = 2 * I, j0 = 2 * J;
+    if (j0 >= ny) return;   // the whole warp shares J
+    const T sig = s_w[0];
+    T ym[NZ];
+#pragma unroll
+    for (int m = 0; m < NZ; ++m) ym[m] = MC > 0 ? s_w[1 + m] : (T)1;
+    const bool c0 = i0 < nx, c1 = i0 + 1 < nx, r1 = j0 + 1 < ny;
+    const bool hd = c0 && j0 > 0, hu = c0 && j0 + 2 < ny;
+    const bool cl = lane == 0 && i0 > 0 && i0 - 1 < nx, cr = lane == 31 && i0 + 2 < nx;
+    const int64_t o0 = (int64_t)j0 * ldx + i0;   // fine offset of (2J, 2I) in a plane
+    const int64_t oc = (int64_t)J * cld + I;      // coarse offset of (J, I)
+    const int64_t oe = o0 + (cl ? -1 : 2);        // outside column of the first / last lane
+    const int64_t oce = oc + (cl ? -1 : 1);
+    // coefficients of the thread's columns and rows (0 where masked)
+    const T *cx = L.x, *cy = L.y;
+    const int i1 = i0 + 1, j1 = j0 + 1;
+    const T xl0 = c0 ? cx[i0] : (T)0, xd0 = c0 ? cx[nx + i0] : (T)0, xu0 = c0 ? cx[2 * nx + i0] : (T)0;
+    const T xl1 = c1 ? cx[i1] : (T)0, xd1 = c1 ? cx[nx + i1] : (T)0, xu1 = c1 ? cx[2 * nx + i1] : (T)0;
+    const T yl0 = c0 ? cy[j0] : (T)0, yd0 = c0 ? cy[ny + j0] : (T)0, yu0 = c0 ? cy[2 * ny + j0] : (T)0;
+    const T yl1 = (c0 && r1) ? cy[j1] : (T)0, yd1 = (c0 && r1) ? cy[ny + j1] : (T)0,
+            yu1 = (c0 && r1) ? cy[2 * ny + j1] : (T)0;
+    // raw loads of one step
+    T A0a = 0, A0b = 0, A1a = 0, A1b = 0, QDa = 0, QDb = 0, QUa = 0, QUb = 0, VE0 = 0, VE1 = 0;
+    T ZO[NZ], ZD[NZ], ZU[NZ], ZE[NZ];
+    auto load = [&](int k, int K) {
+        const T *vk = v + gf.guard + (int64_t)k * gf.plane;
+        const T *zk = Xc + gc.guard + (int64_t)K * gc.plane;
+        A0a = A0b = A1a = A1b = QDa = QDb = QUa = QUb = VE0 = VE1 = (T)0;
+        if (c0) ld_pair_t<T>(vk + o0, A0a, A0b);
+        if (c0 && r1) ld_pair_t<T>(vk + o0 + ldx, A1a, A1b);
+        if (hd) ld_pair_t<T>(vk + o0 - ldx, QDa, QDb);
+        if (hu) ld_pair_t<T>(vk + o0 + 2 * ldx, QUa, QUb);
+#pragma unroll
+        for (int m = 0; m < NZ; ++m) {
+            const T *zm = zk + (int64_t)m * xc_stride;
+            ZO[m] = c0 ? zm[oc] : (T)0;
+            ZD[m] = hd ? zm[oc - cld] : (T)0;
+            ZU[m] = hu ? zm[oc + cld] : (T)0;
+            ZE[m] = (cl || cr) ? zm[oce] : (T)0;
+        }
+        if (cl || cr) {
+            VE0 = vk[oe];
+            if (r1) VE1 = vk[oe + ldx];
+        }
+    };
+    auto comb = [&](const T (&zr)[NZ]) -> T {
+        if (MC == 0) return zr[0];
+        T z = mul_rn(ym[0], zr[0]);
+#pragma unroll
+        for (int m = 1; m < NZ; ++m) z = fma_rn(ym[m], zr[m], z);
+        return z;
+    };
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(k0 + kc, gf.nt + 1);
+    const int kstart = k0 > 0 ? k0 - 1 : 0;
+    // coarse block of fine step k: 0 for k = 0, (k-1)/nu + 1 otherwise (tracked incrementally)
+    int K = (kstart == 0) ? 0 : (kstart - 1) / nu + 1;
+    int ph = (kstart == 0) ? nu - 1 : (kstart - 1) % nu;
+    T p00 = 0, p01 = 0, p10 = 0, p11 = 0;   // x_{k-1}
+    T L00 = 0, L01 = 0, L10 = 0, L11 = 0;   // L x_{k-1}
+    load(kstart, K);
+    for (int k = kstart; k < k1; ++k) {
+        const T a0a = A0a, a0b = A0b, a1a = A1a, a1b = A1b, qda = QDa, qdb = QDb, qua = QUa,
+                qub = QUb, ve0 = VE0, ve1 = VE1;
+        const T zo = comb(ZO), zd = comb(ZD), zu = comb(ZU), ze = comb(ZE);
+        if (k + 1 < k1) {
+            if (ph == nu - 1) {
+                ++K;
+                ph = 0;
+            } else {
+                ++ph;
+            }
+            load(k + 1, K);
+        }
+        const T x00 = c0 ? fma_rn(sig, a0a, -zo) : (T)0;
+        const T x01 = c1 ? fma_rn(sig, a0b, -zo) : (T)0;
+        const T x10 = (c0 && r1) ? fma_rn(sig, a1a, -zo) : (T)0;
+        const T x11 = (c1 && r1) ? fma_rn(sig, a1b, -zo) : (T)0;
+        const T d0 = hd ? fma_rn(sig, qda, -zd) : (T)0, d1 = (hd && c1) ? fma_rn(sig, qdb, -zd) : (T)0;
+        const T e0 = hu ? fma_rn(sig, qua, -zu) : (T)0, e1 = (hu && c1) ? fma_rn(sig, qub, -zu) : (T)0;
+        T l0 = __shfl_up_sync(FULL, x01, 1), l1 = __shfl_up_sync(FULL, x11, 1);
+        T q0 = __shfl_down_sync(FULL, x00, 1), q1 = __shfl_down_sync(FULL, x10, 1);
+        const T xe0 = (cl || cr) ? fma_rn(sig, ve0, -ze) : (T)0;
+        const T xe1 = ((cl || cr) && r1) ? fma_rn(sig, ve1, -ze) : (T)0;
+        if (lane == 0) {
+            l0 = xe0;
+            l1 = xe1;
+        }
+        if (lane == 31) {
+            q0 = xe0;
+            q1 = xe1;
+        }
+        const T s00 = (xd0 * x00 + xl0 * l0 + xu0 * x01) + (yd0 * x00 + yl0 * d0 + yu0 * x10);
+        const T s01 = (xd1 * x01 + xl1 * x00 + xu1 * q0) + (yd0 * x01 + yl0 * d1 + yu0 * x11);
+        const T s10 = (xd0 * x10 + xl0 * l1 + xu0 * x11) + (yd1 * x10 + yl1 * x00 + yu1 * e0);
+        const T s11 = (xd1 * x11 + xl1 * x10 + xu1 * q1) + (yd1 * x11 + yl1 * x01 + yu1 * e1);
+        if (k >= k0 && c0) {
+            auto wk = [&](T c, T Lc, T p, T Lp) -> T {
+                return k == 0 ? c : (c - a * Lc) - (p + b * Lp);
+            };
+            const int64_t f0 = gf.guard + (int64_t)k * gf.plane + o0;
+            st_pair_t<T>(x + f0, x00, x01);
+            st_pair_t<T>(w + f0, wk(x00, s00, p00, L00), c1 ? wk(x01, s01, p01, L01) : (T)0);
+            if (r1) {
+                st_pair_t<T>(x + f0 + ldx, x10, x11);
+                st_pair_t<T>(w + f0 + ldx, wk(x10, s10, p10, L10), c1 ? wk(x11, s11, p11, L11) : (T)0);
+            }
+        }
+        p00 = x00; p01 = x01; p10 = x10; p11 = x11;
+        L00 = s00; L01 = s01; L10 = s10; L11 = s11;
+    }
+}
+
 template <typename Tv, typename Tz, typename Tx, typename Tw, typename Tc>
 void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Weights &w,
                    SpaceOp<Tc> L, const Tv *v, const double *sigma, const Tz *Xc, int mc,
@@ -785,6 +960,35 @@ void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Wei
         // 1D, nu = 2: time-tiled kernel (transfer1d.cu)
     } else if (gf.dim == 1) {
         if (space) MK_INTERP1(true); else MK_INTERP1(false);
+    } else if (std::is_same<Tc, float>::value && std::is_same<Tv, Tc>::value &&
+               std::is_same<Tz, Tc>::value && std::is_same<Tx, Tc>::value &&
+               std::is_same<Tw, Tc>::value && space && (!yc || (mc >= 1 && mc <= 4))) {
+        // 2 x 2 aggregates in FP32 (the FP64 instances would spill registers):
+        // aggregate-per-thread kernel walked in time;
+        // chunks for one full wave of 2048 threads per SM, at least eight fine steps each
+        // (the step before a chunk is formed again), at most 65535 chunks
+        if constexpr (std::is_same<Tc, float>::value && std::is_same<Tv, Tc>::value &&
+                      std::is_same<Tz, Tc>::value && std::is_same<Tx, Tc>::value &&
+                      std::is_same<Tw, Tc>::value) {
+            const int ncx = (gf.nx + 1) / 2, ncy = (gf.ny + 1) / 2;
+            const int nsteps = gf.nt + 1;
+            const int64_t want = (int64_t)g_num_sms * 2048;
+            int64_t kt = ((int64_t)ncx * ncy * nsteps) / (want > 0 ? want : 1);
+            if (kt < 8) kt = 8;
+            if (kt > nsteps) kt = nsteps;
+            while ((nsteps + kt - 1) / kt > 65535) ++kt;
+            const int kct = (int)kt;
+            const dim3 grid((ncx + 31) / 32, (ncy + 7) / 8, (nsteps + kct - 1) / kct), blk(32, 8, 1);
+#define MK_I2T(M)                                                                                \
+    k_interp_2d_ts<Tc, M><<<grid, blk, 0, s>>>(gf, gc, nu, a, b, L, v, sigma, Xc, xc_stride, yc, x, \
+                                               wout, kct, done)
+            if (!yc) MK_I2T(0);
+            else if (mc == 1) MK_I2T(1);
+            else if (mc == 2) MK_I2T(2);
+            else if (mc == 3) MK_I2T(3);
+            else MK_I2T(4);
+#undef MK_I2T
+        }
     } else {
         // 2D: x once per point, then w = A x from the stored x (the fused form evaluated x
         // again at each of the four stencil neighbours of every point)
