@@ -157,7 +157,8 @@ def run_reference(args, world, rank):
 # 603.5 MB.  The ratio scales the average algorithmic bytes of a launch to its DRAM traffic.
 # DRAM bytes / algorithmic bytes that ncu measured per launch of the level-1 Gram-Schmidt
 # kernels, by precision mode (profiles/: the double-float and FP32-basis captures)
-DRAM_TRAFFIC_RATIO = {("multidot@level1", "mixed"): 1.005, ("update@level1", "mixed"): 0.984}
+DRAM_TRAFFIC_RATIO = {("multidot@level1", "mixed"): 1.005, ("update@level1", "mixed"): 0.984,
+                      ("multidot@level1", "mixed32"): 1.005, ("update@level1", "mixed32"): 0.999}
 
 
 def profiled_classes(mk, torch, dev, solve):
@@ -466,9 +467,10 @@ def bench_two_level(mk, torch, dev, steps=1):
     return out
 
 
-def profile_2d():
-    """A few outer iterations of the 2D workload's solver on 255 x 255 x 513 (33.4 M points,
-    double-float vectors of 267 MB: larger than L2, a few GB on the device in all)."""
+def profile_2d(precision="mixed32"):
+    """A few outer iterations of the 2D workload's solver (inner counts 2, 2, the exact coarse
+    solve) on 255 x 255 x 513 (33.4 M points, level-1 vectors of 133 MB (FP32) or 267 MB
+    (double-float): larger than L2, a few GB on the device in all)."""
     import torch
     import paper_2401_00228_gb300 as mk
     n, nt = 255, 512
@@ -476,19 +478,40 @@ def profile_2d():
     s = P.schedule
     u0 = torch.from_numpy(P.u0).cuda()
     u = torch.empty((nt + 1, n, n), dtype=torch.float64, device="cuda")
-    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=s.m_inner, n_cgs=s.n_cgs,
-                     tol=1e-12, restart=10, max_iters=3, precision="mixed")
+    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=(2, 2), n_cgs=0,
+                     tol=1e-12, restart=10, max_iters=3, precision=precision)
     with mk.Problem(2, n, P.tau, P.theta, P.dt, nt, None, ny=n) as p:
         info = mk.mk_solve(p.handle, u0, u, o, allow_not_converged=True)
         torch.cuda.synchronize()
     print(json.dumps({"profile_2d": "heat2d_255x255_nt512", "iterations": int(info.iterations)}))
 
 
+def profile_run_2d(precision="mixed32"):
+    """One warm-up solve and one solve of the 2D workload (255 x 255, n_t = 1024) at a fixed
+    schedule (inner counts 2, 2, the exact coarse solve, restart 12, tol 1e-9), no timing: the
+    command whose launch list ncu records (one pass per launch)."""
+    import torch
+    import paper_2401_00228_gb300 as mk
+    P = W.heat2d_large()
+    s = P.schedule
+    u0 = torch.from_numpy(P.u0).cuda()
+    u = torch.empty((P.nt + 1,) + P.space_shape(), dtype=torch.float64, device="cuda")
+    o = mk.make_opts(levels=s.levels, nu=s.nu, space=s.space, m_inner=(2, 2), n_cgs=0,
+                     tol=1e-9, restart=12, max_iters=3000, precision=precision)
+    with mk.Problem(2, P.nx, P.tau, P.theta, P.dt, P.nt, None, ny=P.ny) as p:
+        for _ in range(2):
+            info = mk.mk_solve(p.handle, u0, u, o)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile_run_2d": "heat2d_255x255_nt1024", "precision": precision,
+                      "iterations": int(info.iterations),
+                      "launches_per_solve": int(info.kernel_launches)}))
+
+
 def bench_batch(mk, torch, dev, args, count_1d=48, count_2d=16, max_iters=3000):
     """The uneven batched workload: 64 members (48 1D with n in 63..2047 and n_t in
     256..8192, 16 2D with side 63..255 and n_t 128..1024, tau log-uniform in [0.1, 10], theta in
-    {1/2, 1}, end time from a Courant number in the range of its theta), mixed precision, tol
-    1e-10.  Each member's schedule comes from the autotuner (mk_tune: the level count too for
+    {1/2, 1}, end time from a Courant number in the range of its theta), the headline's mixed
+    mode, tol 1e-10.  Each member's schedule comes from the autotuner (mk_tune: the level count too for
     1D members, n_cgs, restart, inner counts; a bounded number of trial solves, outside the
     timed region), then all 64 run as one batch whose replay is one CUDA graph per restart
     cycle (tile autotuning on).  Compared, on the same members: the same solves one after
@@ -566,7 +589,7 @@ def bench_batch(mk, torch, dev, args, count_1d=48, count_2d=16, max_iters=3000):
             "converged": int(sum(conv)), "max_rel_diff_vs_march": max(errs),
             "levels": [int(o.levels) for o in ol], "n_cgs": [int(o.n_cgs) for o in ol],
             "iterations": [int(i.iterations) for i in infos],
-            "workload": "batched_problems(seed=4): 48 1D + 16 2D members, mixed, tol 1e-10"}
+            "workload": f"batched_problems(seed=4): 48 1D + 16 2D members, {args.precision}, tol 1e-10"}
 
 
 def main():
@@ -606,13 +629,19 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="run one warm-up solve and one solve of the workload, no timing (the "
                          "command that ncu captures)")
+    ap.add_argument("--profile-run-2d", action="store_true",
+                    help="run one warm-up solve and one solve of the 2D workload at a fixed "
+                         "schedule, no timing (the command whose launch list ncu records)")
     ap.add_argument("--profile-2d", action="store_true",
                     help="run a short 2D solve (255 x 255, n_t = 512, the 2D workload's schedule, "
                          "restart 10, 3 outer iterations), no timing: the small case on which ncu "
                          "captures the 2D level-1 transfer kernels")
     args = ap.parse_args()
+    if args.profile_run_2d:
+        profile_run_2d(args.precision)
+        return
     if args.profile_2d:
-        profile_2d()
+        profile_2d(args.precision)
         return
     args.warmup = max(args.warmup, 3)
     world, rank, local = _dist()
