@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_update(int64_t len, const TW *__
         if (write_next) out[e] = (TV)val;
         acc += val * val;
     }
-    double bs = block_sum((double)acc);
+    double bs = block_sum_t(acc);
     if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
     if (last_block_ticket(rs.counter, threadIdx.x == 0)) {
         double tot = sum_partials(rs.partials, gridDim.x);
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_update_f4(int64_t len, const flo
         acc = fmaf(val.z, val.z, acc);
         acc = fmaf(val.w, val.w, acc);
     }
-    double bs = block_sum((double)acc);
+    double bs = block_sum_t(acc);
     if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
     if (last_block_ticket(rs.counter, threadIdx.x == 0)) {
         double tot = sum_partials(rs.partials, gridDim.x);
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_multidot_sb(int64_t len, const T
     const int nslots = second ? NV : NV + 1;
 #pragma unroll
     for (int i = 0; i <= NV; ++i) {
-        const double t = warp_sum((double)d[i]);
+        const double t = (double)warp_sum_t(d[i]);   // warp stage in the arithmetic type
         if (lane == 0) acc[i * KR_WARPS + warp] = t;
     }
     __syncthreads();
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_update_sb(int64_t len, const T *
 #pragma unroll
         for (int q = 0; q < SB_EPT; ++q) acc += val[q] * val[q];
     }
-    double bs = block_sum((double)acc);
+    double bs = block_sum_t(acc);
     if (threadIdx.x == 0) rs.partials[blockIdx.x] = bs;
     if (last_block_ticket(rs.counter, threadIdx.x == 0)) {
         double tot = sum_partials(rs.partials, gridDim.x);

@@ -43,6 +43,28 @@ __device__ __forceinline__ double block_sum(double v) {
     return r;
 }
 
+// The same for a per-thread value in its arithmetic type T: the warp stage runs in T (an FP32
+// value is summed by FP32 shuffles and adds, not at GB300's FP64 rate, 1/58 of FP32), the
+// warp sums are then added in FP64.  Result valid in thread 0.
+template <typename T>
+__device__ __forceinline__ double block_sum_t(T v) {
+    __shared__ double red_smem_t[32];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, warp = tid >> 5;
+    const double wv = (double)warp_sum_t(v);
+    __syncthreads();  // red_smem_t may still be read by a previous call
+    if (lane == 0) red_smem_t[warp] = wv;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        int nw = (nthreads + 31) >> 5;
+        r = (lane < nw) ? red_smem_t[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
 __device__ __forceinline__ int linear_block() {
     return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
 }
@@ -105,6 +127,24 @@ __device__ __forceinline__ void run_epilogue(double total, KState ks, int epi) {
         if (!isfinite(beta)) {
             ks.flags[3] = 1;
             ks.flags[0] = 1;
+        }
+    }
+}
+
+// Block partial of a per-thread value in its arithmetic type (block_sum_t) -> partial slot;
+// last block sums and runs the epilogue.
+template <typename T>
+__device__ __forceinline__ void block_partial_and_finish_t(T v, const ReduceScratch &rs, int slot,
+                                                           KState ks, int epi) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    double bs = block_sum_t(v);
+    double *part = rs.partials + (int64_t)slot * rs.max_blocks;
+    if (tid == 0) part[linear_block()] = bs;
+    if (last_block_ticket(rs.counter + slot, tid == 0)) {
+        double tot = sum_partials(part, num_blocks());
+        if (tid == 0) {
+            run_epilogue(tot, ks, epi);
+            rs.counter[slot] = 0u;
         }
     }
 }

@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu_rt, T
     const int nu = NU > 0 ? NU : nu_rt;
     int I, J, chunk;
     point_index<DIM>(I, J, chunk);
-    Tc acc2 = (Tc)0;   // per-thread sum in the arithmetic type (FP64 only across threads)
+    Tc acc2 = (Tc)0;   // per-thread and per-warp sums in the arithmetic type, FP64 across warps
     const bool active = I < gc.nx && J < gc.ny;
     if (active) {
         const Tc scale = sigma ? (Tc)(*sigma) : (Tc)1;
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu_rt, T
             acc2 += outv * outv;
         }
     }
-    if (ks.d) block_partial_and_finish((double)acc2, rs, slot, ks, EPI_BETA);
+    if (ks.d) block_partial_and_finish_t(acc2, rs, slot, ks, EPI_BETA);
 }
 
 // 2D specialisation of K3 for 2 x 2 agglomeration and nu = 2 (every coarsening of the 2D
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(256) k_restrict_2d_ts(Geom gf, Geom gc, Tc a, 
     const int K0 = chunk * kc;
     const int K1 = min(K0 + kc, gc.nt + 1);
     if (K0 > 0) step(2 * (K0 - 1), prev, Lprev);
-    Tc acc2 = (Tc)0;   // per-thread sum in the arithmetic type (FP64 only across threads)
+    Tc acc2 = (Tc)0;   // per-thread and per-warp sums in the arithmetic type, FP64 across warps
     for (int K = K0; K < K1; ++K) {
         Tc sum = 0;
         if (K == 0) {
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(256) k_restrict_2d_ts(Geom gf, Geom gc, Tc a, 
             acc2 += outv * outv;
         }
     }
-    if (ks.d) block_partial_and_finish((double)acc2, rs, slot, ks, EPI_BETA);
+    if (ks.d) block_partial_and_finish_t(acc2, rs, slot, ks, EPI_BETA);
 }
 
 // 1D specialisation of K3: one thread per coarse column; each fine value is loaded once and
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(256) k_restrict_1d(Geom gf, Geom gc, int nu, T
             l1 = (Tc)0;
         }
     };
-    Tc acc2 = (Tc)0;   // per-thread sum in the arithmetic type (FP64 only across threads)
+    Tc acc2 = (Tc)0;   // per-thread and per-warp sums in the arithmetic type, FP64 across warps
     const int K0 = blockIdx.y * kc;
     const int K1 = min(K0 + kc, gc.nt + 1);
     Tc pr0 = 0, pr1 = 0, Lp0 = 0, Lp1 = 0;
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(256) k_restrict_1d(Geom gf, Geom gc, int nu, T
             acc2 += outv * outv;
         }
     }
-    if (ks.d) block_partial_and_finish((double)acc2, rs, slot, ks, EPI_BETA);
+    if (ks.d) block_partial_and_finish_t(acc2, rs, slot, ks, EPI_BETA);
 }
 
 template <typename Tin, typename Tout, typename Tc>

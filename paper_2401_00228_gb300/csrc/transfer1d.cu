@@ -150,8 +150,9 @@ __global__ void __launch_bounds__(TT) k_restrict_1d_t(Geom gf, Geom gc, Tc a, Tc
     };
     const Tc scale = sigma ? (Tc)(*sigma) : (Tc)1;
     const int nK = gc.nt + 1 - K0;
-    // the norm of vhat for the next level's beta: summed per thread in the arithmetic type
-    // (FP64 per element would run at the FP64 rate, 1/64 of FP32 here), in FP64 across threads
+    // the norm of vhat for the next level's beta: summed per thread and per warp in the
+    // arithmetic type (FP64 per element would run at the FP64 rate, 1/58 of FP32 here), in FP64
+    // across warps
     Tc acc2 = (Tc)0;
     Tc lp[PT];
     lap(0, lp);
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(TT) k_restrict_1d_t(Geom gf, Geom gc, Tc a, Tc
             }
         }
     }
-    if (ks.d) block_partial_and_finish((double)acc2, rs, slot, ks, EPI_BETA);
+    if (ks.d) block_partial_and_finish_t(acc2, rs, slot, ks, EPI_BETA);
 }
 
 // ---------------------------------------------------------------------------------------
