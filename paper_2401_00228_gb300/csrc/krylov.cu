@@ -393,9 +393,14 @@ __global__ void __launch_bounds__(KR_THREADS) k_update_sb(int64_t len, const T *
     if (done && *done) return;
     if (second && !ks.flags[2]) return;
     constexpr int j = NV - 1;
+    // the coefficients c_i = tmp_i sigma_i, formed once per block (FP64 products and
+    // conversions issue at GB300's FP64 rate)
+    __shared__ T c_s[NV];
+    if (threadIdx.x < NV) c_s[threadIdx.x] = (T)(ks.tmp()[threadIdx.x] * ks.sigma()[threadIdx.x]);
+    __syncthreads();
     T c[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) c[i] = (T)(ks.tmp()[i] * ks.sigma()[i]);
+    for (int i = 0; i < NV; ++i) c[i] = c_s[i];
     T *out = V + (int64_t)(j + 1) * vstride;
     T acc = (T)0;
     for (int64_t base = ((int64_t)blockIdx.x * KR_THREADS + threadIdx.x) * SB_EPT; base < len;

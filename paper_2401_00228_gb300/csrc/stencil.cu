@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int nu_rt, T
     point_index<DIM>(I, J, chunk);
     Tc acc2 = (Tc)0;   // per-thread and per-warp sums in the arithmetic type, FP64 across warps
     const bool active = I < gc.nx && J < gc.ny;
+    const Tc scale = block_scalar<Tc>(sigma);
     if (active) {
-        const Tc scale = sigma ? (Tc)(*sigma) : (Tc)1;
         // fine points of this aggregate
         int ii[PX], jj[PY];
         int npx = 0, npy = 0;
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) k_restrict_2d_ts(Geom gf, Geom gc, Tc a, 
     const Tc yl1 = in10 ? cy[j1] : (Tc)0, yd1 = in10 ? cy[nyf + j1] : (Tc)0, yu1 = in10 ? cy[2 * nyf + j1] : (Tc)0;
     const int npts = (int)in00 + (int)in01 + (int)in10 + (int)in11;
     const Tc inv_count = npts > 0 ? (Tc)1 / (Tc)npts : (Tc)0;
-    const Tc scale = sigma ? (Tc)(*sigma) : (Tc)1;
+    const Tc scale = block_scalar<Tc>(sigma);
     // values and Laplacians of the four points at fine step kf
     auto step = [&](int kf, Tc (&c)[4], Tc (&l)[4]) {
         const int64_t r0 = gf.at(kf, j0, 0);
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(256) k_restrict_1d(Geom gf, Geom gc, int nu, T
     const Tc lo0 = has0 ? cx[p0] : (Tc)0, di0 = has0 ? cx[nf + p0] : (Tc)0, up0 = has0 ? cx[2 * nf + p0] : (Tc)0;
     const Tc lo1 = has1 ? cx[p1] : (Tc)0, di1 = has1 ? cx[nf + p1] : (Tc)0, up1 = has1 ? cx[2 * nf + p1] : (Tc)0;
     const Tc inv_count = SPACE ? ((Tc)1 / (Tc)(has1 ? 2 : 1)) : (Tc)1;
-    const Tc scale = sigma ? (Tc)(*sigma) : (Tc)1;
+    const Tc scale = block_scalar<Tc>(sigma);
     auto fine = [&](int k, int p) -> Tc { return (p >= 0 && p < nf) ? ldv<Tc>(v, gf.at(k, 0, p)) : (Tc)0; };
     // values and Laplacians of the thread's fine points at fine step k
     auto row = [&](int k, Tc &c0, Tc &c1, Tc &l0, Tc &l1) {

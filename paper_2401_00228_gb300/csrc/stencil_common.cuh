@@ -26,6 +26,17 @@ __device__ __forceinline__ double cvt_to<double, float2>(float2 v) {
     return (double)v.x + (double)v.y;
 }
 
+// A device FP64 scalar (may be null: 1) in the arithmetic type, converted once per block: a
+// double -> float conversion issues at GB300's FP64 rate, so per thread it costs as much as
+// the rest of a short kernel's arithmetic.  Every thread of the block must call it.
+template <typename T>
+__device__ __forceinline__ T block_scalar(const double *p) {
+    __shared__ T s_scalar;
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) s_scalar = p ? (T)(*p) : (T)1;
+    __syncthreads();
+    return s_scalar;
+}
+
 template <typename Tc, typename T>
 __device__ __forceinline__ Tc ldv(const T *__restrict__ p, int64_t i) {
     return (Tc)p[i];

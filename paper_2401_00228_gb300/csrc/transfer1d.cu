@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(TT) k_restrict_1d_t(Geom gf, Geom gc, Tc a, Tc
         if (lane == 31) right = eR[r];
         lap4(c[r], left, right, lo, di, up, l);
     };
-    const Tc scale = sigma ? (Tc)(*sigma) : (Tc)1;
+    const Tc scale = block_scalar<Tc>(sigma);
     const int nK = gc.nt + 1 - K0;
     // the norm of vhat for the next level's beta: summed per thread and per warp in the
     // arithmetic type (FP64 per element would run at the FP64 rate, 1/58 of FP32 here), in FP64
