@@ -21,6 +21,7 @@ void prof_reset();
 bool prof_read(int cls, int level, double &ms, double &bytes, int64_t &n);
 
 cudaError_t slab_set_attributes();
+cudaError_t interp2d_set_attributes();
 
 // adjoint helpers (stencil.cu)
 void launch_reverse_pack(const Geom &g, const double *dense, double *padded, cudaStream_t s);
@@ -91,6 +92,7 @@ static mk_status ensure_device() {
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CK(slab_set_attributes());
+    CK(interp2d_set_attributes());
     CK(dst_set_attributes());
     CK(coop_set_attributes());
     CK(march2d_set_attributes());

@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "stencil_common.cuh"
+#include "async_copy.cuh"
 
 namespace mk {
 
@@ -757,33 +758,6 @@ __global__ void __launch_bounds__(256) k_interp_1d(Geom gf, Geom gc, int nu, Tc 
     }
 }
 
-// 2D K4 with 2 x 2 aggregates in one arithmetic type T (FP32), walked in time.  A
-// thread owns the aggregate (I, J): the fine points (2I, 2I+1) x (2J, 2J+1), which share one
-// coarse value (Z vt)_{K(k)}.  Per fine step it forms x at those four points and at the two
-// points of each adjacent row (2J-1, 2J+2: the aggregates J-1 and J+1); the columns 2I-1 and
-// 2I+2 come from the neighbouring lanes by warp shuffles (the first and last lane form them
-// itself).  x_{k-1} and L x_{k-1} stay in registers from the previous step, so x and w are
-// written once per point and v read once per point from HBM (the adjacent rows are the
-// neighbouring threads' rows, served by the caches); the global loads of step k+1 are issued
-// before step k is computed.  The arithmetic is that of k_apply_2d (lap_at's order:
-// x part, then the y part added; w_k = (x_k - a L x_k) - (x_{k-1} + b L x_{k-1})).  MC: the
-// number of coarse directions combined (0: Xc itself).  Row starts are multiples of eight
-// elements and i0 is even, so the paired accesses are 8-byte aligned; a row is read only
-// where it is interior.
-template <typename T>
-__device__ __forceinline__ void ld_pair_t(const T *p, T &a, T &b);
-template <>
-__device__ __forceinline__ void ld_pair_t<float>(const float *p, float &a, float &b) {
-    const float2 q = *reinterpret_cast<const float2 *>(p);
-    a = q.x;
-    b = q.y;
-}
-template <>
-__device__ __forceinline__ void ld_pair_t<double>(const double *p, double &a, double &b) {
-    const double2 q = *reinterpret_cast<const double2 *>(p);
-    a = q.x;
-    b = q.y;
-}
 template <typename T>
 __device__ __forceinline__ void st_pair_t(T *p, T a, T b);
 template <>
@@ -795,21 +769,52 @@ __device__ __forceinline__ void st_pair_t<double>(double *p, double a, double b)
     *reinterpret_cast<double2 *>(p) = make_double2(a, b);
 }
 
-template <typename T, int MC>
-__global__ void __launch_bounds__(256, 2) k_interp_2d_ts(Geom gf, Geom gc, int nu, T a, T b,
-                                                         SpaceOp<T> L, const T *__restrict__ v,
+// 2D K4 with 2 x 2 aggregates in FP32, walked in time.  A thread owns the aggregate (I, J): the
+// fine points (2I, 2I+1) x (2J, 2J+1), which share one coarse value (Z vt)_{K(k)}.  Per fine
+// step it forms x at those four points and at the two points of each adjacent row (2J-1, 2J+2:
+// the aggregates J-1 and J+1); the columns 2I-1 and 2I+2 come from the neighbouring lanes by
+// warp shuffles (the first and last lane form them itself).  x_{k-1} and L x_{k-1} stay in
+// registers from the previous step, so x and w are written once per point and v read once per
+// point from HBM (the adjacent rows are the neighbouring threads' rows, served by the caches).
+// The arithmetic is that of k_apply_2d (lap_at's order: x part, then the y part added;
+// w_k = (x_k - a L x_k) - (x_{k-1} + b L x_{k-1})).  MC: the number of coarse directions
+// combined (0: Xc itself).
+// The loads of later steps are staged in shared memory: every thread copies its own words of
+// step k+2 (the four row pairs, the outer columns of the first and last lane, the coarse
+// values) into a three-stage ring with cp.async while it computes step k, and reads back only
+// what it copied (cp.async.wait_group orders that, no block barrier), so about two steps of
+// loads stay in flight at the register count of one (a register-staged version with one step
+// ahead took 266 us against 208 us per level-1 launch on the 255^2 x 1024 workload).  Fields are
+// laid out field-major (word t of a field belongs to thread t): a warp's accesses are
+// conflict-free.  Row starts are multiples of eight elements and i0 is even, so the paired
+// accesses are 8-byte aligned; a row is read only where it is interior.
+constexpr int I2C_STAGES = 3;
+constexpr int I2C_THREADS = 256;
+__host__ __device__ constexpr int i2c_fields(int nz) { return 10 + 4 * nz; }   // floats per thread and stage
+inline size_t i2c_smem_bytes(int mc) {
+    const int nz = mc > 0 ? mc : 1;
+    return sizeof(float) * (size_t)I2C_STAGES * i2c_fields(nz) * I2C_THREADS;
+}
+
+template <int MC>
+__global__ void __launch_bounds__(256, 2) k_interp_2d_cp(Geom gf, Geom gc, int nu, float a, float b,
+                                                         SpaceOp<float> L,
+                                                         const float *__restrict__ v,
                                                          const double *__restrict__ sigma,
-                                                         const T *__restrict__ Xc,
+                                                         const float *__restrict__ Xc,
                                                          int64_t xc_stride,
                                                          const double *__restrict__ yc,
-                                                         T *__restrict__ x, T *__restrict__ w,
-                                                         int kc, const int *__restrict__ done) {
+                                                         float *__restrict__ x,
+                                                         float *__restrict__ w, int kc,
+                                                         const int *__restrict__ done) {
     if (done && *done) return;   // the same flag for every thread of the block
     constexpr int NZ = MC > 0 ? MC : 1;
-    __shared__ T s_w[NZ + 1];
+    constexpr int SF = i2c_fields(NZ);
+    extern __shared__ float i2c_ring[];   // [I2C_STAGES][SF][I2C_THREADS]
+    __shared__ float s_w[NZ + 1];
     const int t = threadIdx.x + 32 * threadIdx.y;
-    if (t == 0) s_w[0] = sigma ? (T)(*sigma) : (T)1;
-    else if (MC > 0 && t <= MC) s_w[t] = (T)yc[t - 1];
+    if (t == 0) s_w[0] = sigma ? (float)(*sigma) : 1.f;
+    else if (MC > 0 && t <= MC) s_w[t] = (float)yc[t - 1];
     __syncthreads();
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x;
@@ -818,89 +823,109 @@ __global__ void __launch_bounds__(256, 2) k_interp_2d_ts(Geom gf, Geom gc, int n
     const int nx = gf.nx, ny = gf.ny;
     const int64_t ldx = gf.ldx, cld = gc.ldx;
     const int i0 = 2 * I, j0 = 2 * J;
-    if (j0 >= ny) return;   // the whole warp shares J
-    const T sig = s_w[0];
-    T ym[NZ];
+    if (j0 >= ny) return;   // the whole warp shares J; no block barrier follows
+    const float sig = s_w[0];
+    float ym[NZ];
 #pragma unroll
-    for (int m = 0; m < NZ; ++m) ym[m] = MC > 0 ? s_w[1 + m] : (T)1;
+    for (int m = 0; m < NZ; ++m) ym[m] = MC > 0 ? s_w[1 + m] : 1.f;
     const bool c0 = i0 < nx, c1 = i0 + 1 < nx, r1 = j0 + 1 < ny;
     const bool hd = c0 && j0 > 0, hu = c0 && j0 + 2 < ny;
     const bool cl = lane == 0 && i0 > 0 && i0 - 1 < nx, cr = lane == 31 && i0 + 2 < nx;
+    const bool ce = cl || cr;
     const int64_t o0 = (int64_t)j0 * ldx + i0;   // fine offset of (2J, 2I) in a plane
     const int64_t oc = (int64_t)J * cld + I;      // coarse offset of (J, I)
     const int64_t oe = o0 + (cl ? -1 : 2);        // outside column of the first / last lane
     const int64_t oce = oc + (cl ? -1 : 1);
-    // coefficients of the thread's columns and rows (0 where masked)
-    const T *cx = L.x, *cy = L.y;
+    const float *cx = L.x, *cy = L.y;
     const int i1 = i0 + 1, j1 = j0 + 1;
-    const T xl0 = c0 ? cx[i0] : (T)0, xd0 = c0 ? cx[nx + i0] : (T)0, xu0 = c0 ? cx[2 * nx + i0] : (T)0;
-    const T xl1 = c1 ? cx[i1] : (T)0, xd1 = c1 ? cx[nx + i1] : (T)0, xu1 = c1 ? cx[2 * nx + i1] : (T)0;
-    const T yl0 = c0 ? cy[j0] : (T)0, yd0 = c0 ? cy[ny + j0] : (T)0, yu0 = c0 ? cy[2 * ny + j0] : (T)0;
-    const T yl1 = (c0 && r1) ? cy[j1] : (T)0, yd1 = (c0 && r1) ? cy[ny + j1] : (T)0,
-            yu1 = (c0 && r1) ? cy[2 * ny + j1] : (T)0;
-    // raw loads of one step
-    T A0a = 0, A0b = 0, A1a = 0, A1b = 0, QDa = 0, QDb = 0, QUa = 0, QUb = 0, VE0 = 0, VE1 = 0;
-    T ZO[NZ], ZD[NZ], ZU[NZ], ZE[NZ];
-    auto load = [&](int k, int K) {
-        const T *vk = v + gf.guard + (int64_t)k * gf.plane;
-        const T *zk = Xc + gc.guard + (int64_t)K * gc.plane;
-        A0a = A0b = A1a = A1b = QDa = QDb = QUa = QUb = VE0 = VE1 = (T)0;
-        if (c0) ld_pair_t<T>(vk + o0, A0a, A0b);
-        if (c0 && r1) ld_pair_t<T>(vk + o0 + ldx, A1a, A1b);
-        if (hd) ld_pair_t<T>(vk + o0 - ldx, QDa, QDb);
-        if (hu) ld_pair_t<T>(vk + o0 + 2 * ldx, QUa, QUb);
+    const float xl0 = c0 ? cx[i0] : 0.f, xd0 = c0 ? cx[nx + i0] : 0.f, xu0 = c0 ? cx[2 * nx + i0] : 0.f;
+    const float xl1 = c1 ? cx[i1] : 0.f, xd1 = c1 ? cx[nx + i1] : 0.f, xu1 = c1 ? cx[2 * nx + i1] : 0.f;
+    const float yl0 = c0 ? cy[j0] : 0.f, yd0 = c0 ? cy[ny + j0] : 0.f, yu0 = c0 ? cy[2 * ny + j0] : 0.f;
+    const float yl1 = (c0 && r1) ? cy[j1] : 0.f, yd1 = (c0 && r1) ? cy[ny + j1] : 0.f,
+                yu1 = (c0 && r1) ? cy[2 * ny + j1] : 0.f;
+    // ring fields of this thread: pairs of rows j0, j0+1, j0-1, j0+2, the two outer-column
+    // values, then for each coarse direction the values of aggregates (J,I), (J-1,I), (J+1,I)
+    // and the outer one
+    auto field = [&](int stage, int f) -> float * {
+        return i2c_ring + ((int64_t)stage * SF + f) * I2C_THREADS + t;
+    };
+    auto pair = [&](int stage, int f) -> float2 * {   // fields 2f, 2f+1 hold one float2 per thread
+        return reinterpret_cast<float2 *>(i2c_ring + ((int64_t)stage * SF + 2 * f) * I2C_THREADS) + t;
+    };
+    auto issue = [&](int k, int K, int stage) {
+        const float *vk = v + gf.guard + (int64_t)k * gf.plane;
+        const float *zk = Xc + gc.guard + (int64_t)K * gc.plane;
+        if (c0) cp_async8(pair(stage, 0), vk + o0);
+        if (c0 && r1) cp_async8(pair(stage, 1), vk + o0 + ldx);
+        if (hd) cp_async8(pair(stage, 2), vk + o0 - ldx);
+        if (hu) cp_async8(pair(stage, 3), vk + o0 + 2 * ldx);
+        if (ce) {
+            cp_async4(field(stage, 8), vk + oe);
+            if (r1) cp_async4(field(stage, 9), vk + oe + ldx);
+        }
 #pragma unroll
         for (int m = 0; m < NZ; ++m) {
-            const T *zm = zk + (int64_t)m * xc_stride;
-            ZO[m] = c0 ? zm[oc] : (T)0;
-            ZD[m] = hd ? zm[oc - cld] : (T)0;
-            ZU[m] = hu ? zm[oc + cld] : (T)0;
-            ZE[m] = (cl || cr) ? zm[oce] : (T)0;
+            const float *zm = zk + (int64_t)m * xc_stride;
+            if (c0) cp_async4(field(stage, 10 + 4 * m), zm + oc);
+            if (hd) cp_async4(field(stage, 11 + 4 * m), zm + oc - cld);
+            if (hu) cp_async4(field(stage, 12 + 4 * m), zm + oc + cld);
+            if (ce) cp_async4(field(stage, 13 + 4 * m), zm + oce);
         }
-        if (cl || cr) {
-            VE0 = vk[oe];
-            if (r1) VE1 = vk[oe + ldx];
-        }
+        cp_async_commit();
     };
-    auto comb = [&](const T (&zr)[NZ]) -> T {
-        if (MC == 0) return zr[0];
-        T z = mul_rn(ym[0], zr[0]);
+    auto comb = [&](int stage, int f) -> float {   // f: 0 own, 1 below, 2 above, 3 outer
+        if (MC == 0) return *field(stage, 10 + f);
+        float z = mul_rn(ym[0], *field(stage, 10 + f));
 #pragma unroll
-        for (int m = 1; m < NZ; ++m) z = fma_rn(ym[m], zr[m], z);
+        for (int m = 1; m < NZ; ++m) z = fma_rn(ym[m], *field(stage, 10 + 4 * m + f), z);
         return z;
     };
     const int k0 = blockIdx.z * kc;
     const int k1 = min(k0 + kc, gf.nt + 1);
     const int kstart = k0 > 0 ? k0 - 1 : 0;
-    // coarse block of fine step k: 0 for k = 0, (k-1)/nu + 1 otherwise (tracked incrementally)
+    // coarse block of fine step k: 0 for k = 0, (k-1)/nu + 1 otherwise; tracked for the step
+    // being issued, two ahead of the step being computed
     int K = (kstart == 0) ? 0 : (kstart - 1) / nu + 1;
     int ph = (kstart == 0) ? nu - 1 : (kstart - 1) % nu;
-    T p00 = 0, p01 = 0, p10 = 0, p11 = 0;   // x_{k-1}
-    T L00 = 0, L01 = 0, L10 = 0, L11 = 0;   // L x_{k-1}
-    load(kstart, K);
-    for (int k = kstart; k < k1; ++k) {
-        const T a0a = A0a, a0b = A0b, a1a = A1a, a1b = A1b, qda = QDa, qdb = QDb, qua = QUa,
-                qub = QUb, ve0 = VE0, ve1 = VE1;
-        const T zo = comb(ZO), zd = comb(ZD), zu = comb(ZU), ze = comb(ZE);
-        if (k + 1 < k1) {
-            if (ph == nu - 1) {
-                ++K;
-                ph = 0;
-            } else {
-                ++ph;
-            }
-            load(k + 1, K);
+    auto advance = [&]() {
+        if (ph == nu - 1) {
+            ++K;
+            ph = 0;
+        } else {
+            ++ph;
         }
-        const T x00 = c0 ? fma_rn(sig, a0a, -zo) : (T)0;
-        const T x01 = c1 ? fma_rn(sig, a0b, -zo) : (T)0;
-        const T x10 = (c0 && r1) ? fma_rn(sig, a1a, -zo) : (T)0;
-        const T x11 = (c1 && r1) ? fma_rn(sig, a1b, -zo) : (T)0;
-        const T d0 = hd ? fma_rn(sig, qda, -zd) : (T)0, d1 = (hd && c1) ? fma_rn(sig, qdb, -zd) : (T)0;
-        const T e0 = hu ? fma_rn(sig, qua, -zu) : (T)0, e1 = (hu && c1) ? fma_rn(sig, qub, -zu) : (T)0;
-        T l0 = __shfl_up_sync(FULL, x01, 1), l1 = __shfl_up_sync(FULL, x11, 1);
-        T q0 = __shfl_down_sync(FULL, x00, 1), q1 = __shfl_down_sync(FULL, x10, 1);
-        const T xe0 = (cl || cr) ? fma_rn(sig, ve0, -ze) : (T)0;
-        const T xe1 = ((cl || cr) && r1) ? fma_rn(sig, ve1, -ze) : (T)0;
+    };
+    issue(kstart, K, 0);
+    if (kstart + 1 < k1) {
+        advance();
+        issue(kstart + 1, K, 1);
+    } else {
+        cp_async_commit();
+    }
+    float p00 = 0.f, p01 = 0.f, p10 = 0.f, p11 = 0.f;   // x_{k-1}
+    float L00 = 0.f, L01 = 0.f, L10 = 0.f, L11 = 0.f;   // L x_{k-1}
+    int st = 0;   // stage of step k
+    for (int k = kstart; k < k1; ++k) {
+        if (k + 2 < k1) {
+            advance();
+            issue(k + 2, K, (st + 2) % I2C_STAGES);
+        } else {
+            cp_async_commit();
+        }
+        cp_async_wait<2>();   // this thread's copies of step k have landed
+        const float2 A0 = *pair(st, 0), A1 = *pair(st, 1), QD = *pair(st, 2), QU = *pair(st, 3);
+        const float ve0 = *field(st, 8), ve1 = *field(st, 9);
+        const float zo = comb(st, 0), zd = comb(st, 1), zu = comb(st, 2), ze = comb(st, 3);
+        const float x00 = c0 ? fma_rn(sig, A0.x, -zo) : 0.f;
+        const float x01 = c1 ? fma_rn(sig, A0.y, -zo) : 0.f;
+        const float x10 = (c0 && r1) ? fma_rn(sig, A1.x, -zo) : 0.f;
+        const float x11 = (c1 && r1) ? fma_rn(sig, A1.y, -zo) : 0.f;
+        const float d0 = hd ? fma_rn(sig, QD.x, -zd) : 0.f, d1 = (hd && c1) ? fma_rn(sig, QD.y, -zd) : 0.f;
+        const float e0 = hu ? fma_rn(sig, QU.x, -zu) : 0.f, e1 = (hu && c1) ? fma_rn(sig, QU.y, -zu) : 0.f;
+        float l0 = __shfl_up_sync(FULL, x01, 1), l1 = __shfl_up_sync(FULL, x11, 1);
+        float q0 = __shfl_down_sync(FULL, x00, 1), q1 = __shfl_down_sync(FULL, x10, 1);
+        const float xe0 = ce ? fma_rn(sig, ve0, -ze) : 0.f;
+        const float xe1 = (ce && r1) ? fma_rn(sig, ve1, -ze) : 0.f;
         if (lane == 0) {
             l0 = xe0;
             l1 = xe1;
@@ -909,25 +934,42 @@ __global__ void __launch_bounds__(256, 2) k_interp_2d_ts(Geom gf, Geom gc, int n
             q0 = xe0;
             q1 = xe1;
         }
-        const T s00 = (xd0 * x00 + xl0 * l0 + xu0 * x01) + (yd0 * x00 + yl0 * d0 + yu0 * x10);
-        const T s01 = (xd1 * x01 + xl1 * x00 + xu1 * q0) + (yd0 * x01 + yl0 * d1 + yu0 * x11);
-        const T s10 = (xd0 * x10 + xl0 * l1 + xu0 * x11) + (yd1 * x10 + yl1 * x00 + yu1 * e0);
-        const T s11 = (xd1 * x11 + xl1 * x10 + xu1 * q1) + (yd1 * x11 + yl1 * x01 + yu1 * e1);
+        const float s00 = (xd0 * x00 + xl0 * l0 + xu0 * x01) + (yd0 * x00 + yl0 * d0 + yu0 * x10);
+        const float s01 = (xd1 * x01 + xl1 * x00 + xu1 * q0) + (yd0 * x01 + yl0 * d1 + yu0 * x11);
+        const float s10 = (xd0 * x10 + xl0 * l1 + xu0 * x11) + (yd1 * x10 + yl1 * x00 + yu1 * e0);
+        const float s11 = (xd1 * x11 + xl1 * x10 + xu1 * q1) + (yd1 * x11 + yl1 * x01 + yu1 * e1);
         if (k >= k0 && c0) {
-            auto wk = [&](T c, T Lc, T p, T Lp) -> T {
+            auto wk = [&](float c, float Lc, float p, float Lp) -> float {
                 return k == 0 ? c : (c - a * Lc) - (p + b * Lp);
             };
             const int64_t f0 = gf.guard + (int64_t)k * gf.plane + o0;
-            st_pair_t<T>(x + f0, x00, x01);
-            st_pair_t<T>(w + f0, wk(x00, s00, p00, L00), c1 ? wk(x01, s01, p01, L01) : (T)0);
+            st_pair_t<float>(x + f0, x00, x01);
+            st_pair_t<float>(w + f0, wk(x00, s00, p00, L00), c1 ? wk(x01, s01, p01, L01) : 0.f);
             if (r1) {
-                st_pair_t<T>(x + f0 + ldx, x10, x11);
-                st_pair_t<T>(w + f0 + ldx, wk(x10, s10, p10, L10), c1 ? wk(x11, s11, p11, L11) : (T)0);
+                st_pair_t<float>(x + f0 + ldx, x10, x11);
+                st_pair_t<float>(w + f0 + ldx, wk(x10, s10, p10, L10), c1 ? wk(x11, s11, p11, L11) : 0.f);
             }
         }
         p00 = x00; p01 = x01; p10 = x10; p11 = x11;
         L00 = s00; L01 = s01; L10 = s10; L11 = s11;
+        st = (st + 1) % I2C_STAGES;
     }
+    cp_async_wait<0>();   // no copy outlives the kernel
+}
+
+cudaError_t interp2d_set_attributes() {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *f, int mc) {
+        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)i2c_smem_bytes(mc));
+        if (r != cudaSuccess) e = r;
+    };
+    set((const void *)k_interp_2d_cp<0>, 0);
+    set((const void *)k_interp_2d_cp<1>, 1);
+    set((const void *)k_interp_2d_cp<2>, 2);
+    set((const void *)k_interp_2d_cp<3>, 3);
+    set((const void *)k_interp_2d_cp<4>, 4);
+    return e;
 }
 
 template <typename Tv, typename Tz, typename Tx, typename Tw, typename Tc>
@@ -980,8 +1022,8 @@ void launch_interp(const Geom &gf, const Geom &gc, int nu, bool space, const Wei
             const int kct = (int)kt;
             const dim3 grid((ncx + 31) / 32, (ncy + 7) / 8, (nsteps + kct - 1) / kct), blk(32, 8, 1);
 #define MK_I2T(M)                                                                                \
-    k_interp_2d_ts<Tc, M><<<grid, blk, 0, s>>>(gf, gc, nu, a, b, L, v, sigma, Xc, xc_stride, yc, x, \
-                                               wout, kct, done)
+    k_interp_2d_cp<M><<<grid, blk, i2c_smem_bytes(M), s>>>(gf, gc, nu, a, b, L, v, sigma, Xc,       \
+                                                           xc_stride, yc, x, wout, kct, done)
             if (!yc) MK_I2T(0);
             else if (mc == 1) MK_I2T(1);
             else if (mc == 2) MK_I2T(2);
