@@ -461,7 +461,7 @@ void mk_destroy_batch(mk_batch *batch);
    library's device code is loaded, and every completed launch leaves it at zero.
    Set-up: the first call on each device looks up the scratch's address
    (cudaGetSymbolAddress, with that device current), which may load the library's device
-   code; make one call on each device before any stream capture.  The address is kept for
+   code; make that first call where loading device code is allowed.  The address is kept for
    the life of the process: after a device reset (cudaDeviceReset, or a primary-context
    reset by other code) the library's device code is reloaded and calls of this entry point
    are undefined.
