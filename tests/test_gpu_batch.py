@@ -42,7 +42,7 @@ def _handles(ms):
     return [mk.Problem(P.dim, P.nx, P.tau, P.theta, P.dt, P.nt, P.g, ny=P.ny) for P in ms]
 
 
-@pytest.mark.parametrize("precision,bound", [("fp64", 1e-10), ("mixed", 1e-8)])
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-10), ("mixed", 1e-8), ("mixed32", 1e-8)])
 @pytest.mark.parametrize("autotune", [False, True])
 def test_batch_matches_oracle(precision, bound, autotune):
     ms = _members()
@@ -60,7 +60,7 @@ def test_batch_matches_oracle(precision, bound, autotune):
         p.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed32"])
 def test_batch_equals_single_solves(precision):
     ms = _members()
     probs = _handles(ms)
@@ -119,21 +119,28 @@ def test_batch_invalid_arguments():
         p.close()
 
 
-def test_batch_uneven_members_full_size():
+@pytest.fixture(scope="module")
+def uneven_full():
+    ms = W.batched_problems(seed=4, count_1d=6, count_2d=2)
+    refs = [O.theta_march(P.dim, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, P.u0, P.g) for P in ms]
+    return ms, refs
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed32"])
+def test_batch_uneven_members_full_size(uneven_full, precision):
     """Members of the uneven batched workload at their full sizes (1D: n in 63..2047, n_t in
     256..8192; 2D: side in 63..255, n_t in 128..1024; tau in [0.1, 10], theta in {1/2, 1}; end
     time from a Courant number in the range of its theta; the 3-level 1D and 4-level 2D
-    schedules, mixed precision, tol 1e-10).  Every member must converge and match the oracle's
+    schedules, both mixed modes, tol 1e-10).  Every member must converge and match the oracle's
     march within the metric's 1e-8 max relative error."""
-    ms = W.batched_problems(seed=4, count_1d=6, count_2d=2)
+    ms, refs = uneven_full
     probs = _handles(ms)
-    opts = [_opts(P, "mixed", tol=1e-10, max_iters=2000) for P in ms]
+    opts = [_opts(P, precision, tol=1e-10, max_iters=2000) for P in ms]
     outs = [np.empty((P.nt + 1,) + P.space_shape()) for P in ms]
     with mk.Batch(probs, opts) as b:
         infos = b.solve([P.u0 for P in ms], outs)
-    for P, u, info in zip(ms, outs, infos):
+    for P, u, info, ref in zip(ms, outs, infos, refs):
         assert info.rel_residual <= 1e-10 * 1.0001, (P.name, info.iterations)
-        ref = O.theta_march(P.dim, P.nx, P.ny, P.nt, P.tau, P.theta, P.dt, P.u0, P.g)
         assert O.max_rel_error(u, ref) <= 1e-8, (P.name, P.nx, P.nt)
     for p in probs:
         p.close()
