@@ -164,14 +164,16 @@ __global__ void __launch_bounds__(KR_THREADS) k_update(int64_t len, const TW *__
 
 // ---------------------------------------------------------------------------------------
 // FP32 vectors with more than MK_MAX_INNER basis vectors (level 1 with the FP32 basis).
-// multidot: a tile is 16 consecutive elements per thread in four float4 loads (coalesced
+// multidot: a tile is 8 consecutive elements per thread in two float4 loads (coalesced
 // across the block), two basis vectors per sweep with the W tile re-read from L1; sums in
 // FP32 per thread and warp, in FP64 across tiles and warps.  update: four consecutive
 // elements per thread and step (float4), the basis loop unrolled so that its loads overlap.
-// Vector lengths and strides are whole numbers of 4096-element tiles.
+// Vector lengths and strides are whole numbers of 2048-element tiles.  (Four float4 loads per
+// thread and tile left a 33.6 MB vector with 2049 tiles on 608 blocks: 4 against 3.37 per
+// block on average; two per thread raised the 1D level-1 multidot from 4.63 to 4.85 TB/s.)
 // ---------------------------------------------------------------------------------------
-constexpr int F4_Q = 4;                            // float4 loads per thread per tile
-constexpr int F4_TILE = KR_THREADS * 4 * F4_Q;     // elements per block tile (4096)
+constexpr int F4_Q = 2;                            // float4 loads per thread per tile
+constexpr int F4_TILE = KR_THREADS * 4 * F4_Q;     // elements per block tile (2048)
 
 __global__ void __launch_bounds__(KR_THREADS) k_multidot_f4(int64_t len, const float *__restrict__ W,
                                                             const float *__restrict__ V,
